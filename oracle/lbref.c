@@ -1,0 +1,841 @@
+/*
+ * lbref.c -- plain FP64 CPU oracle of the self-diffusiophoretic lattice
+ * Boltzmann time step.  TEST INFRASTRUCTURE ONLY (see lbref.h): it is the
+ * slow definition the CUDA path is compared with, written node by node in the
+ * order the model states it, with no blocking or fusion.
+ *
+ * One step, in order (the paper gives the model as PDEs; the discrete reading
+ * of each step is stated where it is used):
+ *   S1  chemical potentials mu_psi, mu_phi            (Eq. chem_potentials)
+ *   S2  thermodynamic force on the fluid              (reading: -psi grad mu_psi
+ *                                                      - phi grad mu_phi + g)
+ *   S3  D3Q19 pull streaming, halfway bounce-back on walls, moving bounce-back
+ *       on particle links with phoretic slip          (Sec. Particles, Eq. for v_s)
+ *       then BGK collision with Guo forcing
+ *   S4  explicit conservative update of psi and phi   (Eq. diffusion_reaction)
+ *       with Janus production (Eq. activity) and the sink k_d (phi - phi0)
+ *   S5  momentum exchange sums per particle
+ *   S6  implicit particle velocity update, move, rotate
+ *   S7  covering / uncovering of nodes swept by moving particles
+ *
+ * Built with -ffp-contract=off so that no multiply-add is fused; the
+ * geometric decisions (solid or fluid, active or inactive) are then taken with
+ * exactly the products and sums written here.
+ */
+#include "lbref.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define REF_MAXP 255
+
+/* D3Q19 velocity set and weights (order documented in lbref.h). */
+static const int CX[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+static const int CY[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+static const int CZ[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+static const double W[19] = {
+    1.0 / 3.0,
+    1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0,
+    1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
+    1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+static int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+typedef struct {
+    double X[3], U[3], Om[3], m[3];
+    double R, R2, M, I, alpha, mu_p, mu_m, H;
+    double ext_f[3], ext_t[3];
+    int fixed;
+    /* link sums of the current step */
+    double F0[3], T0[3], zeta[6][6];
+    /* impulses of covering/uncovering, applied in the next step */
+    double imp_f[3], imp_t[3];
+    double force[3], torque[3];
+} ref_part;
+
+struct ref_sim {
+    ref_params p;
+    long N;
+    double* f;    /* [19][N] post-collision populations */
+    double* fn;   /* work buffer */
+    double *psi, *phi, *mupsi, *muphi, *u, *psin, *phin;
+    unsigned char *mask, *maskn;
+    int np;
+    ref_part part[REF_MAXP];
+    long nfluid;
+    int err;
+};
+
+/* ------------------------------------------------------------------ */
+/* geometry                                                            */
+/* ------------------------------------------------------------------ */
+
+static long nidx(const ref_sim* s, int x, int y, int z)
+{
+    return (long)x + (long)s->p.nx * ((long)y + (long)s->p.ny * (long)z);
+}
+
+/* Neighbour of node (x,y,z) along (dx,dy,dz), wrapped on periodic axes;
+ * -1 when it lies beyond a wall. */
+static long nbr(const ref_sim* s, int x, int y, int z, int dx, int dy, int dz)
+{
+    int n[3] = {s->p.nx, s->p.ny, s->p.nz};
+    int c[3] = {x + dx, y + dy, z + dz};
+    for (int a = 0; a < 3; ++a) {
+        if (c[a] < 0) {
+            if (!s->p.periodic[a]) return -1;
+            c[a] += n[a];
+        } else if (c[a] >= n[a]) {
+            if (!s->p.periodic[a]) return -1;
+            c[a] -= n[a];
+        }
+    }
+    return nidx(s, c[0], c[1], c[2]);
+}
+
+/* Minimum-image component of d on an axis of length L. */
+static double mimg(double d, int L, int periodic)
+{
+    if (periodic) {
+        if (d > 0.5 * L)
+            d -= L;
+        else if (d < -0.5 * L)
+            d += L;
+    }
+    return d;
+}
+
+/* Node-to-centre offset r = x - X (minimum image). */
+static void node_offset(const ref_sim* s, const ref_part* P, int x, int y, int z, double r[3])
+{
+    r[0] = mimg((double)x - P->X[0], s->p.nx, s->p.periodic[0]);
+    r[1] = mimg((double)y - P->X[1], s->p.ny, s->p.periodic[1]);
+    r[2] = mimg((double)z - P->X[2], s->p.nz, s->p.periodic[2]);
+}
+
+/* A node is inside a sphere when |x - X|^2 < R^2 (strict). */
+static int inside(const ref_sim* s, const ref_part* P, int x, int y, int z)
+{
+    double r[3];
+    node_offset(s, P, x, y, z, r);
+    double d2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    return d2 < P->R2;
+}
+
+/* Mask value of a node: 0 = fluid, k+1 = inside particle k (first match). */
+static unsigned char owner(const ref_sim* s, int x, int y, int z)
+{
+    for (int k = 0; k < s->np; ++k)
+        if (inside(s, &s->part[k], x, y, z)) return (unsigned char)(k + 1);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* lattice Boltzmann pieces                                            */
+/* ------------------------------------------------------------------ */
+
+/* Second-order equilibrium, f_i^eq = w_i rho [1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u^2]. */
+static double feq(int i, double rho, const double u[3])
+{
+    double cu = CX[i] * u[0] + CY[i] * u[1] + CZ[i] * u[2];
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    return W[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+}
+
+static double phi0_of(const ref_sim* s, double psi) { return s->p.phi_b + s->p.E * tanh(psi); }
+
+/* Offset of the link midpoint from the centre: r_b = (x - X) + c_i / 2. */
+static void link_offset(const ref_sim* s, const ref_part* P, int x, int y, int z, int i, double r[3])
+{
+    node_offset(s, P, x, y, z, r);
+    r[0] += 0.5 * CX[i];
+    r[1] += 0.5 * CY[i];
+    r[2] += 0.5 * CZ[i];
+}
+
+/* Isotropic gradient of phi at a fluid node, 3 sum_i w_i c_i phi(x+c_i), with
+ * the value at x standing in for solid and wall neighbours (no flux). */
+static void grad_phi(const ref_sim* s, int x, int y, int z, double g[3])
+{
+    long n = nidx(s, x, y, z);
+    double own = s->phi[n];
+    g[0] = g[1] = g[2] = 0.0;
+    for (int i = 1; i < 19; ++i) {
+        long m = nbr(s, x, y, z, CX[i], CY[i], CZ[i]);
+        double v = (m < 0 || s->mask[m]) ? own : s->phi[m];
+        g[0] += W[i] * CX[i] * v;
+        g[1] += W[i] * CY[i] * v;
+        g[2] += W[i] * CZ[i] * v;
+    }
+    g[0] *= 3.0;
+    g[1] *= 3.0;
+    g[2] *= 3.0;
+}
+
+/* Velocity of the boundary at the midpoint of link x -> x+c_i on particle P:
+ * rigid motion plus phoretic slip v_s = mu (1 - n n) . grad phi, with the
+ * Janus mobility mu_- where m.n <= 0 and mu_+ elsewhere (Sec. Particles). */
+static void link_velocity(const ref_sim* s, const ref_part* P, int x, int y, int z, int i,
+                          double r[3], double ub[3], double vs[3])
+{
+    link_offset(s, P, x, y, z, i, r);
+    double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    double nh[3] = {r[0] / rn, r[1] / rn, r[2] / rn};
+    double side = P->m[0] * r[0] + P->m[1] * r[1] + P->m[2] * r[2];
+    double mu = (side <= 0.0) ? P->mu_m : P->mu_p;
+    double g[3];
+    grad_phi(s, x, y, z, g);
+    double ng = nh[0] * g[0] + nh[1] * g[1] + nh[2] * g[2];
+    for (int a = 0; a < 3; ++a) vs[a] = mu * (g[a] - nh[a] * ng);
+    ub[0] = P->U[0] + (P->Om[1] * r[2] - P->Om[2] * r[1]) + vs[0];
+    ub[1] = P->U[1] + (P->Om[2] * r[0] - P->Om[0] * r[2]) + vs[1];
+    ub[2] = P->U[2] + (P->Om[0] * r[1] - P->Om[1] * r[0]) + vs[2];
+}
+
+/* ------------------------------------------------------------------ */
+/* S1: chemical potentials (Eq. chem_potentials)                       */
+/* ------------------------------------------------------------------ */
+
+static void step_mu(ref_sim* s)
+{
+    const ref_params* p = &s->p;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long n = nidx(s, x, y, z);
+                if (s->mask[n]) {
+                    s->mupsi[n] = 0.0;
+                    s->muphi[n] = 0.0;
+                    continue;
+                }
+                double ps = s->psi[n], ph = s->phi[n];
+                /* isotropic Laplacian 6 sum_i w_i (psi(x+c_i) - psi(x)); a
+                 * solid neighbour carries the wetting ghost
+                 * psi(x) + (H/kappa) c_i.n_hat, a wall neighbour psi(x). */
+                double lap = 0.0;
+                for (int i = 1; i < 19; ++i) {
+                    long m = nbr(s, x, y, z, CX[i], CY[i], CZ[i]);
+                    double v;
+                    if (m < 0) {
+                        v = ps;
+                    } else if (s->mask[m]) {
+                        const ref_part* P = &s->part[s->mask[m] - 1];
+                        if (P->H != 0.0) {
+                            double r[3];
+                            link_offset(s, P, x, y, z, i, r);
+                            double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+                            double cn = (CX[i] * r[0] + CY[i] * r[1] + CZ[i] * r[2]) / rn;
+                            v = ps + (P->H / p->kappa) * cn;
+                        } else {
+                            v = ps;
+                        }
+                    } else {
+                        v = s->psi[m];
+                    }
+                    lap += W[i] * (v - ps);
+                }
+                lap *= 6.0;
+                double dphi = ph - phi0_of(s, ps);
+                double ch = cosh(ps);
+                s->muphi[n] = p->C * dphi;
+                s->mupsi[n] = p->A * (ps * ps * ps - ps) - p->kappa * lap - p->C * p->E * dphi / (ch * ch);
+            }
+}
+
+/* ------------------------------------------------------------------ */
+/* S2 + S3: force, streaming with bounce-back, BGK + Guo collision     */
+/* ------------------------------------------------------------------ */
+
+static void step_collide(ref_sim* s)
+{
+    const ref_params* p = &s->p;
+    const long N = s->N;
+    for (int k = 0; k < s->np; ++k) {
+        ref_part* P = &s->part[k];
+        for (int a = 0; a < 3; ++a) P->F0[a] = P->T0[a] = 0.0;
+        memset(P->zeta, 0, sizeof(P->zeta));
+    }
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long n = nidx(s, x, y, z);
+                if (s->mask[n]) {
+                    for (int i = 0; i < 19; ++i) s->fn[i * N + n] = 0.0;
+                    s->u[n] = s->u[N + n] = s->u[2 * N + n] = 0.0;
+                    continue;
+                }
+                /* S2: F = -psi grad mu_psi - phi grad mu_phi + g, gradients by
+                 * 3 sum_i w_i c_i mu(x+c_i); solid/wall neighbours use mu(x). */
+                double F[3] = {p->body_force[0], p->body_force[1], p->body_force[2]};
+                if (p->thermo_force) {
+                    double gps[3] = {0, 0, 0}, gph[3] = {0, 0, 0};
+                    for (int i = 1; i < 19; ++i) {
+                        long m = nbr(s, x, y, z, CX[i], CY[i], CZ[i]);
+                        double a = (m < 0 || s->mask[m]) ? s->mupsi[n] : s->mupsi[m];
+                        double b = (m < 0 || s->mask[m]) ? s->muphi[n] : s->muphi[m];
+                        gps[0] += W[i] * CX[i] * a;
+                        gps[1] += W[i] * CY[i] * a;
+                        gps[2] += W[i] * CZ[i] * a;
+                        gph[0] += W[i] * CX[i] * b;
+                        gph[1] += W[i] * CY[i] * b;
+                        gph[2] += W[i] * CZ[i] * b;
+                    }
+                    for (int a = 0; a < 3; ++a)
+                        F[a] += -s->psi[n] * (3.0 * gps[a]) - s->phi[n] * (3.0 * gph[a]);
+                }
+                /* S3: pull f_j(x) = f*_j(x - c_j); a wall source reflects
+                 * f*_{jbar}(x); a particle source reflects with the moving
+                 * boundary term (Ladd): f_j = f*_i(x) - 6 w_i rho0 c_i.u_b,
+                 * i = jbar, and the particle receives c_i (f*_i + f_j). */
+                double fl[19];
+                for (int j = 0; j < 19; ++j) {
+                    if (j == 0) {
+                        fl[0] = s->f[n];
+                        continue;
+                    }
+                    long m = nbr(s, x, y, z, -CX[j], -CY[j], -CZ[j]);
+                    int i = opp(j);
+                    if (m < 0) {
+                        fl[j] = s->f[i * N + n];
+                    } else if (s->mask[m]) {
+                        ref_part* P = &s->part[s->mask[m] - 1];
+                        double r[3], ub[3], vs[3];
+                        link_velocity(s, P, x, y, z, i, r, ub, vs);
+                        double cub = CX[i] * ub[0] + CY[i] * ub[1] + CZ[i] * ub[2];
+                        double fi = s->f[i * N + n];
+                        fl[j] = fi - 6.0 * W[i] * p->rho0 * cub;
+                        /* momentum exchange split into the part independent of
+                         * (U, Omega) and the linear drag matrix zeta */
+                        double cvs = CX[i] * vs[0] + CY[i] * vs[1] + CZ[i] * vs[2];
+                        double mag = 2.0 * fi - 6.0 * W[i] * p->rho0 * cvs;
+                        double dP[3] = {CX[i] * mag, CY[i] * mag, CZ[i] * mag};
+                        P->F0[0] += dP[0];
+                        P->F0[1] += dP[1];
+                        P->F0[2] += dP[2];
+                        P->T0[0] += r[1] * dP[2] - r[2] * dP[1];
+                        P->T0[1] += r[2] * dP[0] - r[0] * dP[2];
+                        P->T0[2] += r[0] * dP[1] - r[1] * dP[0];
+                        double g6[6] = {(double)CX[i], (double)CY[i], (double)CZ[i],
+                                        r[1] * CZ[i] - r[2] * CY[i],
+                                        r[2] * CX[i] - r[0] * CZ[i],
+                                        r[0] * CY[i] - r[1] * CX[i]};
+                        double zc = 6.0 * W[i] * p->rho0;
+                        for (int a = 0; a < 6; ++a)
+                            for (int b = 0; b < 6; ++b) P->zeta[a][b] += zc * g6[a] * g6[b];
+                    } else {
+                        fl[j] = s->f[j * N + m];
+                    }
+                }
+                double rho = 0.0, jm[3] = {0, 0, 0};
+                for (int j = 0; j < 19; ++j) {
+                    rho += fl[j];
+                    jm[0] += CX[j] * fl[j];
+                    jm[1] += CY[j] * fl[j];
+                    jm[2] += CZ[j] * fl[j];
+                }
+                double u[3];
+                for (int a = 0; a < 3; ++a) u[a] = (jm[a] + 0.5 * F[a]) / rho;
+                double omf = 1.0 - 0.5 / p->tau;
+                for (int j = 0; j < 19; ++j) {
+                    double c[3] = {(double)CX[j], (double)CY[j], (double)CZ[j]};
+                    double cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+                    /* Guo source w_j [3 (c - u) + 9 (c.u) c] . F */
+                    double S = 0.0;
+                    for (int a = 0; a < 3; ++a) S += (3.0 * (c[a] - u[a]) + 9.0 * cu * c[a]) * F[a];
+                    S *= W[j];
+                    double fe = feq(j, rho, u);
+                    s->fn[j * N + n] = fl[j] - (fl[j] - fe) / p->tau + omf * S;
+                }
+                s->u[n] = u[0];
+                s->u[N + n] = u[1];
+                s->u[2 * N + n] = u[2];
+            }
+    double* t = s->f;
+    s->f = s->fn;
+    s->fn = t;
+}
+
+/* ------------------------------------------------------------------ */
+/* S4: scalar transport (Eq. diffusion_reaction) with source and sink  */
+/* ------------------------------------------------------------------ */
+
+static void step_scalars(ref_sim* s)
+{
+    const ref_params* p = &s->p;
+    const long N = s->N;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long n = nidx(s, x, y, z);
+                if (s->mask[n]) {
+                    s->psin[n] = 0.0;
+                    s->phin[n] = 0.0;
+                    continue;
+                }
+                double ps = s->psi[n], ph = s->phi[n];
+                double u0[3] = {s->u[n], s->u[N + n], s->u[2 * N + n]};
+                double dps = 0.0, dph = 0.0;
+                unsigned char adj[REF_MAXP];
+                memset(adj, 0, (size_t)s->np);
+                /* flux on each fluid-fluid link: diffusion M (mu(y) - mu(x))
+                 * minus the advective flux, taken upwind (donor cell) with
+                 * the link-mean velocity ub = c.(u(x) + u(y))/2; links to
+                 * solid or wall carry no flux. */
+                for (int i = 1; i < 19; ++i) {
+                    long m = nbr(s, x, y, z, CX[i], CY[i], CZ[i]);
+                    if (m < 0) continue;
+                    if (s->mask[m]) {
+                        adj[s->mask[m] - 1] = 1;
+                        continue;
+                    }
+                    double cu0 = CX[i] * u0[0] + CY[i] * u0[1] + CZ[i] * u0[2];
+                    double cu1 = CX[i] * s->u[m] + CY[i] * s->u[N + m] + CZ[i] * s->u[2 * N + m];
+                    double ub = 0.5 * (cu0 + cu1);
+                    double aps = ub > 0.0 ? ub * ps : ub * s->psi[m];
+                    double aph = ub > 0.0 ? ub * ph : ub * s->phi[m];
+                    dps += W[i] * (p->M_psi * (s->mupsi[m] - s->mupsi[n]) - aps);
+                    dph += W[i] * (p->M_phi * (s->muphi[m] - s->muphi[n]) - aph);
+                }
+                s->psin[n] = ps + 6.0 * dps;
+                double pn = ph + 6.0 * dph - p->k_d * (ph - phi0_of(s, ps));
+                /* Janus production (Eq. activity) at fluid nodes next to the
+                 * surface whose offset from the centre has m.(x - X) <= 0 */
+                for (int k = 0; k < s->np; ++k) {
+                    if (!adj[k]) continue;
+                    const ref_part* P = &s->part[k];
+                    double r[3];
+                    node_offset(s, P, x, y, z, r);
+                    double side = P->m[0] * r[0] + P->m[1] * r[1] + P->m[2] * r[2];
+                    if (side <= 0.0) pn += P->alpha;
+                }
+                s->phin[n] = pn;
+            }
+    double* t = s->psi;
+    s->psi = s->psin;
+    s->psin = t;
+    t = s->phi;
+    s->phi = s->phin;
+    s->phin = t;
+}
+
+/* ------------------------------------------------------------------ */
+/* S5 + S6: particle velocity update and motion                        */
+/* ------------------------------------------------------------------ */
+
+/* Gaussian elimination with partial pivoting on a 6x6 system. */
+static int solve6(double A[6][6], double b[6], double x[6])
+{
+    int perm[6] = {0, 1, 2, 3, 4, 5};
+    for (int c = 0; c < 6; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 6; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (A[piv][c] == 0.0) return -1;
+        if (piv != c) {
+            for (int k = 0; k < 6; ++k) {
+                double t = A[c][k];
+                A[c][k] = A[piv][k];
+                A[piv][k] = t;
+            }
+            double t = b[c];
+            b[c] = b[piv];
+            b[piv] = t;
+            int ti = perm[c];
+            perm[c] = perm[piv];
+            perm[piv] = ti;
+        }
+        for (int r = c + 1; r < 6; ++r) {
+            double l = A[r][c] / A[c][c];
+            for (int k = c; k < 6; ++k) A[r][k] -= l * A[c][k];
+            b[r] -= l * b[c];
+        }
+    }
+    for (int r = 5; r >= 0; --r) {
+        double acc = b[r];
+        for (int k = r + 1; k < 6; ++k) acc -= A[r][k] * x[k];
+        x[r] = acc / A[r][r];
+    }
+    return 0;
+}
+
+static void step_particles(ref_sim* s)
+{
+    const int L[3] = {s->p.nx, s->p.ny, s->p.nz};
+    for (int k = 0; k < s->np; ++k) {
+        ref_part* P = &s->part[k];
+        double F0[6];
+        for (int a = 0; a < 3; ++a) {
+            F0[a] = P->F0[a] + P->imp_f[a] + P->ext_f[a];
+            F0[3 + a] = P->T0[a] + P->imp_t[a] + P->ext_t[a];
+        }
+        double V[6] = {P->U[0], P->U[1], P->U[2], P->Om[0], P->Om[1], P->Om[2]};
+        if (!P->fixed) {
+            /* (Mdiag + zeta) V' = Mdiag V + F0 */
+            double Mm[6] = {P->M, P->M, P->M, P->I, P->I, P->I};
+            double A[6][6], b[6], Vn[6];
+            for (int a = 0; a < 6; ++a) {
+                for (int c = 0; c < 6; ++c) A[a][c] = P->zeta[a][c];
+                A[a][a] += Mm[a];
+                b[a] = Mm[a] * V[a] + F0[a];
+            }
+            if (solve6(A, b, Vn) != 0) s->err = -3;
+            for (int a = 0; a < 6; ++a) V[a] = Vn[a];
+        }
+        for (int a = 0; a < 6; ++a) {
+            double zv = 0.0;
+            for (int c = 0; c < 6; ++c) zv += P->zeta[a][c] * V[c];
+            if (a < 3)
+                P->force[a] = F0[a] - zv;
+            else
+                P->torque[a - 3] = F0[a] - zv;
+        }
+        for (int a = 0; a < 3; ++a) {
+            P->U[a] = V[a];
+            P->Om[a] = V[3 + a];
+            P->imp_f[a] = P->imp_t[a] = 0.0;
+        }
+        /* translate, wrapping periodic axes into [0, L) */
+        for (int a = 0; a < 3; ++a) {
+            double X = P->X[a] + P->U[a];
+            if (s->p.periodic[a]) {
+                if (X >= L[a])
+                    X -= L[a];
+                else if (X < 0.0)
+                    X += L[a];
+            } else if (X - P->R < 1.0 || X + P->R > L[a] - 2.0) {
+                s->err = -4;
+            }
+            P->X[a] = X;
+        }
+        /* rotate m by the angle |Omega| about Omega (Rodrigues), renormalise */
+        double w = sqrt(P->Om[0] * P->Om[0] + P->Om[1] * P->Om[1] + P->Om[2] * P->Om[2]);
+        if (w > 0.0) {
+            double k3[3] = {P->Om[0] / w, P->Om[1] / w, P->Om[2] / w};
+            double c = cos(w), sn = sin(w);
+            double* m = P->m;
+            double kxm[3] = {k3[1] * m[2] - k3[2] * m[1], k3[2] * m[0] - k3[0] * m[2],
+                             k3[0] * m[1] - k3[1] * m[0]};
+            double km = k3[0] * m[0] + k3[1] * m[1] + k3[2] * m[2];
+            double mn[3];
+            for (int a = 0; a < 3; ++a) mn[a] = m[a] * c + kxm[a] * sn + k3[a] * km * (1.0 - c);
+            double nn = sqrt(mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]);
+            for (int a = 0; a < 3; ++a) m[a] = mn[a] / nn;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* S7: covering and uncovering                                          */
+/* ------------------------------------------------------------------ */
+
+static void step_cover(ref_sim* s)
+{
+    const ref_params* p = &s->p;
+    const long N = s->N;
+    if (s->np == 0) return;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) s->maskn[nidx(s, x, y, z)] = owner(s, x, y, z);
+    double dpsi = 0.0, dphi = 0.0;
+    long dfl = 0;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long n = nidx(s, x, y, z);
+                unsigned char o = s->mask[n], q = s->maskn[n];
+                if (o == q) continue;
+                if (o == 0) {
+                    /* newly covered: the particle takes the node's momentum,
+                     * the node's psi and phi are removed */
+                    ref_part* P = &s->part[q - 1];
+                    double rho = 0.0;
+                    for (int i = 0; i < 19; ++i) rho += s->f[i * N + n];
+                    double j[3] = {rho * s->u[n], rho * s->u[N + n], rho * s->u[2 * N + n]};
+                    double r[3];
+                    node_offset(s, P, x, y, z, r);
+                    for (int a = 0; a < 3; ++a) P->imp_f[a] += j[a];
+                    P->imp_t[0] += r[1] * j[2] - r[2] * j[1];
+                    P->imp_t[1] += r[2] * j[0] - r[0] * j[2];
+                    P->imp_t[2] += r[0] * j[1] - r[1] * j[0];
+                    dpsi += s->psi[n];
+                    dphi += s->phi[n];
+                    s->psi[n] = s->phi[n] = 0.0;
+                    for (int i = 0; i < 19; ++i) s->f[i * N + n] = 0.0;
+                    s->u[n] = s->u[N + n] = s->u[2 * N + n] = 0.0;
+                    --dfl;
+                } else if (q == 0) {
+                    /* newly uncovered: equilibrium at the boundary velocity with
+                     * the mean density of the neighbours that are fluid before
+                     * and after; psi, phi = neighbour means */
+                    ref_part* P = &s->part[o - 1];
+                    double rb = 0.0, pb = 0.0, hb = 0.0;
+                    int cnt = 0;
+                    for (int i = 1; i < 19; ++i) {
+                        long m = nbr(s, x, y, z, CX[i], CY[i], CZ[i]);
+                        if (m < 0 || s->mask[m] || s->maskn[m]) continue;
+                        double rm = 0.0;
+                        for (int k = 0; k < 19; ++k) rm += s->f[k * N + m];
+                        rb += rm;
+                        pb += s->psi[m];
+                        hb += s->phi[m];
+                        ++cnt;
+                    }
+                    if (cnt == 0) {
+                        s->err = -4;
+                        rb = p->rho0;
+                        pb = hb = 0.0;
+                    } else {
+                        rb /= cnt;
+                        pb /= cnt;
+                        hb /= cnt;
+                    }
+                    double r[3], ub[3];
+                    node_offset(s, P, x, y, z, r);
+                    ub[0] = P->U[0] + (P->Om[1] * r[2] - P->Om[2] * r[1]);
+                    ub[1] = P->U[1] + (P->Om[2] * r[0] - P->Om[0] * r[2]);
+                    ub[2] = P->U[2] + (P->Om[0] * r[1] - P->Om[1] * r[0]);
+                    for (int i = 0; i < 19; ++i) s->f[i * N + n] = feq(i, rb, ub);
+                    for (int a = 0; a < 3; ++a) s->u[a * N + n] = ub[a];
+                    double j[3] = {rb * ub[0], rb * ub[1], rb * ub[2]};
+                    for (int a = 0; a < 3; ++a) P->imp_f[a] -= j[a];
+                    P->imp_t[0] -= r[1] * j[2] - r[2] * j[1];
+                    P->imp_t[1] -= r[2] * j[0] - r[0] * j[2];
+                    P->imp_t[2] -= r[0] * j[1] - r[1] * j[0];
+                    s->psi[n] = pb;
+                    s->phi[n] = hb;
+                    dpsi -= pb;
+                    dphi -= hb;
+                    ++dfl;
+                } else {
+                    s->err = -4; /* node passed directly between two particles */
+                }
+            }
+    memcpy(s->mask, s->maskn, (size_t)N);
+    s->nfluid += dfl;
+    if (dfl == 0 && dpsi == 0.0 && dphi == 0.0) return;
+    /* restore the totals of psi and phi: spread the removed minus the added
+     * amount uniformly over every fluid node */
+    double cps = dpsi / (double)s->nfluid, cph = dphi / (double)s->nfluid;
+    for (long n = 0; n < N; ++n) {
+        if (s->mask[n]) continue;
+        s->psi[n] += cps;
+        s->phi[n] += cph;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* public entry points                                                 */
+/* ------------------------------------------------------------------ */
+
+ref_sim* ref_create(const ref_params* p)
+{
+    if (p->nx <= 0 || p->ny <= 0 || p->nz <= 0 || p->tau <= 0.5 || p->rho0 <= 0.0) return NULL;
+    ref_sim* s = (ref_sim*)calloc(1, sizeof(ref_sim));
+    if (!s) return NULL;
+    s->p = *p;
+    s->N = (long)p->nx * p->ny * p->nz;
+    long N = s->N;
+    s->f = (double*)calloc((size_t)(19 * N), sizeof(double));
+    s->fn = (double*)calloc((size_t)(19 * N), sizeof(double));
+    s->psi = (double*)calloc((size_t)N, sizeof(double));
+    s->phi = (double*)calloc((size_t)N, sizeof(double));
+    s->psin = (double*)calloc((size_t)N, sizeof(double));
+    s->phin = (double*)calloc((size_t)N, sizeof(double));
+    s->mupsi = (double*)calloc((size_t)N, sizeof(double));
+    s->muphi = (double*)calloc((size_t)N, sizeof(double));
+    s->u = (double*)calloc((size_t)(3 * N), sizeof(double));
+    s->mask = (unsigned char*)calloc((size_t)N, 1);
+    s->maskn = (unsigned char*)calloc((size_t)N, 1);
+    if (!s->f || !s->fn || !s->psi || !s->phi || !s->psin || !s->phin || !s->mupsi || !s->muphi ||
+        !s->u || !s->mask || !s->maskn) {
+        ref_destroy(s);
+        return NULL;
+    }
+    s->nfluid = N;
+    double u0[3] = {0, 0, 0};
+    for (int i = 0; i < 19; ++i)
+        for (long n = 0; n < N; ++n) s->f[i * N + n] = feq(i, p->rho0, u0);
+    return s;
+}
+
+void ref_destroy(ref_sim* s)
+{
+    if (!s) return;
+    free(s->f);
+    free(s->fn);
+    free(s->psi);
+    free(s->phi);
+    free(s->psin);
+    free(s->phin);
+    free(s->mupsi);
+    free(s->muphi);
+    free(s->u);
+    free(s->mask);
+    free(s->maskn);
+    free(s);
+}
+
+int ref_set_fields(ref_sim* s, const double* rho, const double* u, const double* psi, const double* phi)
+{
+    const long N = s->N;
+    for (long n = 0; n < N; ++n) {
+        if (psi) s->psi[n] = s->mask[n] ? 0.0 : psi[n];
+        if (phi) s->phi[n] = s->mask[n] ? 0.0 : phi[n];
+        if (u)
+            for (int a = 0; a < 3; ++a) s->u[a * N + n] = s->mask[n] ? 0.0 : u[a * N + n];
+    }
+    for (long n = 0; n < N; ++n) {
+        double r = 0.0;
+        for (int i = 0; i < 19; ++i) r += s->f[i * N + n];
+        double rr = rho ? rho[n] : r;
+        double uu[3] = {s->u[n], s->u[N + n], s->u[2 * N + n]};
+        for (int i = 0; i < 19; ++i) s->f[i * N + n] = s->mask[n] ? 0.0 : feq(i, rr, uu);
+    }
+    return 0;
+}
+
+int ref_add_particle(ref_sim* s, const ref_particle_desc* d)
+{
+    if (s->np >= REF_MAXP || d->R <= 0.0) return -1;
+    if (d->H != 0.0 && s->p.kappa <= 0.0) return -1;
+    ref_part* P = &s->part[s->np];
+    memset(P, 0, sizeof(*P));
+    double mn = sqrt(d->m_hat[0] * d->m_hat[0] + d->m_hat[1] * d->m_hat[1] + d->m_hat[2] * d->m_hat[2]);
+    if (!(mn > 0.0)) return -1;
+    for (int a = 0; a < 3; ++a) {
+        P->X[a] = d->pos[a];
+        P->m[a] = d->m_hat[a] / mn;
+        P->U[a] = d->vel[a];
+        P->Om[a] = d->omega[a];
+        P->ext_f[a] = d->ext_force[a];
+        P->ext_t[a] = d->ext_torque[a];
+    }
+    P->R = d->R;
+    P->R2 = d->R * d->R;
+    double rp = d->rho_p > 0.0 ? d->rho_p : 1.0;
+    P->M = rp * (4.0 / 3.0) * M_PI * d->R * d->R * d->R;
+    P->I = 0.4 * P->M * d->R * d->R;
+    P->alpha = d->alpha;
+    P->mu_p = d->mu_plus;
+    P->mu_m = d->mu_minus;
+    P->H = d->H;
+    P->fixed = d->fixed;
+    s->np++;
+    const long N = s->N;
+    for (int z = 0; z < s->p.nz; ++z)
+        for (int y = 0; y < s->p.ny; ++y)
+            for (int x = 0; x < s->p.nx; ++x) {
+                long n = nidx(s, x, y, z);
+                if (s->mask[n]) continue;
+                if (inside(s, P, x, y, z)) {
+                    s->mask[n] = (unsigned char)s->np;
+                    s->psi[n] = s->phi[n] = 0.0;
+                    for (int i = 0; i < 19; ++i) s->f[i * N + n] = 0.0;
+                    s->u[n] = s->u[N + n] = s->u[2 * N + n] = 0.0;
+                    s->nfluid--;
+                }
+            }
+    return s->np - 1;
+}
+
+int ref_step(ref_sim* s, int nsteps)
+{
+    for (int t = 0; t < nsteps; ++t) {
+        step_mu(s);
+        step_collide(s);
+        step_scalars(s);
+        step_particles(s);
+        step_cover(s);
+    }
+    return s->err;
+}
+
+int ref_read_fields(const ref_sim* s, double* rho, double* u, double* psi, double* phi)
+{
+    const long N = s->N;
+    for (long n = 0; n < N; ++n) {
+        if (rho) {
+            double r = 0.0;
+            for (int i = 0; i < 19; ++i) r += s->f[i * N + n];
+            rho[n] = r;
+        }
+        if (psi) psi[n] = s->psi[n];
+        if (phi) phi[n] = s->phi[n];
+    }
+    if (u) memcpy(u, s->u, (size_t)(3 * N) * sizeof(double));
+    return 0;
+}
+
+int ref_read_mu(const ref_sim* s, double* mu_psi, double* mu_phi)
+{
+    if (mu_psi) memcpy(mu_psi, s->mupsi, (size_t)s->N * sizeof(double));
+    if (mu_phi) memcpy(mu_phi, s->muphi, (size_t)s->N * sizeof(double));
+    return 0;
+}
+
+int ref_read_populations(const ref_sim* s, double* f)
+{
+    memcpy(f, s->f, (size_t)(19 * s->N) * sizeof(double));
+    return 0;
+}
+
+int ref_read_mask(const ref_sim* s, unsigned char* mask)
+{
+    memcpy(mask, s->mask, (size_t)s->N);
+    return 0;
+}
+
+int ref_read_particles(const ref_sim* s, ref_particle_state* out, int cap)
+{
+    int n = s->np < cap ? s->np : cap;
+    for (int k = 0; k < n; ++k) {
+        const ref_part* P = &s->part[k];
+        for (int a = 0; a < 3; ++a) {
+            out[k].pos[a] = P->X[a];
+            out[k].vel[a] = P->U[a];
+            out[k].omega[a] = P->Om[a];
+            out[k].m_hat[a] = P->m[a];
+            out[k].force[a] = P->force[a];
+            out[k].torque[a] = P->torque[a];
+        }
+    }
+    return s->np;
+}
+
+int ref_conservation(const ref_sim* s, double sums[3])
+{
+    const long N = s->N;
+    double r = 0.0, a = 0.0, b = 0.0;
+    for (long n = 0; n < N; ++n) {
+        if (s->mask[n]) continue;
+        for (int i = 0; i < 19; ++i) r += s->f[i * N + n];
+        a += s->psi[n];
+        b += s->phi[n];
+    }
+    sums[0] = r;
+    sums[1] = a;
+    sums[2] = b;
+    return 0;
+}
+
+int ref_error(const ref_sim* s) { return s->err; }
+long ref_fluid_count(const ref_sim* s) { return s->nfluid; }
+
+/* cos(theta_c) = [(1+h)^{3/2} - (1-h)^{3/2}] / 2 (Sec. Particles, wetting);
+ * the right side increases monotonically on [-1, 1], so bisection finds h. */
+double ref_wetting_h(double theta_deg)
+{
+    double target = cos(theta_deg * M_PI / 180.0);
+    double lo = -1.0, hi = 1.0;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        double v = 0.5 * (pow(1.0 + mid, 1.5) - pow(1.0 - mid, 1.5));
+        if (v < target)
+            lo = mid;
+        else
+            hi = mid;
+        if (hi - lo < 1e-16) break;
+    }
+    return 0.5 * (lo + hi);
+}
