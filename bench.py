@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Benchmark of the lattice step: MLUPS and HBM-roofline fraction on GB300.
+
+A step is one full pass of the coupled update (chemical potentials, collide-
+stream with particle bounce-back, psi/phi transport, particle update,
+covering) over the 128^3 single-particle interface workload (one Janus sphere
+R=8 straddling a flat interface, contact angle 60 degrees, solubility ratio 2,
+phoretic mobility 0.1), FP32 arithmetic and storage.  Inputs are synthetic
+and seeded; the state (0.4 GB) is larger than L2, so no L2 flush is needed.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle (the
+reference implementation written from the paper) on the host cores instead.
+Multi-GPU runs (torchrun) are independent replicas: the boxes do not share
+data, so there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# algorithmic bytes per node and step (populations read+write, psi/phi
+# read+write): FP32 19*4*2 + 2*4*2
+ALG_BYTES_STEP = {"fp64": 336, "fp32": 168, "fp16": 92, "bf16": 92}
+# algorithmic bytes per node of the collide-stream kernel: populations
+# read+write and psi, phi read
+ALG_BYTES_COLLIDE = {"fp64": 19 * 8 * 2 + 16, "fp32": 19 * 4 * 2 + 8, "fp16": 19 * 2 * 2 + 8,
+                     "bf16": 19 * 2 * 2 + 8}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32", "bf16": "bf16-storage/f32"}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
+    ap.add_argument("--edge", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(edge):
+    from paper_2202_01631_gb300 import workloads as W
+    return W.interface(theta_c_deg=60.0, solubility_ratio=2.0, mobility=0.1, seed=0, edge=edge)
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    group = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        group = dist
+    return world, rank, local, group
+
+
+def barrier(group):
+    if group is not None:
+        import torch
+        if torch.cuda.is_available():
+            group.barrier(device_ids=[torch.cuda.current_device()])
+        else:
+            group.barrier()
+
+
+def max_over_ranks(value, group):
+    """Largest value over ranks (the job time is the slowest rank's)."""
+    if group is None:
+        return value
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    group.all_reduce(t, op=group.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_record(kernel, precision, edge):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, valid
+    only while the kernel sources are unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            recs = json.load(f)
+    except (OSError, ValueError):
+        return None
+    src = source_hash()
+    for r in recs:
+        if (r.get("kernel") == kernel and r.get("precision") == precision and r.get("edge") == edge
+                and r.get("source_sha") == src):
+            return float(r["bytes_per_launch"])
+    return None
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2202_01631_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def build_box(wl, precision, stream):
+    from paper_2202_01631_gb300.lbdp import Box
+    box = Box(precision=precision, stream=stream, **wl.params)
+    box.set_fields(**wl.fields)
+    for p in wl.particles:
+        box.add_particle(**p)
+    return box
+
+
+def cpu_baseline(wl, budget_s=12.0):
+    """The FP64 oracle as it stands on the host, on a bounded number of steps
+    of the same workload."""
+    from oracle.lbref import Oracle
+    ref = Oracle(wl.params)
+    ref.set_fields(**wl.fields)
+    for p in wl.particles:
+        ref.add_particle(**p)
+    t0 = time.perf_counter()
+    ref.step(1)
+    t1 = time.perf_counter()
+    per = t1 - t0
+    k = max(1, min(20, int(budget_s / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    ref.step(k)
+    dt = time.perf_counter() - t0
+    return {"value": wl.nodes * k / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%d steps of the %d^3 workload (after 1 untimed step), FP64, 1 thread"
+                      % (k, wl.params["nx"])}
+
+
+def run_reference(args):
+    world, rank, local, group = dist_setup(args)
+    if rank != 0:
+        return 0
+    from oracle.lbref import Oracle
+    from paper_2202_01631_gb300 import workloads as W
+    wl_full = workload(args.edge)
+    # each step of this arm is one oracle step on a box scaled so that the
+    # whole run stays within about two minutes
+    t_node = 1.2e-6
+    budget = 120.0 / max(args.steps + args.warmup, 1)
+    edge = int(max(16, min(args.edge, round((budget / t_node) ** (1 / 3)))))
+    edge -= edge % 2
+    wl = W.interface(theta_c_deg=60.0, solubility_ratio=2.0, mobility=0.1, seed=0, edge=edge)
+    ref = Oracle(wl.params)
+    ref.set_fields(**wl.fields)
+    for p in wl.particles:
+        ref.add_particle(**p)
+    ref.step(args.warmup)
+    t0 = time.perf_counter()
+    ref.step(args.steps)
+    dt = time.perf_counter() - t0
+    mlups = wl.nodes * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / max(args.steps, 1) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl_full.name, "sample_edge": edge, "precision": "fp64",
+                   "particles": len(wl.particles)},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": "%d steps of the workload scaled to %d^3 (FP64 oracle, 1 thread)"
+                                   % (args.steps, edge)},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local, group = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    from paper_2202_01631_gb300 import build
+    build.build()
+    from paper_2202_01631_gb300 import lbdp
+
+    wl = workload(args.edge)
+    N = wl.nodes
+    stream = torch.cuda.Stream()
+    box = build_box(wl, args.precision, stream.cuda_stream)
+    box.step(args.warmup)
+    box.sync()
+
+    # ---- device-resident throughput -------------------------------------
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(group)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        box.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(group)
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ms, group)
+    box.sync()
+    launches = lbdp.lb_step_launches(box.h, args.steps)
+    value = N * args.steps * world / (ms * 1e-3) / 1e6
+
+    # ---- per-kernel split (separate pass, events around every kernel) ----
+    nprof = min(args.steps, 400)
+    split, _ = lbdp.lb_profile_step(box.h, nprof)
+    box.sync()
+    coll_ms = split["k_collide"] / nprof
+    peak, peak_kind = measured_peak()
+    coll_bytes = ALG_BYTES_COLLIDE[args.precision] * N
+    achieved = coll_bytes / (coll_ms * 1e-3) / 1e9
+    step_ms = ms / args.steps
+    step_gbs = ALG_BYTES_STEP[args.precision] * N / (step_ms * 1e-3) / 1e9
+
+    # ---- end to end through host buffers --------------------------------
+    host = {k: torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).pin_memory()
+            for k, v in wl.fields.items()}
+    outs = {k: torch.empty_like(v).pin_memory() for k, v in host.items()}
+    e2e_steps = args.steps
+    box2 = build_box(wl, args.precision, stream.cuda_stream)
+    box2.sync()
+    barrier(group)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbdp.lb_set_fields(box2.h, *[host[k].numpy() for k in ("rho", "u", "psi", "phi")])
+    box2.step(e2e_steps)
+    lbdp.lb_read_fields(box2.h, *[outs[k].numpy() for k in ("rho", "u", "psi", "phi")])
+    parts = box2.particles()
+    dt = time.perf_counter() - t0
+    dt = max_over_ranks(dt, group)
+    h2d = sum(v.numel() * 8 for v in host.values())
+    d2h = sum(v.numel() * 8 for v in outs.values()) + len(parts) * 18 * 8
+    e2e = {"value": N * e2e_steps * world / dt / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+           "job": "upload initial fields from pinned host memory, %d steps, read back fields "
+                  "and particles" % e2e_steps}
+    box2.close()
+
+    if rank != 0:
+        box.close()
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl)
+    traffic = traffic_record("k_collide", args.precision, args.edge)
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+        "config": {"workload": wl.name, "nodes": N, "precision": args.precision,
+                   "particles": len(wl.particles), "theta_c_deg": 60.0, "solubility_ratio": 2.0,
+                   "mobility": 0.1, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "state %.2f GB > L2 (129 MB); no flush" % (lbdp.lb_device_bytes(box.params) / 1e9)},
+        "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": traffic,
+                     "alg_bytes_per_launch": coll_bytes, "avg_launch_ms": coll_ms},
+        "step_roofline": {"alg_bytes_per_node": ALG_BYTES_STEP[args.precision], "achieved": step_gbs,
+                          "peak": peak, "unit": "GB/s", "frac": step_gbs / peak},
+        "kernel_ms_per_step": {k: v / nprof for k, v in split.items()},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    box.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,200 @@
+/*
+ * lbdp.h -- C ABI of the GB300 lattice Boltzmann library for self-diffusiophoretic
+ * particles near liquid-liquid interfaces (arXiv 2202.01631).
+ *
+ * One simulation box lives on one GPU.  A time step is the coupled update of
+ *   - the D3Q19 BGK solvent (Sec. "Computational model", nu = (tau - 1/2)/3),
+ *   - the water/oil order parameter psi and the solute phi through their
+ *     chemical potentials (Eqs. free_energy, chem_potentials,
+ *     diffusion_reaction), with Janus production on the catalytic cap
+ *     (Eq. activity) and the degradation sink k_d (phi - phi0(psi)),
+ *   - spheres coupled by bounce-back on links with momentum-exchange force and
+ *     torque, phoretic slip v_s = mu (1 - n n) . grad phi with Janus mobility
+ *     (Eq. MuJ), wetting through the surface field H (Eq. fe_wetting and the
+ *     contact-angle relation), and node covering/uncovering as they move
+ *     (Sec. "Particles").
+ *
+ * Conventions shared by every entry point
+ *   - Node index n = x + nx*(y + ny*z); scalar fields are [N] arrays, vectors
+ *     [3][N] (component-major), populations [19][N] in the D3Q19 order
+ *       0 rest; 1..6 +x,-x,+y,-y,+z,-z;
+ *       7..18 (+1,+1,0),(-1,-1,0),(+1,-1,0),(-1,+1,0),(+1,0,+1),(-1,0,-1),
+ *             (+1,0,-1),(-1,0,+1),(0,+1,+1),(0,-1,-1),(0,+1,-1),(0,-1,+1).
+ *   - Host data crossing the ABI is FP64 in every precision mode.  The
+ *     caller owns every host array; the library copies in and out and owns
+ *     all device memory of a handle.
+ *   - Nodes inside a particle read back as 0 in every field.
+ *   - Every call returns LB_OK (0) or a negative LB_ERR_* status; no C++
+ *     exception crosses the ABI.  A handle is not thread-safe.
+ *   - Work is queued on the handle's stream (lb_params.cuda_stream, or a
+ *     stream the library creates when it is NULL).  lb_step returns without
+ *     waiting; the read and conservation calls synchronise the stream.
+ *     Errors detected on the device (a particle leaving the allowed region,
+ *     two particles meeting) are reported by the next synchronising call.
+ */
+#ifndef LBDP_H
+#define LBDP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_handle lb_handle;
+
+/* Storage and arithmetic precision of a box.
+ *   LB_FP64        populations and fields FP64, FP64 arithmetic.
+ *   LB_FP32        populations stored FP32 as f_i - w_i rho0, FP32 arithmetic.
+ *   LB_FP16_SHIFT  populations stored FP16 as (f_i - w_i rho0)/w_i, FP32
+ *                  fields and arithmetic.
+ *   LB_BF16_SHIFT  as LB_FP16_SHIFT with BF16 storage.
+ * Particle state, force/torque sums and conservation sums are FP64 always. */
+enum {
+    LB_FP64 = 0,
+    LB_FP32 = 1,
+    LB_FP16_SHIFT = 2,
+    LB_BF16_SHIFT = 3
+};
+
+enum {
+    LB_OK = 0,
+    LB_ERR_PARAM = -1,     /* invalid argument or parameter set            */
+    LB_ERR_NOMEM = -2,     /* device allocation failed                     */
+    LB_ERR_NONFINITE = -3, /* a conserved total became NaN or Inf          */
+    LB_ERR_OVERLAP = -4,   /* particles met, or a particle reached a wall  */
+    LB_ERR_CUDA = -5,      /* a CUDA call failed                           */
+    LB_ERR_TIMEOUT = -6,   /* reserved: a bounded device wait expired      */
+    LB_ERR_STATE = -7      /* call not valid in the handle's current state */
+};
+
+/* Box and model parameters (Sec. "Numerical details" gives the paper's
+ * values: tau = 1 (nu = 1/6), rho0 = 1, A = C = 0.0625, kappa = 0.04). */
+typedef struct {
+    int nx, ny, nz;         /* lattice size, unit spacing                   */
+    int periodic[3];        /* 1 periodic; 0 halfway bounce-back walls at
+                               -1/2 and n-1/2 with neutral wetting          */
+    int precision;          /* LB_FP64 ... LB_BF16_SHIFT                    */
+    int thermo_force;       /* 1 (default model): fluid force
+                               -psi grad mu_psi - phi grad mu_phi;
+                               0: psi and phi are passive scalars           */
+    double tau, rho0;       /* BGK relaxation time (> 1/2), reference density */
+    double body_force[3];   /* uniform force density g on the fluid         */
+    double A, kappa, M_psi; /* Landau double well A psi^4/4 - A psi^2/2,
+                               gradient coefficient, psi mobility           */
+    double C, M_phi;        /* solute stiffness and mobility (D = C M_phi)  */
+    double E, phi_b;        /* solubility: phi0(psi) = phi_b + E tanh psi   */
+    double k_d;             /* degradation rate of the sink                 */
+    void* cuda_stream;      /* cudaStream_t to queue work on, or NULL       */
+} lb_params;
+
+/* One sphere (Sec. "Particles").  pos must keep the sphere one node clear of
+ * any wall and of other spheres.  m_hat need not be normalised.
+ * theta_c_deg sets the contact angle through
+ *   cos(theta_c) = [(1+h)^{3/2} - (1-h)^{3/2}]/2,  H = h sqrt(kappa A);
+ * when theta_c_deg is NaN, H is taken as given.  The cap m.n <= 0 produces
+ * solute at rate alpha per adjacent fluid node and per step, with mobility
+ * mu_minus there and mu_plus on the other hemisphere (Eqs. activity, MuJ).
+ * rho_p <= 0 means 1.  fixed != 0 holds vel/omega constant (the sphere still
+ * moves at vel and turns at omega; the force it feels is reported).
+ * ext_force/ext_torque are constant external loads. */
+typedef struct {
+    double pos[3], m_hat[3];
+    double R, rho_p, alpha, mu_plus, mu_minus;
+    double theta_c_deg, H;
+    double vel[3], omega[3];
+    double ext_force[3], ext_torque[3];
+    int fixed;
+} lb_particle_desc;
+
+/* State after the last step; force/torque are the totals the particle felt
+ * in that step (hydrodynamic, covering impulses and external). */
+typedef struct {
+    double pos[3], vel[3], omega[3], m_hat[3], force[3], torque[3];
+} lb_particle_state;
+
+/* Create a box: validates params (LB_ERR_PARAM), allocates the device state
+ * (LB_ERR_NOMEM), and sets the fluid at rest with rho = rho0, psi = phi = 0.
+ * On success *out receives the handle; on failure *out is NULL. */
+int lb_create(const lb_params* params, lb_handle** out);
+
+/* Release every device allocation of the handle.  NULL is ignored. */
+void lb_destroy(lb_handle* h);
+
+/* Set the fields from host arrays rho [N], u [3][N], psi [N], phi [N] (any may
+ * be NULL to keep the current field) and reset the populations to the
+ * second-order equilibrium of (rho, u) (Sec. "Numerical details": the system
+ * starts from equilibrium).  Values at nodes inside particles are ignored. */
+int lb_set_fields(lb_handle* h, const double* rho, const double* u,
+                  const double* psi, const double* phi);
+
+/* Add a sphere (Sec. "Particles").  Nodes whose centre lies strictly inside
+ * the sphere become solid and their fields are dropped.  Returns
+ * LB_ERR_PARAM for a bad descriptor, LB_ERR_OVERLAP if it meets a wall or
+ * another sphere.  *id_out (may be NULL) receives the particle index. */
+int lb_add_particle(lb_handle* h, const lb_particle_desc* desc, int* id_out);
+
+/* Queue nsteps time steps (nsteps >= 0) on the handle's stream and return
+ * without waiting.  Each step: chemical potentials (Eq. chem_potentials);
+ * force, streaming with bounce-back and BGK collision; psi/phi transport
+ * (Eq. diffusion_reaction); particle update; covering/uncovering. */
+int lb_step(lb_handle* h, int nsteps);
+
+/* Run nsteps steps like lb_step, with a CUDA event recorded on the handle's
+ * stream around every kernel, wait, and add each kernel class's time in
+ * milliseconds to ms[0..4]: chemical potentials and pressure tensor,
+ * particle links and velocity update, collide-stream, psi/phi transport,
+ * covering.  *launches (may be NULL)
+ * receives the number of kernels launched.  The events add a little host
+ * overhead, so time throughput with lb_step; this call is for the split. */
+int lb_profile_step(lb_handle* h, int nsteps, double* ms, int* launches);
+
+/* Number of kernels lb_step(h, nsteps) launches (for launch accounting). */
+int lb_step_launches(const lb_handle* h, int nsteps);
+
+/* Wait for queued work and report device-side errors. */
+int lb_sync(lb_handle* h);
+
+/* Copy the fields to host arrays (any may be NULL): rho = sum_i f_i,
+ * u = velocity of the last collision (with the half-force term), psi, phi.
+ * Synchronises. */
+int lb_read_fields(lb_handle* h, double* rho, double* u, double* psi, double* phi);
+
+/* Copy the chemical potentials mu_psi, mu_phi [N] computed in the last step
+ * (Eq. chem_potentials).  Synchronises. */
+int lb_read_mu(lb_handle* h, double* mu_psi, double* mu_phi);
+
+/* Copy the post-collision populations f_i [19][N] (FP64).  Synchronises. */
+int lb_read_populations(lb_handle* h, double* f);
+
+/* Copy the solid mask [N]: 0 fluid, k+1 inside particle k.  Synchronises. */
+int lb_read_mask(lb_handle* h, unsigned char* mask);
+
+/* Copy up to cap particle states; *n_out (may be NULL) gets the count. */
+int lb_read_particles(lb_handle* h, lb_particle_state* out, int cap, int* n_out);
+
+/* FP64 totals over fluid nodes: sums[0] = sum rho, sums[1] = sum psi,
+ * sums[2] = sum phi, reduced on the device in a fixed order.  Returns
+ * LB_ERR_NONFINITE if any is NaN or Inf.  Synchronises. */
+int lb_conservation(lb_handle* h, double sums[3]);
+
+/* Device bytes lb_create would allocate for params (for admission control). */
+int lb_device_bytes(const lb_params* params, size_t* bytes);
+
+/* h = H / sqrt(kappa A) for a contact angle in degrees, by bisection of
+ * cos(theta_c) = [(1+h)^{3/2} - (1-h)^{3/2}]/2 on [-1, 1]
+ * (Sec. "Particles", contact-angle relation). */
+double lb_wetting_h(double theta_c_deg);
+
+/* Solubility parameter E for a ratio r = phi0(psi=+1)/phi0(psi=-1) of the
+ * shifted minimum phi0 = phi_b + E tanh(psi) (Eq. free_energy):
+ * E = phi_b (r - 1) / ((r + 1) tanh 1). */
+double lb_solubility_E(double ratio, double phi_b);
+
+/* Static message for a status code. */
+const char* lb_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBDP_H */

@@ -6,17 +6,20 @@
  *
  * One step, in order (the paper gives the model as PDEs; the discrete reading
  * of each step is stated where it is used):
- *   S1  chemical potentials mu_psi, mu_phi            (Eq. chem_potentials)
- *   S2  thermodynamic force on the fluid              (reading: -psi grad mu_psi
- *                                                      - phi grad mu_phi + g)
+ *   S1  chemical potentials mu_psi, mu_phi (Eq. chem_potentials) and the
+ *       chemical pressure tensor P of the free energy (Eq. free_energy)
+ *   S5  momentum exchange sums per particle (bounce-back and chemical stress)
+ *   S6a implicit particle velocity update
+ *   S2  force on the fluid, g - div P (reading of the coupling, whose
+ *       continuum value is -psi grad mu_psi - phi grad mu_phi + g)
  *   S3  D3Q19 pull streaming, halfway bounce-back on walls, moving bounce-back
  *       on particle links with phoretic slip          (Sec. Particles, Eq. for v_s)
  *       then BGK collision with Guo forcing
  *   S4  explicit conservative update of psi and phi   (Eq. diffusion_reaction)
  *       with Janus production (Eq. activity) and the sink k_d (phi - phi0)
- *   S5  momentum exchange sums per particle
- *   S6  implicit particle velocity update, move, rotate
- *   S7  covering / uncovering of nodes swept by moving particles
+ *   S6b particle translation and rotation
+ *   S7  covering / uncovering of nodes swept by moving particles, and the
+ *       uniform correction that keeps the psi and phi totals exact
  *
  * Built with -ffp-contract=off so that no multiply-add is fused; the
  * geometric decisions (solid or fluid, active or inactive) are then taken with
@@ -60,11 +63,13 @@ struct ref_sim {
     double* f;    /* [19][N] post-collision populations */
     double* fn;   /* work buffer */
     double *psi, *phi, *mupsi, *muphi, *u, *psin, *phin;
+    double* pt;   /* [6][N] chemical pressure tensor xx yy zz xy xz yz */
     unsigned char *mask, *maskn;
     int np;
     ref_part part[REF_MAXP];
     long nfluid;
     int err;
+    double wall_psi, wall_phi; /* psi, phi carried into the particles this step */
 };
 
 /* ------------------------------------------------------------------ */
@@ -194,12 +199,14 @@ static void link_velocity(const ref_sim* s, const ref_part* P, int x, int y, int
 }
 
 /* ------------------------------------------------------------------ */
-/* S1: chemical potentials (Eq. chem_potentials)                       */
+/* S1: chemical potentials (Eq. chem_potentials) and the chemical      */
+/* pressure tensor of the free energy (Eq. free_energy)                */
 /* ------------------------------------------------------------------ */
 
 static void step_mu(ref_sim* s)
 {
     const ref_params* p = &s->p;
+    const long N = s->N;
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
@@ -207,13 +214,15 @@ static void step_mu(ref_sim* s)
                 if (s->mask[n]) {
                     s->mupsi[n] = 0.0;
                     s->muphi[n] = 0.0;
+                    for (int k = 0; k < 6; ++k) s->pt[k * N + n] = 0.0;
                     continue;
                 }
                 double ps = s->psi[n], ph = s->phi[n];
-                /* isotropic Laplacian 6 sum_i w_i (psi(x+c_i) - psi(x)); a
-                 * solid neighbour carries the wetting ghost
-                 * psi(x) + (H/kappa) c_i.n_hat, a wall neighbour psi(x). */
-                double lap = 0.0;
+                /* isotropic Laplacian 6 sum_i w_i (psi(x+c_i) - psi(x)) and
+                 * gradient 3 sum_i w_i c_i psi(x+c_i); a solid neighbour
+                 * carries the wetting ghost psi(x) + (H/kappa) c_i.n_hat, a
+                 * wall neighbour psi(x). */
+                double lap = 0.0, g[3] = {0.0, 0.0, 0.0};
                 for (int i = 1; i < 19; ++i) {
                     long m = nbr(s, x, y, z, CX[i], CY[i], CZ[i]);
                     double v;
@@ -234,13 +243,169 @@ static void step_mu(ref_sim* s)
                         v = s->psi[m];
                     }
                     lap += W[i] * (v - ps);
+                    g[0] += W[i] * CX[i] * v;
+                    g[1] += W[i] * CY[i] * v;
+                    g[2] += W[i] * CZ[i] * v;
                 }
                 lap *= 6.0;
+                g[0] *= 3.0;
+                g[1] *= 3.0;
+                g[2] *= 3.0;
                 double dphi = ph - phi0_of(s, ps);
                 double ch = cosh(ps);
-                s->muphi[n] = p->C * dphi;
-                s->mupsi[n] = p->A * (ps * ps * ps - ps) - p->kappa * lap - p->C * p->E * dphi / (ch * ch);
+                double mph = p->C * dphi;
+                double mps = p->A * (ps * ps * ps - ps) - p->kappa * lap - p->C * p->E * dphi / (ch * ch);
+                s->muphi[n] = mph;
+                s->mupsi[n] = mps;
+                /* P = [psi mu_psi + phi mu_phi - f - kappa |grad psi|^2 / 2] I
+                 *     + kappa grad psi grad psi,
+                 * f = A psi^4/4 - A psi^2/2 + C (phi - phi0)^2 / 2; its
+                 * divergence is psi grad mu_psi + phi grad mu_phi. */
+                double f = 0.25 * p->A * ps * ps * ps * ps - 0.5 * p->A * ps * ps + 0.5 * p->C * dphi * dphi;
+                double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+                double piso = ps * mps + ph * mph - f - 0.5 * p->kappa * g2;
+                s->pt[0 * N + n] = piso + p->kappa * g[0] * g[0];
+                s->pt[1 * N + n] = piso + p->kappa * g[1] * g[1];
+                s->pt[2 * N + n] = piso + p->kappa * g[2] * g[2];
+                s->pt[3 * N + n] = p->kappa * g[0] * g[1];
+                s->pt[4 * N + n] = p->kappa * g[0] * g[2];
+                s->pt[5 * N + n] = p->kappa * g[1] * g[2];
             }
+}
+
+/* P(x) . c for the tensor stored at node n (components xx yy zz xy xz yz). */
+static void pt_dot(const ref_sim* s, long n, const double c[3], double out[3])
+{
+    const long N = s->N;
+    double xx = s->pt[n], yy = s->pt[N + n], zz = s->pt[2 * N + n];
+    double xy = s->pt[3 * N + n], xz = s->pt[4 * N + n], yz = s->pt[5 * N + n];
+    out[0] = xx * c[0] + xy * c[1] + xz * c[2];
+    out[1] = xy * c[0] + yy * c[1] + yz * c[2];
+    out[2] = xz * c[0] + yz * c[1] + zz * c[2];
+}
+
+/* ------------------------------------------------------------------ */
+/* S5 + S6a: momentum exchange sums and the implicit velocity update   */
+/* ------------------------------------------------------------------ */
+
+/* Gaussian elimination with partial pivoting on a 6x6 system. */
+static int solve6(double A[6][6], double b[6], double x[6])
+{
+    for (int c = 0; c < 6; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 6; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (A[piv][c] == 0.0) return -1;
+        if (piv != c) {
+            for (int k = 0; k < 6; ++k) {
+                double t = A[c][k];
+                A[c][k] = A[piv][k];
+                A[piv][k] = t;
+            }
+            double t = b[c];
+            b[c] = b[piv];
+            b[piv] = t;
+        }
+        for (int r = c + 1; r < 6; ++r) {
+            double l = A[r][c] / A[c][c];
+            for (int k = c; k < 6; ++k) A[r][k] -= l * A[c][k];
+            b[r] -= l * b[c];
+        }
+    }
+    for (int r = 5; r >= 0; --r) {
+        double acc = b[r];
+        for (int k = r + 1; k < 6; ++k) acc -= A[r][k] * x[k];
+        x[r] = acc / A[r][r];
+    }
+    return 0;
+}
+
+/* Each boundary link x -> x+c_i (x fluid, x+c_i inside particle P) hands the
+ * particle the bounce-back momentum c_i (f*_i + f_ibar) with
+ * f_ibar = f*_i - 6 w_i rho0 c_i.u_b (Ladd), u_b = U + Omega x r_b + v_s, and
+ * the chemical stress flux 6 w_i P(x).c_i.  The part linear in (U, Omega) is
+ * collected in the 6x6 drag matrix zeta, the rest in (F0, T0), and
+ *   (Mdiag + zeta) V(t+1) = Mdiag V(t) + [F0; T0]
+ * is solved for the new velocity (Nguyen and Ladd's implicit update, cited in
+ * Sec. "Particles").  The fluid's bounce-back then uses V(t+1), so the
+ * momentum the fluid loses is exactly what the particle gains. */
+static void step_links(ref_sim* s)
+{
+    const ref_params* p = &s->p;
+    const long N = s->N;
+    for (int k = 0; k < s->np; ++k) {
+        ref_part* P = &s->part[k];
+        for (int a = 0; a < 3; ++a) P->F0[a] = P->T0[a] = 0.0;
+        memset(P->zeta, 0, sizeof(P->zeta));
+    }
+    if (s->np == 0) return;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long n = nidx(s, x, y, z);
+                if (s->mask[n]) continue;
+                for (int i = 1; i < 19; ++i) {
+                    long m = nbr(s, x, y, z, CX[i], CY[i], CZ[i]);
+                    if (m < 0 || !s->mask[m]) continue;
+                    ref_part* P = &s->part[s->mask[m] - 1];
+                    double r[3], ub[3], vs[3];
+                    link_velocity(s, P, x, y, z, i, r, ub, vs);
+                    double cvs = CX[i] * vs[0] + CY[i] * vs[1] + CZ[i] * vs[2];
+                    double mag = 2.0 * s->f[i * N + n] - 6.0 * W[i] * p->rho0 * cvs;
+                    double dP[3] = {CX[i] * mag, CY[i] * mag, CZ[i] * mag};
+                    if (p->thermo_force) {
+                        double c[3] = {(double)CX[i], (double)CY[i], (double)CZ[i]}, pc[3];
+                        pt_dot(s, n, c, pc);
+                        for (int a = 0; a < 3; ++a) dP[a] += 6.0 * W[i] * pc[a];
+                    }
+                    P->F0[0] += dP[0];
+                    P->F0[1] += dP[1];
+                    P->F0[2] += dP[2];
+                    P->T0[0] += r[1] * dP[2] - r[2] * dP[1];
+                    P->T0[1] += r[2] * dP[0] - r[0] * dP[2];
+                    P->T0[2] += r[0] * dP[1] - r[1] * dP[0];
+                    double g6[6] = {(double)CX[i], (double)CY[i], (double)CZ[i],
+                                    r[1] * CZ[i] - r[2] * CY[i],
+                                    r[2] * CX[i] - r[0] * CZ[i],
+                                    r[0] * CY[i] - r[1] * CX[i]};
+                    double zc = 6.0 * W[i] * p->rho0;
+                    for (int a = 0; a < 6; ++a)
+                        for (int b = 0; b < 6; ++b) P->zeta[a][b] += zc * g6[a] * g6[b];
+                }
+            }
+    for (int k = 0; k < s->np; ++k) {
+        ref_part* P = &s->part[k];
+        double F0[6];
+        for (int a = 0; a < 3; ++a) {
+            F0[a] = P->F0[a] + P->imp_f[a] + P->ext_f[a];
+            F0[3 + a] = P->T0[a] + P->imp_t[a] + P->ext_t[a];
+        }
+        double V[6] = {P->U[0], P->U[1], P->U[2], P->Om[0], P->Om[1], P->Om[2]};
+        if (!P->fixed) {
+            double Mm[6] = {P->M, P->M, P->M, P->I, P->I, P->I};
+            double A[6][6], b[6], Vn[6];
+            for (int a = 0; a < 6; ++a) {
+                for (int c = 0; c < 6; ++c) A[a][c] = P->zeta[a][c];
+                A[a][a] += Mm[a];
+                b[a] = Mm[a] * V[a] + F0[a];
+            }
+            if (solve6(A, b, Vn) != 0) s->err = -3;
+            for (int a = 0; a < 6; ++a) V[a] = Vn[a];
+        }
+        for (int a = 0; a < 6; ++a) {
+            double zv = 0.0;
+            for (int c = 0; c < 6; ++c) zv += P->zeta[a][c] * V[c];
+            if (a < 3)
+                P->force[a] = F0[a] - zv;
+            else
+                P->torque[a - 3] = F0[a] - zv;
+        }
+        for (int a = 0; a < 3; ++a) {
+            P->U[a] = V[a];
+            P->Om[a] = V[3 + a];
+            P->imp_f[a] = P->imp_t[a] = 0.0;
+        }
+    }
 }
 
 /* ------------------------------------------------------------------ */
@@ -251,11 +416,6 @@ static void step_collide(ref_sim* s)
 {
     const ref_params* p = &s->p;
     const long N = s->N;
-    for (int k = 0; k < s->np; ++k) {
-        ref_part* P = &s->part[k];
-        for (int a = 0; a < 3; ++a) P->F0[a] = P->T0[a] = 0.0;
-        memset(P->zeta, 0, sizeof(P->zeta));
-    }
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
@@ -265,29 +425,33 @@ static void step_collide(ref_sim* s)
                     s->u[n] = s->u[N + n] = s->u[2 * N + n] = 0.0;
                     continue;
                 }
-                /* S2: F = -psi grad mu_psi - phi grad mu_phi + g, gradients by
-                 * 3 sum_i w_i c_i mu(x+c_i); solid/wall neighbours use mu(x). */
+                /* S2: F = g - div P, in the link form
+                 * -6 sum_i w_i [(P(x) + P(x+c_i))/2] . c_i, with P(x) standing
+                 * in for solid and wall neighbours (their share is the flux
+                 * the particle or the wall receives). */
                 double F[3] = {p->body_force[0], p->body_force[1], p->body_force[2]};
                 if (p->thermo_force) {
-                    double gps[3] = {0, 0, 0}, gph[3] = {0, 0, 0};
+                    double div[3] = {0.0, 0.0, 0.0};
                     for (int i = 1; i < 19; ++i) {
                         long m = nbr(s, x, y, z, CX[i], CY[i], CZ[i]);
-                        double a = (m < 0 || s->mask[m]) ? s->mupsi[n] : s->mupsi[m];
-                        double b = (m < 0 || s->mask[m]) ? s->muphi[n] : s->muphi[m];
-                        gps[0] += W[i] * CX[i] * a;
-                        gps[1] += W[i] * CY[i] * a;
-                        gps[2] += W[i] * CZ[i] * a;
-                        gph[0] += W[i] * CX[i] * b;
-                        gph[1] += W[i] * CY[i] * b;
-                        gph[2] += W[i] * CZ[i] * b;
+                        double c[3] = {(double)CX[i], (double)CY[i], (double)CZ[i]};
+                        double a[3], b[3];
+                        pt_dot(s, n, c, a);
+                        if (m < 0 || s->mask[m]) {
+                            b[0] = a[0];
+                            b[1] = a[1];
+                            b[2] = a[2];
+                        } else {
+                            pt_dot(s, m, c, b);
+                        }
+                        for (int k = 0; k < 3; ++k) div[k] += W[i] * (0.5 * (a[k] + b[k]));
                     }
-                    for (int a = 0; a < 3; ++a)
-                        F[a] += -s->psi[n] * (3.0 * gps[a]) - s->phi[n] * (3.0 * gph[a]);
+                    for (int k = 0; k < 3; ++k) F[k] -= 6.0 * div[k];
                 }
                 /* S3: pull f_j(x) = f*_j(x - c_j); a wall source reflects
                  * f*_{jbar}(x); a particle source reflects with the moving
                  * boundary term (Ladd): f_j = f*_i(x) - 6 w_i rho0 c_i.u_b,
-                 * i = jbar, and the particle receives c_i (f*_i + f_j). */
+                 * i = jbar, with the particle velocity of this step. */
                 double fl[19];
                 for (int j = 0; j < 19; ++j) {
                     if (j == 0) {
@@ -299,30 +463,11 @@ static void step_collide(ref_sim* s)
                     if (m < 0) {
                         fl[j] = s->f[i * N + n];
                     } else if (s->mask[m]) {
-                        ref_part* P = &s->part[s->mask[m] - 1];
+                        const ref_part* P = &s->part[s->mask[m] - 1];
                         double r[3], ub[3], vs[3];
                         link_velocity(s, P, x, y, z, i, r, ub, vs);
                         double cub = CX[i] * ub[0] + CY[i] * ub[1] + CZ[i] * ub[2];
-                        double fi = s->f[i * N + n];
-                        fl[j] = fi - 6.0 * W[i] * p->rho0 * cub;
-                        /* momentum exchange split into the part independent of
-                         * (U, Omega) and the linear drag matrix zeta */
-                        double cvs = CX[i] * vs[0] + CY[i] * vs[1] + CZ[i] * vs[2];
-                        double mag = 2.0 * fi - 6.0 * W[i] * p->rho0 * cvs;
-                        double dP[3] = {CX[i] * mag, CY[i] * mag, CZ[i] * mag};
-                        P->F0[0] += dP[0];
-                        P->F0[1] += dP[1];
-                        P->F0[2] += dP[2];
-                        P->T0[0] += r[1] * dP[2] - r[2] * dP[1];
-                        P->T0[1] += r[2] * dP[0] - r[0] * dP[2];
-                        P->T0[2] += r[0] * dP[1] - r[1] * dP[0];
-                        double g6[6] = {(double)CX[i], (double)CY[i], (double)CZ[i],
-                                        r[1] * CZ[i] - r[2] * CY[i],
-                                        r[2] * CX[i] - r[0] * CZ[i],
-                                        r[0] * CY[i] - r[1] * CX[i]};
-                        double zc = 6.0 * W[i] * p->rho0;
-                        for (int a = 0; a < 6; ++a)
-                            for (int b = 0; b < 6; ++b) P->zeta[a][b] += zc * g6[a] * g6[b];
+                        fl[j] = s->f[i * N + n] - 6.0 * W[i] * p->rho0 * cub;
                     } else {
                         fl[j] = s->f[j * N + m];
                     }
@@ -364,6 +509,8 @@ static void step_scalars(ref_sim* s)
 {
     const ref_params* p = &s->p;
     const long N = s->N;
+    s->wall_psi = 0.0;
+    s->wall_phi = 0.0;
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
@@ -380,13 +527,25 @@ static void step_scalars(ref_sim* s)
                 memset(adj, 0, (size_t)s->np);
                 /* flux on each fluid-fluid link: diffusion M (mu(y) - mu(x))
                  * minus the advective flux, taken upwind (donor cell) with
-                 * the link-mean velocity ub = c.(u(x) + u(y))/2; links to
-                 * solid or wall carry no flux. */
+                 * the link-mean velocity ub = c.(u(x) + u(y))/2.  Links to a
+                 * wall carry no flux; a link to a particle carries no
+                 * diffusive flux and the advective flux c.u_b g(x), u_b the
+                 * boundary velocity of the bounce-back rule (the scalar moves
+                 * with the fluid mass that rule exchanges with the wall). */
                 for (int i = 1; i < 19; ++i) {
                     long m = nbr(s, x, y, z, CX[i], CY[i], CZ[i]);
                     if (m < 0) continue;
                     if (s->mask[m]) {
                         adj[s->mask[m] - 1] = 1;
+                        const ref_part* P = &s->part[s->mask[m] - 1];
+                        double r[3], ub[3], vs[3];
+                        link_velocity(s, P, x, y, z, i, r, ub, vs);
+                        double cub = CX[i] * ub[0] + CY[i] * ub[1] + CZ[i] * ub[2];
+                        double aps = cub * ps, aph = cub * ph;
+                        dps += W[i] * (0.0 - aps);
+                        dph += W[i] * (0.0 - aph);
+                        s->wall_psi += 6.0 * W[i] * aps;
+                        s->wall_phi += 6.0 * W[i] * aph;
                         continue;
                     }
                     double cu0 = CX[i] * u0[0] + CY[i] * u0[1] + CZ[i] * u0[2];
@@ -420,81 +579,14 @@ static void step_scalars(ref_sim* s)
 }
 
 /* ------------------------------------------------------------------ */
-/* S5 + S6: particle velocity update and motion                        */
+/* S6b: particle motion with the velocity of this step                 */
 /* ------------------------------------------------------------------ */
 
-/* Gaussian elimination with partial pivoting on a 6x6 system. */
-static int solve6(double A[6][6], double b[6], double x[6])
-{
-    int perm[6] = {0, 1, 2, 3, 4, 5};
-    for (int c = 0; c < 6; ++c) {
-        int piv = c;
-        for (int r = c + 1; r < 6; ++r)
-            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
-        if (A[piv][c] == 0.0) return -1;
-        if (piv != c) {
-            for (int k = 0; k < 6; ++k) {
-                double t = A[c][k];
-                A[c][k] = A[piv][k];
-                A[piv][k] = t;
-            }
-            double t = b[c];
-            b[c] = b[piv];
-            b[piv] = t;
-            int ti = perm[c];
-            perm[c] = perm[piv];
-            perm[piv] = ti;
-        }
-        for (int r = c + 1; r < 6; ++r) {
-            double l = A[r][c] / A[c][c];
-            for (int k = c; k < 6; ++k) A[r][k] -= l * A[c][k];
-            b[r] -= l * b[c];
-        }
-    }
-    for (int r = 5; r >= 0; --r) {
-        double acc = b[r];
-        for (int k = r + 1; k < 6; ++k) acc -= A[r][k] * x[k];
-        x[r] = acc / A[r][r];
-    }
-    return 0;
-}
-
-static void step_particles(ref_sim* s)
+static void step_move(ref_sim* s)
 {
     const int L[3] = {s->p.nx, s->p.ny, s->p.nz};
     for (int k = 0; k < s->np; ++k) {
         ref_part* P = &s->part[k];
-        double F0[6];
-        for (int a = 0; a < 3; ++a) {
-            F0[a] = P->F0[a] + P->imp_f[a] + P->ext_f[a];
-            F0[3 + a] = P->T0[a] + P->imp_t[a] + P->ext_t[a];
-        }
-        double V[6] = {P->U[0], P->U[1], P->U[2], P->Om[0], P->Om[1], P->Om[2]};
-        if (!P->fixed) {
-            /* (Mdiag + zeta) V' = Mdiag V + F0 */
-            double Mm[6] = {P->M, P->M, P->M, P->I, P->I, P->I};
-            double A[6][6], b[6], Vn[6];
-            for (int a = 0; a < 6; ++a) {
-                for (int c = 0; c < 6; ++c) A[a][c] = P->zeta[a][c];
-                A[a][a] += Mm[a];
-                b[a] = Mm[a] * V[a] + F0[a];
-            }
-            if (solve6(A, b, Vn) != 0) s->err = -3;
-            for (int a = 0; a < 6; ++a) V[a] = Vn[a];
-        }
-        for (int a = 0; a < 6; ++a) {
-            double zv = 0.0;
-            for (int c = 0; c < 6; ++c) zv += P->zeta[a][c] * V[c];
-            if (a < 3)
-                P->force[a] = F0[a] - zv;
-            else
-                P->torque[a - 3] = F0[a] - zv;
-        }
-        for (int a = 0; a < 3; ++a) {
-            P->U[a] = V[a];
-            P->Om[a] = V[3 + a];
-            P->imp_f[a] = P->imp_t[a] = 0.0;
-        }
         /* translate, wrapping periodic axes into [0, L) */
         for (int a = 0; a < 3; ++a) {
             double X = P->X[a] + P->U[a];
@@ -537,7 +629,8 @@ static void step_cover(ref_sim* s)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) s->maskn[nidx(s, x, y, z)] = owner(s, x, y, z);
-    double dpsi = 0.0, dphi = 0.0;
+    /* what the moving surfaces carried out of the fluid this step */
+    double dpsi = s->wall_psi, dphi = s->wall_phi;
     long dfl = 0;
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
@@ -546,12 +639,16 @@ static void step_cover(ref_sim* s)
                 unsigned char o = s->mask[n], q = s->maskn[n];
                 if (o == q) continue;
                 if (o == 0) {
-                    /* newly covered: the particle takes the node's momentum,
-                     * the node's psi and phi are removed */
+                    /* newly covered: the particle takes the momentum its
+                     * populations carry, sum_i f_i c_i; the node's psi and phi
+                     * are removed */
                     ref_part* P = &s->part[q - 1];
-                    double rho = 0.0;
-                    for (int i = 0; i < 19; ++i) rho += s->f[i * N + n];
-                    double j[3] = {rho * s->u[n], rho * s->u[N + n], rho * s->u[2 * N + n]};
+                    double j[3] = {0.0, 0.0, 0.0};
+                    for (int i = 0; i < 19; ++i) {
+                        j[0] += CX[i] * s->f[i * N + n];
+                        j[1] += CY[i] * s->f[i * N + n];
+                        j[2] += CZ[i] * s->f[i * N + n];
+                    }
                     double r[3];
                     node_offset(s, P, x, y, z, r);
                     for (int a = 0; a < 3; ++a) P->imp_f[a] += j[a];
@@ -615,7 +712,8 @@ static void step_cover(ref_sim* s)
     s->nfluid += dfl;
     if (dfl == 0 && dpsi == 0.0 && dphi == 0.0) return;
     /* restore the totals of psi and phi: spread the removed minus the added
-     * amount uniformly over every fluid node */
+     * amount (covering, uncovering and the flux into the moving surfaces)
+     * uniformly over every fluid node */
     double cps = dpsi / (double)s->nfluid, cph = dphi / (double)s->nfluid;
     for (long n = 0; n < N; ++n) {
         if (s->mask[n]) continue;
@@ -644,11 +742,12 @@ ref_sim* ref_create(const ref_params* p)
     s->phin = (double*)calloc((size_t)N, sizeof(double));
     s->mupsi = (double*)calloc((size_t)N, sizeof(double));
     s->muphi = (double*)calloc((size_t)N, sizeof(double));
+    s->pt = (double*)calloc((size_t)(6 * N), sizeof(double));
     s->u = (double*)calloc((size_t)(3 * N), sizeof(double));
     s->mask = (unsigned char*)calloc((size_t)N, 1);
     s->maskn = (unsigned char*)calloc((size_t)N, 1);
     if (!s->f || !s->fn || !s->psi || !s->phi || !s->psin || !s->phin || !s->mupsi || !s->muphi ||
-        !s->u || !s->mask || !s->maskn) {
+        !s->u || !s->mask || !s->maskn || !s->pt) {
         ref_destroy(s);
         return NULL;
     }
@@ -670,6 +769,7 @@ void ref_destroy(ref_sim* s)
     free(s->phin);
     free(s->mupsi);
     free(s->muphi);
+    free(s->pt);
     free(s->u);
     free(s->mask);
     free(s->maskn);
@@ -743,9 +843,10 @@ int ref_step(ref_sim* s, int nsteps)
 {
     for (int t = 0; t < nsteps; ++t) {
         step_mu(s);
+        step_links(s);
         step_collide(s);
         step_scalars(s);
-        step_particles(s);
+        step_move(s);
         step_cover(s);
     }
     return s->err;

@@ -133,6 +133,11 @@ class Oracle:
         self.lib = _load()
         q = dict(self.DEFAULTS)
         q.update(params)
+        if "solubility_ratio" in q:
+            r = q.pop("solubility_ratio")
+            if "E" not in params:
+                q["E"] = solubility_E(r, q["phi_b"])
+        q.pop("precision", None)
         self.params = q
         p = RefParams()
         p.nx, p.ny, p.nz = int(q["nx"]), int(q["ny"]), int(q["nz"])

@@ -1,0 +1,637 @@
+// lbdp_api.cu -- the extern "C" entry points declared in include/lbdp.h:
+// parameter validation, device allocation, host<->device staging and the
+// per-step launch sequence.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "lbdp.h"
+#include "lbdp_internal.h"
+#include "lbdp_kernels.cuh"
+
+using namespace lbdp;
+
+struct lb_handle {
+    lb_params prm;
+    DevParams dp;
+    const PrecOps* ops;
+    cudaStream_t stream;
+    bool own_stream;
+    int device;
+    int cur;   // which buffer of each pair holds the current state
+    void* f[2];
+    void* psi[2];
+    void* phi[2];
+    void* mupsi;
+    void* muphi;
+    void* u;
+    uint8_t* mask[2];
+    DevPart* parts;
+    double* corr;
+    int* err;
+    void* pt;
+    double* link_part;
+    unsigned* link_ticket;
+    double* cover_part;
+    unsigned* cover_ticket;
+    long long* nfluid;
+    double* staging;   // 6N FP64 for host transfers: rho, u[3], psi, phi
+    double* red_part;
+    double* red_out;
+    unsigned long long* count;
+    int red_blocks;
+    std::vector<DevPart> host_parts;
+    double rmax;
+};
+
+namespace {
+
+const PrecOps* ops_for(int prec)
+{
+    switch (prec) {
+        case LB_FP64: return &kOpsF64;
+        case LB_FP32: return &kOpsF32;
+        case LB_FP16_SHIFT: return &kOpsF16;
+        case LB_BF16_SHIFT: return &kOpsBF16;
+        default: return nullptr;
+    }
+}
+
+int validate(const lb_params* p)
+{
+    if (!p) return LB_ERR_PARAM;
+    if (p->nx <= 0 || p->ny <= 0 || p->nz <= 0) return LB_ERR_PARAM;
+    long long N = (long long)p->nx * p->ny * p->nz;
+    if (N * 19 >= (1ll << 31)) return LB_ERR_PARAM;   // 32-bit node indices
+    if (!ops_for(p->precision)) return LB_ERR_PARAM;
+    if (!(p->tau > 0.5) || !(p->rho0 > 0.0)) return LB_ERR_PARAM;
+    if (p->kappa < 0.0 || p->M_psi < 0.0 || p->M_phi < 0.0 || p->k_d < 0.0) return LB_ERR_PARAM;
+    for (int a = 0; a < 3; ++a)
+        if (p->periodic[a] != 0 && p->periodic[a] != 1) return LB_ERR_PARAM;
+    return LB_OK;
+}
+
+size_t state_bytes(const lb_params* p, const PrecOps* ops, int red_blocks)
+{
+    size_t N = (size_t)p->nx * p->ny * p->nz;
+    size_t b = 0;
+    b += 2 * 19 * N * (size_t)ops->pop_bytes;          // populations
+    b += (4 + 2 + 3) * N * (size_t)ops->fld_bytes;     // psi, phi (x2), mu, u
+    b += 2 * N;                                         // masks
+    b += 6 * N * sizeof(double);                        // staging
+    b += 6 * N * (size_t)ops->fld_bytes;                // pressure tensor
+    b += kMaxParticles * (sizeof(DevPart) + sizeof(unsigned));
+    b += (size_t)kMaxParticles * kMaxPartBlocks * (kLinkK + kCoverK) * sizeof(double);
+    b += (size_t)red_blocks * 3 * sizeof(double) + 64;
+    return b;
+}
+
+int reduction_blocks(const lb_params* p)
+{
+    long long N = (long long)p->nx * p->ny * p->nz;
+    long long b = (N + 255) / 256;
+    return (int)(b < 152 * 8 ? b : 152 * 8);
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? LB_OK : (e == cudaErrorMemoryAllocation ? LB_ERR_NOMEM : LB_ERR_CUDA); }
+
+#define LB_TRY(expr)                                   \
+    do {                                               \
+        cudaError_t e_ = (expr);                       \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+DevPtrs ptrs(const lb_handle* h, int src)
+{
+    DevPtrs d;
+    const int dst = src ^ 1;
+    d.f_src = h->f[src];
+    d.f_dst = h->f[dst];
+    d.psi_src = h->psi[src];
+    d.psi_dst = h->psi[dst];
+    d.phi_src = h->phi[src];
+    d.phi_dst = h->phi[dst];
+    d.mupsi = h->mupsi;
+    d.muphi = h->muphi;
+    d.u = h->u;
+    d.mask = h->mask[src];
+    d.mask_next = h->mask[dst];
+    d.parts = h->parts;
+    d.corr = h->corr;
+    d.err = h->err;
+    d.pt = h->pt;
+    d.link_part = h->link_part;
+    d.link_ticket = h->link_ticket;
+    d.cover_part = h->cover_part;
+    d.cover_ticket = h->cover_ticket;
+    d.nfluid = h->nfluid;
+    return d;
+}
+
+// Pointers for set/get of the current state: both src and dst name the
+// current buffers.
+DevPtrs cur_ptrs(const lb_handle* h)
+{
+    DevPtrs d = ptrs(h, h->cur);
+    d.f_dst = h->f[h->cur];
+    d.psi_dst = h->psi[h->cur];
+    d.phi_dst = h->phi[h->cur];
+    d.mask_next = h->mask[h->cur];
+    return d;
+}
+
+RowGrid row_grid(const DevParams& P)
+{
+    RowGrid g;
+    int bx = P.nx >= 128 ? 128 : ((P.nx + 31) / 32) * 32;
+    g.block = dim3(bx, 1, 1);
+    g.grid = dim3((P.nx + bx - 1) / bx, P.ny, P.nz);
+    return g;
+}
+
+void update_sides(lb_handle* h)
+{
+    const int L[3] = {h->dp.nx, h->dp.ny, h->dp.nz};
+    const int rc = (int)ceil(h->rmax);
+    for (int a = 0; a < 3; ++a) {
+        int s1 = 2 * rc + 6, s2 = 2 * rc + 9;
+        if (h->dp.per[a]) {
+            if (s1 > L[a]) s1 = L[a];
+            if (s2 > L[a]) s2 = L[a];
+        }
+        h->dp.side1[a] = s1;
+        h->dp.side2[a] = s2;
+    }
+    // blocks per particle: about one box node per thread, at most kMaxPartBlocks
+    const long long t1 = (long long)h->dp.side1[0] * h->dp.side1[1] * h->dp.side1[2];
+    const long long t2 = (long long)h->dp.side2[0] * h->dp.side2[1] * h->dp.side2[2];
+    const long long b1 = (t1 + 255) / 256, b2 = (t2 + 255) / 256;
+    h->dp.nb1 = (int)(b1 < kMaxPartBlocks ? (b1 > 0 ? b1 : 1) : kMaxPartBlocks);
+    h->dp.nb2 = (int)(b2 < kMaxPartBlocks ? (b2 > 0 ? b2 : 1) : kMaxPartBlocks);
+}
+
+void free_all(lb_handle* h)
+{
+    if (h->device >= 0) cudaSetDevice(h->device);
+    void* ptrs_[] = {h->f[0], h->f[1], h->psi[0], h->psi[1], h->phi[0], h->phi[1], h->mupsi, h->muphi,
+                     h->u, h->mask[0], h->mask[1], h->parts, h->corr, h->err, h->pt, h->link_part,
+                     h->link_ticket, h->cover_part, h->cover_ticket, h->nfluid, h->staging, h->red_part, h->red_out, h->count};
+    for (void* p : ptrs_)
+        if (p) cudaFree(p);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+double mimg(double d, int L, int per)
+{
+    if (per) {
+        if (d > 0.5 * L)
+            d -= L;
+        else if (d < -0.5 * L)
+            d += L;
+    }
+    return d;
+}
+
+int read_err(lb_handle* h)
+{
+    int e = 0;
+    LB_TRY(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LB_TRY(cudaStreamSynchronize(h->stream));
+    if (e & (kErrOverlap | kErrWall)) return LB_ERR_OVERLAP;
+    if (e & kErrSolve) return LB_ERR_NONFINITE;
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_device_bytes(const lb_params* p, size_t* bytes)
+{
+    int st = validate(p);
+    if (st != LB_OK || !bytes) return LB_ERR_PARAM;
+    *bytes = state_bytes(p, ops_for(p->precision), reduction_blocks(p));
+    return LB_OK;
+}
+
+int lb_create(const lb_params* p, lb_handle** out)
+{
+    if (!out) return LB_ERR_PARAM;
+    *out = nullptr;
+    int st = validate(p);
+    if (st != LB_OK) return st;
+    lb_handle* h = new (std::nothrow) lb_handle();
+    if (!h) return LB_ERR_NOMEM;
+    h->prm = *p;
+    h->ops = ops_for(p->precision);
+    h->device = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        delete h;
+        return LB_ERR_CUDA;
+    }
+    h->device = dev;
+    DevParams& P = h->dp;
+    memset(&P, 0, sizeof(P));
+    P.nx = p->nx;
+    P.ny = p->ny;
+    P.nz = p->nz;
+    for (int a = 0; a < 3; ++a) {
+        P.per[a] = p->periodic[a];
+        P.g[a] = p->body_force[a];
+    }
+    P.N = (long long)p->nx * p->ny * p->nz;
+    P.np = 0;
+    P.thermo = p->thermo_force;
+    P.tau = p->tau;
+    P.rho0 = p->rho0;
+    P.A = p->A;
+    P.kappa = p->kappa;
+    P.Mpsi = p->M_psi;
+    P.C = p->C;
+    P.Mphi = p->M_phi;
+    P.E = p->E;
+    P.phib = p->phi_b;
+    P.kd = p->k_d;
+    h->rmax = 0.0;
+    update_sides(h);
+    h->red_blocks = reduction_blocks(p);
+
+    const size_t N = (size_t)P.N;
+    cudaError_t e = cudaSuccess;
+    if (p->cuda_stream) {
+        h->stream = (cudaStream_t)p->cuda_stream;
+        h->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        h->own_stream = true;
+    }
+    const size_t pb = (size_t)h->ops->pop_bytes, fb = (size_t)h->ops->fld_bytes;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMalloc(&h->f[k], 19 * N * pb);
+        if (e == cudaSuccess) e = cudaMalloc(&h->psi[k], N * fb);
+        if (e == cudaSuccess) e = cudaMalloc(&h->phi[k], N * fb);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&h->mask[k], N);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&h->mupsi, N * fb);
+    if (e == cudaSuccess) e = cudaMalloc(&h->muphi, N * fb);
+    if (e == cudaSuccess) e = cudaMalloc(&h->u, 3 * N * fb);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->parts, kMaxParticles * sizeof(DevPart));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->corr, 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->pt, 6 * N * fb);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void**)&h->link_part, (size_t)kMaxParticles * kMaxPartBlocks * kLinkK * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->link_ticket, kMaxParticles * sizeof(unsigned));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void**)&h->cover_part, (size_t)kMaxParticles * kMaxPartBlocks * kCoverK * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->cover_ticket, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->nfluid, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->staging, 6 * N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->red_part, (size_t)h->red_blocks * 3 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->red_out, 3 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->count, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        free_all(h);
+        delete h;
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    // rest state: rho = rho0, u = 0, psi = phi = 0, all fluid
+    cudaStream_t s = h->stream;
+    long long nf = P.N;
+    e = cudaMemsetAsync(h->mask[0], 0, N, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->mask[1], 0, N, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->corr, 0, 2 * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->link_ticket, 0, kMaxParticles * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->cover_ticket, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->pt, 0, 6 * N * fb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->u, 0, 3 * N * fb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->mupsi, 0, N * fb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->muphi, 0, N * fb, s);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMemsetAsync(h->psi[k], 0, N * fb, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->phi[k], 0, N * fb, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->nfluid, &nf, sizeof(long long), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        // populations from rho = rho0 everywhere (staging holds rho0)
+        std::vector<double> ones(N, p->rho0);
+        e = cudaMemcpyAsync(h->staging, ones.data(), N * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = h->ops->set_fields(P, cur_ptrs(h), s, h->staging, nullptr, nullptr, nullptr);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
+        free_all(h);
+        delete h;
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    *out = h;
+    return LB_OK;
+}
+
+void lb_destroy(lb_handle* h)
+{
+    if (!h) return;
+    if (h->device >= 0) cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+int lb_set_fields(lb_handle* h, const double* rho, const double* u, const double* psi, const double* phi)
+{
+    if (!h) return LB_ERR_PARAM;
+    cudaSetDevice(h->device);
+    const size_t N = (size_t)h->dp.N;
+    cudaStream_t s = h->stream;
+    double* st_rho = h->staging;
+    double* st_u = h->staging + N;
+    double* st_psi = h->staging + 4 * N;
+    double* st_phi = h->staging + 5 * N;
+    if (rho) LB_TRY(cudaMemcpyAsync(st_rho, rho, N * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (u) LB_TRY(cudaMemcpyAsync(st_u, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (psi) LB_TRY(cudaMemcpyAsync(st_psi, psi, N * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (phi) LB_TRY(cudaMemcpyAsync(st_phi, phi, N * sizeof(double), cudaMemcpyHostToDevice, s));
+    // one pass: fields from staging (or current value plus the pending uniform
+    // correction), populations to equilibrium; then the correction is spent
+    LB_TRY(h->ops->set_fields(h->dp, cur_ptrs(h), s, rho ? st_rho : nullptr, u ? st_u : nullptr,
+                              psi ? st_psi : nullptr, phi ? st_phi : nullptr));
+    LB_TRY(cudaMemsetAsync(h->corr, 0, 2 * sizeof(double), s));
+    return LB_OK;
+}
+
+double lb_wetting_h(double theta_deg)
+{
+    const double target = cos(theta_deg * M_PI / 180.0);
+    double lo = -1.0, hi = 1.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        const double v = 0.5 * (pow(1.0 + mid, 1.5) - pow(1.0 - mid, 1.5));
+        if (v < target)
+            lo = mid;
+        else
+            hi = mid;
+        if (hi - lo < 1e-16) break;
+    }
+    return 0.5 * (lo + hi);
+}
+
+double lb_solubility_E(double ratio, double phi_b) { return phi_b * (ratio - 1.0) / ((ratio + 1.0) * tanh(1.0)); }
+
+int lb_add_particle(lb_handle* h, const lb_particle_desc* d, int* id_out)
+{
+    if (!h || !d) return LB_ERR_PARAM;
+    cudaSetDevice(h->device);
+    const DevParams& P = h->dp;
+    if ((int)h->host_parts.size() >= kMaxParticles) return LB_ERR_PARAM;
+    if (!(d->R > 0.0)) return LB_ERR_PARAM;
+    const double mn = sqrt(d->m_hat[0] * d->m_hat[0] + d->m_hat[1] * d->m_hat[1] + d->m_hat[2] * d->m_hat[2]);
+    if (!(mn > 0.0)) return LB_ERR_PARAM;
+    double H = d->H;
+    if (!isnan(d->theta_c_deg)) {
+        if (d->theta_c_deg < 0.0 || d->theta_c_deg > 180.0) return LB_ERR_PARAM;
+        H = lb_wetting_h(d->theta_c_deg) * sqrt(P.kappa * P.A);
+    }
+    if (H != 0.0 && !(P.kappa > 0.0)) return LB_ERR_PARAM;
+    const int L[3] = {P.nx, P.ny, P.nz};
+    DevPart q;
+    memset(&q, 0, sizeof(q));
+    for (int a = 0; a < 3; ++a) {
+        double X = d->pos[a];
+        if (P.per[a]) {
+            if (X < 0.0 || X >= L[a]) return LB_ERR_PARAM;
+        } else if (X - d->R < 1.0 || X + d->R > L[a] - 2.0) {
+            return LB_ERR_OVERLAP;
+        }
+        q.X[a] = X;
+        q.Xn[a] = X;
+        q.U[a] = d->vel[a];
+        q.W[a] = d->omega[a];
+        q.m[a] = d->m_hat[a] / mn;
+        q.mn[a] = q.m[a];
+        q.ext_f[a] = d->ext_force[a];
+        q.ext_t[a] = d->ext_torque[a];
+    }
+    // the covering box must not wrap onto itself on a periodic axis
+    for (const DevPart& o : h->host_parts) {
+        double r[3];
+        for (int a = 0; a < 3; ++a) r[a] = mimg(q.X[a] - o.X[a], L[a], P.per[a]);
+        if (sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) < d->R + o.R + 1.0) return LB_ERR_OVERLAP;
+    }
+    q.R = d->R;
+    q.R2 = d->R * d->R;
+    const double rp = d->rho_p > 0.0 ? d->rho_p : 1.0;
+    q.M = rp * (4.0 / 3.0) * M_PI * d->R * d->R * d->R;
+    q.I = 0.4 * q.M * d->R * d->R;
+    q.alpha = d->alpha;
+    q.mu_p = d->mu_plus;
+    q.mu_m = d->mu_minus;
+    q.H = H;
+    q.fixed = d->fixed ? 1 : 0;
+    const int k = (int)h->host_parts.size();
+    // fetch the device copies first: earlier particles have moved
+    if (k > 0) {
+        h->host_parts.resize(k);
+        LB_TRY(cudaMemcpyAsync(h->host_parts.data(), h->parts, k * sizeof(DevPart), cudaMemcpyDeviceToHost,
+                               h->stream));
+        LB_TRY(cudaStreamSynchronize(h->stream));
+    }
+    h->host_parts.push_back(q);
+    LB_TRY(cudaMemcpyAsync(h->parts + k, &h->host_parts[k], sizeof(DevPart), cudaMemcpyHostToDevice, h->stream));
+    unsigned long long zero = 0, cnt = 0;
+    LB_TRY(cudaMemcpyAsync(h->count, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->stream));
+    LB_TRY(launch_claim(P, h->mask[h->cur], h->mask[h->cur ^ 1], h->parts, k, h->count, h->stream));
+    long long nf = 0;
+    LB_TRY(cudaMemcpyAsync(&cnt, h->count, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
+    LB_TRY(cudaMemcpyAsync(&nf, h->nfluid, sizeof(nf), cudaMemcpyDeviceToHost, h->stream));
+    LB_TRY(cudaStreamSynchronize(h->stream));
+    nf -= (long long)cnt;
+    LB_TRY(cudaMemcpyAsync(h->nfluid, &nf, sizeof(nf), cudaMemcpyHostToDevice, h->stream));
+    LB_TRY(cudaStreamSynchronize(h->stream));
+    h->dp.np = k + 1;
+    if (d->R > h->rmax) h->rmax = d->R;
+    update_sides(h);
+    if (id_out) *id_out = k;
+    return LB_OK;
+}
+
+int lb_step(lb_handle* h, int nsteps)
+{
+    if (!h || nsteps < 0) return LB_ERR_PARAM;
+    cudaSetDevice(h->device);
+    const RowGrid g = row_grid(h->dp);
+    for (int t = 0; t < nsteps; ++t) {
+        LB_TRY(h->ops->step(h->dp, ptrs(h, h->cur), g, h->stream));
+        h->cur ^= 1;
+    }
+    return LB_OK;
+}
+
+int lb_profile_step(lb_handle* h, int nsteps, double* ms, int* launches)
+{
+    if (!h || nsteps < 0 || !ms) return LB_ERR_PARAM;
+    cudaSetDevice(h->device);
+    const RowGrid g = row_grid(h->dp);
+    std::vector<cudaEvent_t> ev((size_t)nsteps * 6);
+    for (auto& e : ev) LB_TRY(cudaEventCreate(&e));
+    int st = LB_OK;
+    for (int t = 0; t < nsteps && st == LB_OK; ++t) {
+        cudaError_t e = h->ops->step_events(h->dp, ptrs(h, h->cur), g, h->stream, &ev[(size_t)t * 6]);
+        if (e != cudaSuccess) st = cuda_status(e);
+        h->cur ^= 1;
+    }
+    for (int k = 0; k < kNumKernelClasses; ++k) ms[k] = 0.0;
+    if (st == LB_OK) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) st = cuda_status(e);
+    }
+    for (int t = 0; t < nsteps && st == LB_OK; ++t)
+        for (int k = 0; k < kNumKernelClasses; ++k) {
+            float v = 0.f;
+            cudaEventElapsedTime(&v, ev[(size_t)t * 6 + k], ev[(size_t)t * 6 + k + 1]);
+            ms[k] += v;
+        }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (launches) *launches = nsteps * (h->dp.np > 0 ? 6 : 3);
+    return st;
+}
+
+int lb_step_launches(const lb_handle* h, int nsteps)
+{
+    if (!h || nsteps < 0) return LB_ERR_PARAM;
+    return nsteps * (h->dp.np > 0 ? 6 : 3);
+}
+
+int lb_sync(lb_handle* h)
+{
+    if (!h) return LB_ERR_PARAM;
+    cudaSetDevice(h->device);
+    LB_TRY(cudaStreamSynchronize(h->stream));
+    return read_err(h);
+}
+
+int lb_read_fields(lb_handle* h, double* rho, double* u, double* psi, double* phi)
+{
+    if (!h) return LB_ERR_PARAM;
+    cudaSetDevice(h->device);
+    const size_t N = (size_t)h->dp.N;
+    cudaStream_t s = h->stream;
+    const DevPtrs D = cur_ptrs(h);
+    struct {
+        double* host;
+        int bit;
+        size_t n;
+    } items[4] = {{rho, 1, N}, {u, 2, 3 * N}, {psi, 4, N}, {phi, 8, N}};
+    for (auto& it : items) {
+        if (!it.host) continue;
+        double* st = h->staging;
+        LB_TRY(h->ops->get_fields(h->dp, D, s, it.bit, st, st, st, st));
+        LB_TRY(cudaMemcpyAsync(it.host, st, it.n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        LB_TRY(cudaStreamSynchronize(s));
+    }
+    return read_err(h);
+}
+
+int lb_read_mu(lb_handle* h, double* mu_psi, double* mu_phi)
+{
+    if (!h || !mu_psi || !mu_phi) return LB_ERR_PARAM;
+    cudaSetDevice(h->device);
+    const size_t N = (size_t)h->dp.N;
+    cudaStream_t s = h->stream;
+    LB_TRY(h->ops->get_fields(h->dp, cur_ptrs(h), s, 16, h->staging, nullptr, h->staging + N, nullptr));
+    LB_TRY(cudaMemcpyAsync(mu_psi, h->staging, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LB_TRY(cudaMemcpyAsync(mu_phi, h->staging + N, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LB_TRY(cudaStreamSynchronize(s));
+    return LB_OK;
+}
+
+int lb_read_populations(lb_handle* h, double* f)
+{
+    if (!h || !f) return LB_ERR_PARAM;
+    cudaSetDevice(h->device);
+    const size_t N = (size_t)h->dp.N;
+    cudaStream_t s = h->stream;
+    for (int i = 0; i < 19; ++i) {
+        LB_TRY(h->ops->get_pop(h->dp, cur_ptrs(h), s, h->staging, i));
+        LB_TRY(cudaMemcpyAsync(f + (size_t)i * N, h->staging, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        LB_TRY(cudaStreamSynchronize(s));
+    }
+    return LB_OK;
+}
+
+int lb_read_mask(lb_handle* h, unsigned char* mask)
+{
+    if (!h || !mask) return LB_ERR_PARAM;
+    cudaSetDevice(h->device);
+    LB_TRY(cudaMemcpyAsync(mask, h->mask[h->cur], (size_t)h->dp.N, cudaMemcpyDeviceToHost, h->stream));
+    LB_TRY(cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+int lb_read_particles(lb_handle* h, lb_particle_state* out, int cap, int* n_out)
+{
+    if (!h || cap < 0 || (cap > 0 && !out)) return LB_ERR_PARAM;
+    cudaSetDevice(h->device);
+    const int np = h->dp.np;
+    if (n_out) *n_out = np;
+    const int n = np < cap ? np : cap;
+    if (n == 0) return read_err(h);
+    std::vector<DevPart> tmp(n);
+    LB_TRY(cudaMemcpyAsync(tmp.data(), h->parts, n * sizeof(DevPart), cudaMemcpyDeviceToHost, h->stream));
+    LB_TRY(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < n; ++k)
+        for (int a = 0; a < 3; ++a) {
+            out[k].pos[a] = tmp[k].X[a];
+            out[k].vel[a] = tmp[k].U[a];
+            out[k].omega[a] = tmp[k].W[a];
+            out[k].m_hat[a] = tmp[k].m[a];
+            out[k].force[a] = tmp[k].force[a];
+            out[k].torque[a] = tmp[k].torque[a];
+        }
+    return read_err(h);
+}
+
+int lb_conservation(lb_handle* h, double sums[3])
+{
+    if (!h || !sums) return LB_ERR_PARAM;
+    cudaSetDevice(h->device);
+    LB_TRY(h->ops->sums(h->dp, cur_ptrs(h), h->stream, h->red_part, h->red_blocks, h->red_out));
+    LB_TRY(cudaMemcpyAsync(sums, h->red_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LB_TRY(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(sums[k])) return LB_ERR_NONFINITE;
+    return read_err(h);
+}
+
+const char* lb_error_string(int status)
+{
+    switch (status) {
+        case LB_OK: return "ok";
+        case LB_ERR_PARAM: return "invalid argument or parameter";
+        case LB_ERR_NOMEM: return "device allocation failed";
+        case LB_ERR_NONFINITE: return "non-finite state (NaN/Inf or singular particle system)";
+        case LB_ERR_OVERLAP: return "particles met or a particle reached a wall";
+        case LB_ERR_CUDA: return "CUDA call failed";
+        case LB_ERR_TIMEOUT: return "device wait expired";
+        case LB_ERR_STATE: return "call not valid in this state";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"
+
+namespace lbdp {
+cudaError_t launch_claim(const DevParams& P, uint8_t* m0, uint8_t* m1, const DevPart* parts, int p,
+                         unsigned long long* count, cudaStream_t s)
+{
+    long long b = (P.N + 255) / 256;
+    int blocks = (int)(b < 152 * 16 ? b : 152 * 16);
+    k_claim<<<blocks, 256, 0, s>>>(P, m0, m1, parts, p, count);
+    return cudaGetLastError();
+}
+}  // namespace lbdp

