@@ -178,6 +178,35 @@ int lb_read_particles(lb_handle* h, lb_particle_state* out, int cap, int* n_out)
  * LB_ERR_NONFINITE if any is NaN or Inf.  Synchronises. */
 int lb_conservation(lb_handle* h, double sums[3]);
 
+/* FP64 totals of caller-owned fields, computed without allocating device
+ * memory.  The paper has no counterpart: this call exists for callers that
+ * must not allocate -- a serving process whose device memory is planned and
+ * owned by its own arena allocator, or a latency-critical loop that cannot
+ * pay for the device-wide synchronisation cudaMalloc/cudaFree may imply.
+ *
+ * Inputs are device pointers in plain (unshifted) layout of the given
+ * precision (LB_FP64 double or LB_FP32 float): populations f [19][N],
+ * psi [N], phi [N], and mask [N] (u8, 0 = fluid; NULL counts every node).
+ * sums (device, 3 doubles) receives sum rho = sum_i f_i, sum psi, sum phi
+ * over the counted nodes, in the same fixed order on every call.  Work is
+ * queued on stream (a cudaStream_t, NULL = legacy default stream) and the
+ * call returns without waiting.
+ *
+ * Per-block partials live in one fixed 192 KiB array in the library's
+ * device memory (3 doubles for each of 8192 blocks of 2048 nodes), which
+ * every GPU that loads the library holds until the process exits.  Boxes of
+ * more than 8192 * 2048 = 16,777,216 nodes (256^3) are rejected with
+ * LB_ERR_PARAM before anything is queued.  The first call on each device
+ * looks up that array's device address (cudaGetSymbolAddress), so make the
+ * first call on a device before any stream capture.  All calls share the
+ * array: each call overwrites every slot it reads, so nothing carries over,
+ * but calls that overlap on the GPU (on different streams without ordering)
+ * race on it.  No cudaMalloc, cudaFree or other allocating routine is
+ * called.  Returns LB_OK, LB_ERR_PARAM or LB_ERR_CUDA. */
+int lb_totals_noalloc(int precision, int nx, int ny, int nz, const void* f,
+                      const void* psi, const void* phi, const unsigned char* mask,
+                      double* sums, void* stream);
+
 /* Device bytes lb_create would allocate for params (for admission control). */
 int lb_device_bytes(const lb_params* params, size_t* bytes);
 

@@ -86,6 +86,8 @@ def _load():
         "lb_read_mask": (C.c_int, [h, P(C.c_ubyte)]),
         "lb_read_particles": (C.c_int, [h, P(LbParticleState), C.c_int, P(C.c_int)]),
         "lb_conservation": (C.c_int, [h, dp]),
+        "lb_totals_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
         "lb_device_bytes": (C.c_int, [P(LbParams), P(C.c_size_t)]),
         "lb_wetting_h": (C.c_double, [C.c_double]),
         "lb_solubility_E": (C.c_double, [C.c_double, C.c_double]),
@@ -200,6 +202,16 @@ def lb_conservation(h) -> np.ndarray:
     s = np.zeros(3)
     _check(_lib.lb_conservation(h, _dptr(s)), "lb_conservation")
     return s
+
+
+def lb_totals_noalloc(precision, nx, ny, nz, f_ptr, psi_ptr, phi_ptr, mask_ptr, sums_ptr, stream=None) -> None:
+    """FP64 totals (sum rho, psi, phi) of caller-owned device arrays into the
+    device buffer ``sums_ptr``, without any device allocation (for callers
+    whose device memory is owned by their own allocator).  Pointers are raw
+    device addresses (ints); ``mask_ptr`` may be None."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(_lib.lb_totals_noalloc(prec, int(nx), int(ny), int(nz), f_ptr, psi_ptr, phi_ptr, mask_ptr,
+                                  sums_ptr, stream), "lb_totals_noalloc")
 
 
 def lb_device_bytes(params: LbParams) -> int:
