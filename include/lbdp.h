@@ -160,7 +160,7 @@ int lb_sync(lb_handle* h);
  * Synchronises. */
 int lb_read_fields(lb_handle* h, double* rho, double* u, double* psi, double* phi);
 
-/* Copy the chemical potentials mu_psi, mu_phi [N] computed in the last step
+/* Copy the chemical potentials mu_psi, mu_phi [N] of the current fields
  * (Eq. chem_potentials).  Synchronises. */
 int lb_read_mu(lb_handle* h, double* mu_psi, double* mu_phi);
 

@@ -868,8 +868,9 @@ int ref_read_fields(const ref_sim* s, double* rho, double* u, double* psi, doubl
     return 0;
 }
 
-int ref_read_mu(const ref_sim* s, double* mu_psi, double* mu_phi)
+int ref_read_mu(ref_sim* s, double* mu_psi, double* mu_phi)
 {
+    step_mu(s); /* chemical potentials of the current fields */
     if (mu_psi) memcpy(mu_psi, s->mupsi, (size_t)s->N * sizeof(double));
     if (mu_phi) memcpy(mu_phi, s->muphi, (size_t)s->N * sizeof(double));
     return 0;

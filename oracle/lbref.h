@@ -61,7 +61,7 @@ int  ref_add_particle(ref_sim* s, const ref_particle_desc* d);
 int  ref_step(ref_sim* s, int nsteps);
 int  ref_read_fields(const ref_sim* s, double* rho, double* u, double* psi,
                      double* phi);
-int  ref_read_mu(const ref_sim* s, double* mu_psi, double* mu_phi);
+int  ref_read_mu(ref_sim* s, double* mu_psi, double* mu_phi); /* of the current fields */
 int  ref_read_populations(const ref_sim* s, double* f);
 int  ref_read_mask(const ref_sim* s, unsigned char* mask);
 int  ref_read_particles(const ref_sim* s, ref_particle_state* out, int cap);

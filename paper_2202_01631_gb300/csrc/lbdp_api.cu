@@ -29,9 +29,11 @@ struct lb_handle {
     void* u;
     uint8_t* mask[2];
     DevPart* parts;
-    double* corr;
+    double* corr;   // [2] FP64 followed by [2] FP32 copies (corr_f)
     int* err;
     void* pt;
+    void* force;
+    uint8_t* bflag;
     double* link_part;
     unsigned* link_ticket;
     double* cover_part;
@@ -81,7 +83,7 @@ size_t state_bytes(const lb_params* p, const PrecOps* ops, int red_blocks)
     b += (4 + 2 + 3) * N * (size_t)ops->fld_bytes;     // psi, phi (x2), mu, u
     b += 2 * N;                                         // masks
     b += 6 * N * sizeof(double);                        // staging
-    b += 6 * N * (size_t)ops->fld_bytes;                // pressure tensor
+    b += 9 * N * (size_t)ops->fld_bytes + N;            // pressure tensor, force, boundary flags
     b += kMaxParticles * (sizeof(DevPart) + sizeof(unsigned));
     b += (size_t)kMaxParticles * kMaxPartBlocks * (kLinkK + kCoverK) * sizeof(double);
     b += (size_t)red_blocks * 3 * sizeof(double) + 64;
@@ -120,8 +122,11 @@ DevPtrs ptrs(const lb_handle* h, int src)
     d.mask_next = h->mask[dst];
     d.parts = h->parts;
     d.corr = h->corr;
+    d.corr_f = (float*)(h->corr + 2);
     d.err = h->err;
     d.pt = h->pt;
+    d.force = h->force;
+    d.bflag = h->bflag;
     d.link_part = h->link_part;
     d.link_ticket = h->link_ticket;
     d.cover_part = h->cover_part;
@@ -176,7 +181,7 @@ void free_all(lb_handle* h)
 {
     if (h->device >= 0) cudaSetDevice(h->device);
     void* ptrs_[] = {h->f[0], h->f[1], h->psi[0], h->psi[1], h->phi[0], h->phi[1], h->mupsi, h->muphi,
-                     h->u, h->mask[0], h->mask[1], h->parts, h->corr, h->err, h->pt, h->link_part,
+                     h->u, h->mask[0], h->mask[1], h->parts, h->corr, h->err, h->pt, h->force, h->bflag, h->link_part,
                      h->link_ticket, h->cover_part, h->cover_ticket, h->nfluid, h->staging, h->red_part, h->red_out, h->count};
     for (void* p : ptrs_)
         if (p) cudaFree(p);
@@ -255,6 +260,8 @@ int lb_create(const lb_params* p, lb_handle** out)
     P.E = p->E;
     P.phib = p->phi_b;
     P.kd = p->k_d;
+    fill_prm(P.pf, P);
+    fill_prm(P.pd, P);
     h->rmax = 0.0;
     update_sides(h);
     h->red_blocks = reduction_blocks(p);
@@ -279,9 +286,11 @@ int lb_create(const lb_params* p, lb_handle** out)
     if (e == cudaSuccess) e = cudaMalloc(&h->muphi, N * fb);
     if (e == cudaSuccess) e = cudaMalloc(&h->u, 3 * N * fb);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->parts, kMaxParticles * sizeof(DevPart));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->corr, 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->corr, 4 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->force, 3 * N * fb);
     if (e == cudaSuccess) e = cudaMalloc(&h->pt, 6 * N * fb);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->bflag, N);
     if (e == cudaSuccess)
         e = cudaMalloc((void**)&h->link_part, (size_t)kMaxParticles * kMaxPartBlocks * kLinkK * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->link_ticket, kMaxParticles * sizeof(unsigned));
@@ -304,11 +313,13 @@ int lb_create(const lb_params* p, lb_handle** out)
     long long nf = P.N;
     e = cudaMemsetAsync(h->mask[0], 0, N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->mask[1], 0, N, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->corr, 0, 2 * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->corr, 0, 4 * sizeof(double), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->link_ticket, 0, kMaxParticles * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->cover_ticket, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->force, 0, 3 * N * fb, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->pt, 0, 6 * N * fb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->bflag, 0, N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->u, 0, 3 * N * fb, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->mupsi, 0, N * fb, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->muphi, 0, N * fb, s);
@@ -361,7 +372,7 @@ int lb_set_fields(lb_handle* h, const double* rho, const double* u, const double
     // correction), populations to equilibrium; then the correction is spent
     LB_TRY(h->ops->set_fields(h->dp, cur_ptrs(h), s, rho ? st_rho : nullptr, u ? st_u : nullptr,
                               psi ? st_psi : nullptr, phi ? st_phi : nullptr));
-    LB_TRY(cudaMemsetAsync(h->corr, 0, 2 * sizeof(double), s));
+    LB_TRY(cudaMemsetAsync(h->corr, 0, 4 * sizeof(double), s));
     return LB_OK;
 }
 
@@ -432,6 +443,15 @@ int lb_add_particle(lb_handle* h, const lb_particle_desc* d, int* id_out)
     q.mu_p = d->mu_plus;
     q.mu_m = d->mu_minus;
     q.H = H;
+    q.Hk = H != 0.0 ? H / P.kappa : 0.0;
+    q.Hk_f = (float)q.Hk;
+    q.alpha_f = (float)q.alpha;
+    q.mu_pf = (float)q.mu_p;
+    q.mu_mf = (float)q.mu_m;
+    for (int a = 0; a < 3; ++a) {
+        q.Uf[a] = (float)q.U[a];
+        q.Wf[a] = (float)q.W[a];
+    }
     q.fixed = d->fixed ? 1 : 0;
     const int k = (int)h->host_parts.size();
     // fetch the device copies first: earlier particles have moved
@@ -446,6 +466,7 @@ int lb_add_particle(lb_handle* h, const lb_particle_desc* d, int* id_out)
     unsigned long long zero = 0, cnt = 0;
     LB_TRY(cudaMemcpyAsync(h->count, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->stream));
     LB_TRY(launch_claim(P, h->mask[h->cur], h->mask[h->cur ^ 1], h->parts, k, h->count, h->stream));
+    LB_TRY(launch_bflag(P, h->mask[h->cur], h->bflag, h->stream));
     long long nf = 0;
     LB_TRY(cudaMemcpyAsync(&cnt, h->count, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
     LB_TRY(cudaMemcpyAsync(&nf, h->nfluid, sizeof(nf), cudaMemcpyDeviceToHost, h->stream));
@@ -497,14 +518,14 @@ int lb_profile_step(lb_handle* h, int nsteps, double* ms, int* launches)
             ms[k] += v;
         }
     for (auto& e : ev) cudaEventDestroy(e);
-    if (launches) *launches = nsteps * (h->dp.np > 0 ? 6 : 3);
+    if (launches) *launches = nsteps * (h->dp.np > 0 ? 7 : 4);
     return st;
 }
 
 int lb_step_launches(const lb_handle* h, int nsteps)
 {
     if (!h || nsteps < 0) return LB_ERR_PARAM;
-    return nsteps * (h->dp.np > 0 ? 6 : 3);
+    return nsteps * (h->dp.np > 0 ? 7 : 4);
 }
 
 int lb_sync(lb_handle* h)
@@ -626,6 +647,14 @@ const char* lb_error_string(int status)
 }  // extern "C"
 
 namespace lbdp {
+cudaError_t launch_bflag(const DevParams& P, const uint8_t* mask, uint8_t* bflag, cudaStream_t s)
+{
+    long long b = (P.N + 255) / 256;
+    int blocks = (int)(b < 152 * 16 ? b : 152 * 16);
+    k_bflag_all<<<blocks, 256, 0, s>>>(P, mask, bflag);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_claim(const DevParams& P, uint8_t* m0, uint8_t* m1, const DevPart* parts, int p,
                          unsigned long long* count, cudaStream_t s)
 {

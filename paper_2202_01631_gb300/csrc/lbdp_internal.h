@@ -41,6 +41,7 @@ extern const PrecOps kOpsF32;
 extern const PrecOps kOpsF16;
 extern const PrecOps kOpsBF16;
 
+cudaError_t launch_bflag(const DevParams& P, const uint8_t* mask, uint8_t* bflag, cudaStream_t s);
 cudaError_t launch_claim(const DevParams& P, uint8_t* m0, uint8_t* m1, const DevPart* parts, int p,
                          unsigned long long* count, cudaStream_t s);
 

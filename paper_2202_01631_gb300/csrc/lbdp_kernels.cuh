@@ -1,20 +1,31 @@
 // lbdp_kernels.cuh -- the per-step kernels of the lattice update, templated on
 // the precision configuration.  One step is
-//   k_mu           chemical potentials (Eq. chem_potentials) with wetting
-//                  ghosts, and the chemical pressure tensor P of Eq. free_energy
+//   k_force        tiled: psi, phi staged in shared memory with a two-node
+//                  halo; chemical potentials (Eq. chem_potentials, wetting
+//                  ghosts) and pressure tensor P (Eq. free_energy) on the tile
+//                  plus one node; force F = g - div P on the tile
 //   k_links        per particle: bounce-back and chemical-stress momentum sums
 //                  over its boundary links, implicit velocity update, new
 //                  position and orientation (Sec. "Particles")
-//   k_collide      force g - div P, D3Q19 pull streaming with halfway
-//                  bounce-back on walls and moving bounce-back plus phoretic
-//                  slip on particle links, BGK + Guo
-//   k_scalars      conservative psi/phi transport (Eq. diffusion_reaction),
-//                  Janus production (Eq. activity) and the k_d sink
+//   k_collide      D3Q19 pull streaming, halfway bounce-back on walls, moving
+//                  bounce-back plus phoretic slip on particle links, BGK + Guo
+//                  with F; nodes away from walls and particles take a
+//                  branch-free path
+//   k_scalars      tiled: psi/phi transport (Eq. diffusion_reaction) with mu
+//                  recomputed in shared memory, Janus production (Eq. activity)
+//                  and the k_d sink
 //   k_cover_mark   per particle: solid mask at the new positions
-//   k_cover_apply  per particle: covering/uncovering; the last block folds
-//                  the psi/phi deficits into the uniform correction and moves
-//                  the particles
+//   k_cover_apply  per particle: covering/uncovering and boundary flags; the
+//                  last block folds the psi/phi deficits into the uniform
+//                  correction and moves the particles
 // Every kernel is HBM-bound stencil or streaming work: no tensor cores.
+//
+// Precision: node and link arithmetic runs in the mode's real type R.  FP64
+// is kept where the method needs it in every mode -- the solid/fluid and
+// active-cap decisions (exact, unfused products and sums, as in the CPU
+// oracle), the force/torque/conservation sums and the particle solve -- and
+// nowhere else, because GB300 executes FP64 (and FP64 conversions) on a narrow
+// pipe.
 #pragma once
 
 #include "lbdp_lattice.cuh"
@@ -35,50 +46,148 @@ using CfgBF16 = Cfg<__nv_bfloat16, float, float>;
 constexpr int kRowThreads = 128;
 constexpr int kPartThreads = 256;
 
+// Tiles of the shared-memory stencil kernels: TX x TY x TZ output nodes, a
+// two-node halo for psi/phi (the pressure tensor of a halo node needs the
+// Laplacian of psi there), a one-node halo for mu, P and u.
+constexpr int TX = 32, TY = 4, TZ = 4;
+constexpr int H2X = TX + 4, H2Y = TY + 4, H2Z = TZ + 4;
+constexpr int H1X = TX + 2, H1Y = TY + 2, H1Z = TZ + 2;
+constexpr int kN2 = H2X * H2Y * H2Z;   // 2304 slots
+constexpr int kN1 = H1X * H1Y * H1Z;   // 1224 slots
+constexpr int kNT = TX * TY * TZ;      // 512 nodes
+constexpr int kTileThreads = 256;
+constexpr uint8_t kWallSlot = 0xFF;    // slot beyond a non-periodic wall
+
+__host__ __device__ constexpr int off2(int i) { return cx(i) + H2X * (cy(i) + H2Y * cz(i)); }
+__host__ __device__ constexpr int off1(int i) { return cx(i) + H1X * (cy(i) + H1Y * cz(i)); }
+
+template <class R>
+__host__ __device__ constexpr size_t tile_smem_force()
+{
+    return (size_t)kN2 * (2 * sizeof(R) + 1) + (size_t)kN1 * 6 * sizeof(R) + 64;
+}
+template <class R>
+__host__ __device__ constexpr size_t tile_smem_scalars()
+{
+    return (size_t)kN2 * (2 * sizeof(R) + 1) + (size_t)kN1 * 5 * sizeof(R) + 64;
+}
+
+// ---------------------------------------------------------------------------
+// precision accessors
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ R corr_r(const DevPtrs& D, int k);
+template <>
+__device__ __forceinline__ float corr_r<float>(const DevPtrs& D, int k) { return D.corr_f[k]; }
+template <>
+__device__ __forceinline__ double corr_r<double>(const DevPtrs& D, int k) { return D.corr[k]; }
+
+template <class R>
+struct PartR;
+template <>
+struct PartR<float> {
+    static __device__ __forceinline__ float U(const DevPart& q, int a) { return q.Uf[a]; }
+    static __device__ __forceinline__ float W(const DevPart& q, int a) { return q.Wf[a]; }
+    static __device__ __forceinline__ float mu_m(const DevPart& q) { return q.mu_mf; }
+    static __device__ __forceinline__ float mu_p(const DevPart& q) { return q.mu_pf; }
+    static __device__ __forceinline__ float Hk(const DevPart& q) { return q.Hk_f; }
+    static __device__ __forceinline__ float alpha(const DevPart& q) { return q.alpha_f; }
+};
+template <>
+struct PartR<double> {
+    static __device__ __forceinline__ double U(const DevPart& q, int a) { return q.U[a]; }
+    static __device__ __forceinline__ double W(const DevPart& q, int a) { return q.W[a]; }
+    static __device__ __forceinline__ double mu_m(const DevPart& q) { return q.mu_m; }
+    static __device__ __forceinline__ double mu_p(const DevPart& q) { return q.mu_p; }
+    static __device__ __forceinline__ double Hk(const DevPart& q) { return q.Hk; }
+    static __device__ __forceinline__ double alpha(const DevPart& q) { return q.alpha; }
+};
+
 // ---------------------------------------------------------------------------
 // shared device helpers
 // ---------------------------------------------------------------------------
 
 // Isotropic gradient of phi at a fluid node, 3 sum_i w_i c_i phi(x+c_i), with
 // the node's own value standing in for solid and wall neighbours.
-template <class Fld>
-__device__ __forceinline__ void grad_phi_at(const int nb[19], const Fld* phi, const uint8_t* mask, double own,
-                                            double dphi, double g[3])
+template <class R, class Fld>
+__device__ __forceinline__ void grad_phi_at(const int nb[19], const Fld* phi, const uint8_t* mask, R own, R dphi,
+                                            R g[3])
 {
-    g[0] = g[1] = g[2] = 0.0;
+    g[0] = g[1] = g[2] = (R)0;
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
         int m = nb[i];
-        double v = (m < 0 || mask[m]) ? own : (double)phi[m] + dphi;
-        g[0] += wgt(i) * cx(i) * v;
-        g[1] += wgt(i) * cy(i) * v;
-        g[2] += wgt(i) * cz(i) * v;
+        R v = (m < 0 || mask[m]) ? own : (R)phi[m] + dphi;
+        g[0] += wgt_r<R>(i) * (R)cx(i) * v;
+        g[1] += wgt_r<R>(i) * (R)cy(i) * v;
+        g[2] += wgt_r<R>(i) * (R)cz(i) * v;
     }
-    g[0] *= 3.0;
-    g[1] *= 3.0;
-    g[2] *= 3.0;
+    g[0] *= (R)3;
+    g[1] *= (R)3;
+    g[2] *= (R)3;
 }
 
-// Boundary velocity at the midpoint of link x -> x + c_i of particle q:
-// u_b = U + Omega x r + v_s, v_s = mu (1 - n n) . grad phi, mu = mu_- where
-// m.r <= 0 else mu_+ (Eq. MuJ).  Returns r (midpoint offset), u_b and v_s.
-__device__ __forceinline__ void link_velocity(const DevParams& P, const DevPart& q, int x, int y, int z, int i,
-                                              const double gphi[3], double r[3], double ub[3], double vs[3])
+// Midpoint offset r_b = (x - X) + c_i/2 of link x -> x + c_i (FP64, exact
+// roundings) and the side of the Janus cap, m.r_b <= 0.
+__device__ __forceinline__ void link_offset(const DevParams& P, const DevPart& q, int x, int y, int z, int i,
+                                            double r[3])
 {
     node_offset(P, q, x, y, z, r);
     r[0] = __dadd_rn(r[0], 0.5 * cx(i));
     r[1] = __dadd_rn(r[1], 0.5 * cy(i));
     r[2] = __dadd_rn(r[2], 0.5 * cz(i));
-    double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-    double nh[3] = {r[0] / rn, r[1] / rn, r[2] / rn};
-    double side = dot3_rn(q.m, r);
-    double mu = (side <= 0.0) ? q.mu_m : q.mu_p;
-    double ng = nh[0] * gphi[0] + nh[1] * gphi[1] + nh[2] * gphi[2];
+}
+
+// Boundary velocity at the midpoint of link x -> x + c_i of particle q:
+// u_b = U + Omega x r + v_s, v_s = mu (1 - n n) . grad phi, mu = mu_- where
+// m.r <= 0 else mu_+ (Eq. MuJ).  Returns r (midpoint offset), u_b and v_s.
+template <class R>
+__device__ __forceinline__ void link_velocity(const DevParams& P, const DevPart& q, int x, int y, int z, int i,
+                                              const R gphi[3], R r[3], R ub[3], R vs[3])
+{
+    double rd[3];
+    link_offset(P, q, x, y, z, i, rd);
+    const double side = dot3_rn(q.m, rd);
+    const R mu = (side <= 0.0) ? PartR<R>::mu_m(q) : PartR<R>::mu_p(q);
+    r[0] = (R)rd[0];
+    r[1] = (R)rd[1];
+    r[2] = (R)rd[2];
+    const R rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    const R nh[3] = {r[0] / rn, r[1] / rn, r[2] / rn};
+    const R ng = nh[0] * gphi[0] + nh[1] * gphi[1] + nh[2] * gphi[2];
 #pragma unroll
     for (int a = 0; a < 3; ++a) vs[a] = mu * (gphi[a] - nh[a] * ng);
-    ub[0] = q.U[0] + (q.W[1] * r[2] - q.W[2] * r[1]) + vs[0];
-    ub[1] = q.U[1] + (q.W[2] * r[0] - q.W[0] * r[2]) + vs[1];
-    ub[2] = q.U[2] + (q.W[0] * r[1] - q.W[1] * r[0]) + vs[2];
+    const R U0 = PartR<R>::U(q, 0), U1 = PartR<R>::U(q, 1), U2 = PartR<R>::U(q, 2);
+    const R W0 = PartR<R>::W(q, 0), W1 = PartR<R>::W(q, 1), W2 = PartR<R>::W(q, 2);
+    ub[0] = U0 + (W1 * r[2] - W2 * r[1]) + vs[0];
+    ub[1] = U1 + (W2 * r[0] - W0 * r[2]) + vs[1];
+    ub[2] = U2 + (W0 * r[1] - W1 * r[0]) + vs[2];
+}
+
+// Wetting ghost of psi at the solid neighbour x + c_i of fluid node x:
+// psi(x) + (H/kappa) c_i . n_hat at the link midpoint.
+template <class R>
+__device__ __forceinline__ R psi_ghost(const DevParams& P, const DevPart& q, int x, int y, int z, int i, R ps)
+{
+    if (q.H == 0.0) return ps;
+    double rd[3];
+    link_offset(P, q, x, y, z, i, rd);
+    const R r0 = (R)rd[0], r1 = (R)rd[1], r2 = (R)rd[2];
+    const R rn = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+    const R cn = ((R)cx(i) * r0 + (R)cy(i) * r1 + (R)cz(i) * r2) / rn;
+    return ps + PartR<R>::Hk(q) * cn;
+}
+
+// c_i . (a, b, c) with the zero components of c_i dropped at compile time
+// once the direction loop is unrolled (x + (-0) folds to x; a product with 0
+// could not be removed because of NaN and signed-zero rules).
+template <class R>
+__device__ __forceinline__ R cdot(int i, R a, R b, R c)
+{
+    const R ta = cx(i) == 0 ? (R)-0.0 : (cx(i) > 0 ? a : -a);
+    const R tb = cy(i) == 0 ? (R)-0.0 : (cy(i) > 0 ? b : -b);
+    const R tc = cz(i) == 0 ? (R)-0.0 : (cz(i) > 0 ? c : -c);
+    return ta + tb + tc;
 }
 
 template <class Real>
@@ -86,24 +195,71 @@ __device__ __forceinline__ Real feq_i(int i, Real rho, Real ux, Real uy, Real uz
 {
     Real cu = (Real)cx(i) * ux + (Real)cy(i) * uy + (Real)cz(i) * uz;
     Real uu = ux * ux + uy * uy + uz * uz;
-    return (Real)wgt(i) * rho * ((Real)1 + (Real)3 * cu + (Real)4.5 * cu * cu - (Real)1.5 * uu);
+    return wgt_r<Real>(i) * rho * ((Real)1 + (Real)3 * cu + (Real)4.5 * cu * cu - (Real)1.5 * uu);
 }
 
 __device__ __forceinline__ float tanh_r(float v) { return tanhf(v); }
 __device__ __forceinline__ double tanh_r(double v) { return tanh(v); }
-__device__ __forceinline__ float cosh_r(float v) { return coshf(v); }
-__device__ __forceinline__ double cosh_r(double v) { return cosh(v); }
 
-// P(n) . c_i from the six stored components (xx yy zz xy xz yz).
-template <class F, class R>
-__device__ __forceinline__ void pt_dot(const F* pt, size_t N, int n, int i, R out[3])
+// Chemical potentials and (optionally) the pressure tensor at one fluid node
+// from v[0] = psi(x) and v[i] = psi at neighbour i (ghost-resolved), ph = phi(x):
+//   mu_psi = A(psi^3 - psi) - kappa lap psi - C E (phi - phi0)/cosh^2 psi,
+//   mu_phi = C (phi - phi0),  phi0 = phi_b + E tanh psi          (Eq. chem_potentials)
+//   P = [psi mu_psi + phi mu_phi - f - kappa |grad psi|^2/2] I + kappa grad psi grad psi,
+//   f = A psi^4/4 - A psi^2/2 + C (phi - phi0)^2/2.               (Eq. free_energy)
+// 1/cosh^2 is taken as 1 - tanh^2.  P is returned as xx yy zz xy xz yz.
+template <class R>
+__device__ __forceinline__ void mu_pressure(const PrmR<R>& Q, const R v[19], R ph, bool want_p, R& mps, R& mph,
+                                            R pt[6])
 {
-    const R xx = (R)pt[n], yy = (R)pt[N + n], zz = (R)pt[2 * N + n];
-    const R xy = (R)pt[3 * N + n], xz = (R)pt[4 * N + n], yz = (R)pt[5 * N + n];
-    const R c0 = (R)cx(i), c1 = (R)cy(i), c2 = (R)cz(i);
-    out[0] = xx * c0 + xy * c1 + xz * c2;
-    out[1] = xy * c0 + yy * c1 + yz * c2;
-    out[2] = xz * c0 + yz * c1 + zz * c2;
+    const R ps = v[0];
+    R lap = 0, g0 = 0, g1 = 0, g2 = 0;
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        const R w = wgt_r<R>(i);
+        const R wv = w * v[i];
+        lap += w * (v[i] - ps);
+        if (cx(i) != 0) g0 += cx(i) > 0 ? wv : -wv;
+        if (cy(i) != 0) g1 += cy(i) > 0 ? wv : -wv;
+        if (cz(i) != 0) g2 += cz(i) > 0 ? wv : -wv;
+    }
+    lap *= (R)6;
+    g0 *= (R)3;
+    g1 *= (R)3;
+    g2 *= (R)3;
+    const R th = tanh_r(ps);
+    const R dphi = ph - (Q.phib + Q.E * th);
+    mph = Q.C * dphi;
+    mps = Q.A * (ps * ps * ps - ps) - Q.kappa * lap - Q.C * Q.E * dphi * ((R)1 - th * th);
+    if (!want_p) return;
+    const R f = (R)0.25 * Q.A * ps * ps * ps * ps - (R)0.5 * Q.A * ps * ps + (R)0.5 * Q.C * dphi * dphi;
+    const R gg = g0 * g0 + g1 * g1 + g2 * g2;
+    const R piso = ps * mps + ph * mph - f - (R)0.5 * Q.kappa * gg;
+    pt[0] = piso + Q.kappa * g0 * g0;
+    pt[1] = piso + Q.kappa * g1 * g1;
+    pt[2] = piso + Q.kappa * g2 * g2;
+    pt[3] = Q.kappa * g0 * g1;
+    pt[4] = Q.kappa * g0 * g2;
+    pt[5] = Q.kappa * g1 * g2;
+}
+
+// Gather the 19 ghost-resolved psi values of fluid node n from global memory.
+template <class R, class F>
+__device__ __forceinline__ void gather_psi(const DevParams& P, const DevPtrs& D, const F* psi, int x, int y, int z,
+                                           const int nb[19], R v[19])
+{
+    const R dps = corr_r<R>(D, 0);
+    v[0] = (R)psi[nb[0]] + dps;
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        const int m = nb[i];
+        if (m < 0) {
+            v[i] = v[0];
+        } else {
+            const uint8_t q = D.mask[m];
+            v[i] = q ? psi_ghost<R>(P, D.parts[q - 1], x, y, z, i, v[0]) : (R)psi[m] + dps;
+        }
+    }
 }
 
 // FP64 block reduction: sums K values per thread over the block in a fixed
@@ -121,46 +277,60 @@ __device__ void block_sum(double (&v)[K], double* smem /* [32*K] */)
     if (lane == 0)
         for (int k = 0; k < K; ++k) smem[warp * K + k] = v[k];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < K; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += smem[w * K + k];
-            v[k] = s;
-        }
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += smem[w * K + threadIdx.x];
+        smem[32 * K - K + threadIdx.x] = s;
     }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < K; ++k) v[k] = smem[32 * K - K + k];
     __syncthreads();
 }
 
-// Gaussian elimination with partial pivoting, 6x6 (single thread).
-__device__ inline int solve6(double A[6][6], double b[6], double x[6])
+// FP64 block reduction through shared memory: each warp transposes its K x 32
+// values so that lane k adds column k (warps holding only zeros skip it), then
+// K threads add the warp results in warp order.  The order is fixed, so the
+// result is deterministic; it is valid in thread 0.  sm holds
+// (32 + 1) * K * (blockDim.x / 32) doubles.
+template <int K>
+__device__ void block_sum_t(double (&v)[K], double* sm)
 {
-    for (int c = 0; c < 6; ++c) {
-        int piv = c;
-        for (int r = c + 1; r < 6; ++r)
-            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
-        if (A[piv][c] == 0.0) return -1;
-        if (piv != c) {
-            for (int k = 0; k < 6; ++k) {
-                double t = A[c][k];
-                A[c][k] = A[piv][k];
-                A[piv][k] = t;
-            }
-            double t = b[c];
-            b[c] = b[piv];
-            b[piv] = t;
-        }
-        for (int r = c + 1; r < 6; ++r) {
-            double l = A[r][c] / A[c][c];
-            for (int k = c; k < 6; ++k) A[r][k] -= l * A[c][k];
-            b[r] -= l * b[c];
-        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    bool nz = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) nz = nz || (v[k] != 0.0);
+    const bool any = __any_sync(0xffffffffu, nz);
+    double* wbuf = sm + (size_t)warp * 32 * K;
+    double* wres = sm + (size_t)nw * 32 * K;
+    if (any) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) wbuf[lane * K + k] = v[k];
     }
-    for (int r = 5; r >= 0; --r) {
-        double acc = b[r];
-        for (int k = r + 1; k < 6; ++k) acc -= A[r][k] * x[k];
-        x[r] = acc / A[r][r];
+    __syncwarp();
+    if (lane < K) {
+        double s = 0.0;
+        if (any)
+            for (int l = 0; l < 32; ++l) s += wbuf[l * K + lane];
+        wres[warp * K + lane] = s;
     }
-    return 0;
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += wres[w * K + threadIdx.x];
+        sm[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = sm[k];
+    __syncthreads();
+}
+
+template <int K>
+__host__ __device__ constexpr size_t block_sum_t_bytes(int threads)
+{
+    return (size_t)(32 + 1) * K * (threads / 32) * sizeof(double);
 }
 
 // Lattice node of slot t in a box of edges s[3] starting at o[3]; false when
@@ -174,11 +344,62 @@ __device__ __forceinline__ bool box_node(const DevParams& P, const int o[3], con
     return x >= 0 && y >= 0 && z >= 0;
 }
 
+// Stage psi, phi (with the uniform correction) and the mask of the tile plus a
+// two-node halo into shared memory; solid and wall slots hold 0.
+template <class R, class F>
+__device__ __forceinline__ void stage_tile(const DevParams& P, const DevPtrs& D, int bx0, int by0, int bz0, R* s_psi,
+                                           R* s_phi, uint8_t* s_mask)
+{
+    const F* psi = (const F*)D.psi_src;
+    const F* phi = (const F*)D.phi_src;
+    const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
+    for (int s = threadIdx.x; s < kN2; s += blockDim.x) {
+        const int lx = s % H2X - 2, ly = (s / H2X) % H2Y - 2, lz = s / (H2X * H2Y) - 2;
+        const int gx = wrap_coord(bx0 + lx, P.nx, P.per[0]);
+        const int gy = wrap_coord(by0 + ly, P.ny, P.per[1]);
+        const int gz = wrap_coord(bz0 + lz, P.nz, P.per[2]);
+        uint8_t mk = kWallSlot;
+        R a = 0, b = 0;
+        if (gx >= 0 && gy >= 0 && gz >= 0) {
+            const int n = gx + P.nx * (gy + P.ny * gz);
+            mk = D.mask[n];
+            if (!mk) {
+                a = (R)psi[n] + dps;
+                b = (R)phi[n] + dph;
+            }
+        }
+        s_mask[s] = mk;
+        s_psi[s] = a;
+        s_phi[s] = b;
+    }
+}
+
+// Ghost-resolved psi values around slot s (fluid) of the staged tile.
+template <class R>
+__device__ __forceinline__ void gather_psi_tile(const DevParams& P, const DevPtrs& D, const R* s_psi,
+                                                const uint8_t* s_mask, int s, int gx, int gy, int gz, R v[19])
+{
+    v[0] = s_psi[s];
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        const int t = s + off2(i);
+        const uint8_t mk = s_mask[t];
+        if (mk == 0)
+            v[i] = s_psi[t];
+        else if (mk == kWallSlot)
+            v[i] = v[0];
+        else
+            v[i] = psi_ghost<R>(P, D.parts[mk - 1], gx, gy, gz, i, v[0]);
+    }
+}
+
 // ---------------------------------------------------------------------------
-// S1: chemical potentials and pressure tensor
+// S1: chemical potentials and pressure tensor, one thread per node.  Every
+// neighbour load is issued before any decision (walls clamp to the node
+// itself), so the loads overlap instead of waiting behind mask branches.
 // ---------------------------------------------------------------------------
 template <class C>
-__global__ void __launch_bounds__(kRowThreads) k_mu(DevParams P, DevPtrs D)
+__global__ void __launch_bounds__(kRowThreads) k_mup(DevParams P, DevPtrs D)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
@@ -187,69 +408,87 @@ __global__ void __launch_bounds__(kRowThreads) k_mu(DevParams P, DevPtrs D)
     if (x >= P.nx) return;
     const int n = x + P.nx * (y + P.ny * z);
     if (D.mask[n]) return;
+    const PrmR<R>& Q = prm<R>(P);
     const size_t N = (size_t)P.N;
     const F* psi = (const F*)D.psi_src;
     const F* phi = (const F*)D.phi_src;
-    const R dps = (R)D.corr[0], dph = (R)D.corr[1];
-    const R ps = (R)psi[n] + dps, ph = (R)phi[n] + dph;
+    const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
     int nb[19];
     neighbours(P, x, y, z, nb);
-    R lap = 0, g0 = 0, g1 = 0, g2 = 0;
+    R v[19];
+    uint8_t mk[19];
+    v[0] = (R)psi[n] + dps;
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-        const int m = nb[i];
-        R v;
-        if (m < 0) {
-            v = ps;
-        } else {
-            const uint8_t q = D.mask[m];
-            if (q) {
-                // wetting ghost psi(x) + (H/kappa) c_i . n_hat at the link midpoint
-                const DevPart& pq = D.parts[q - 1];
-                if (pq.H != 0.0) {
-                    double r[3];
-                    node_offset(P, pq, x, y, z, r);
-                    r[0] = __dadd_rn(r[0], 0.5 * cx(i));
-                    r[1] = __dadd_rn(r[1], 0.5 * cy(i));
-                    r[2] = __dadd_rn(r[2], 0.5 * cz(i));
-                    double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-                    double cn = (cx(i) * r[0] + cy(i) * r[1] + cz(i) * r[2]) / rn;
-                    v = ps + (R)((pq.H / P.kappa) * cn);
-                } else {
-                    v = ps;
-                }
-            } else {
-                v = (R)psi[m] + dps;
-            }
-        }
-        const R w = (R)wgt(i);
-        lap += w * (v - ps);
-        g0 += w * (R)cx(i) * v;
-        g1 += w * (R)cy(i) * v;
-        g2 += w * (R)cz(i) * v;
+        const int m = nb[i] >= 0 ? nb[i] : n;
+        mk[i] = nb[i] >= 0 ? D.mask[m] : kWallSlot;
+        v[i] = (R)psi[m] + dps;
     }
-    lap *= (R)6;
-    g0 *= (R)3;
-    g1 *= (R)3;
-    g2 *= (R)3;
-    const R A = (R)P.A, Cc = (R)P.C, kap = (R)P.kappa;
-    const R dphi = ph - ((R)P.phib + (R)P.E * tanh_r(ps));
-    const R ch = cosh_r(ps);
-    const R mph = Cc * dphi;
-    const R mps = A * (ps * ps * ps - ps) - kap * lap - Cc * (R)P.E * dphi / (ch * ch);
-    ((F*)D.muphi)[n] = (F)mph;
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        if (mk[i] == kWallSlot)
+            v[i] = v[0];
+        else if (mk[i])
+            v[i] = psi_ghost<R>(P, D.parts[mk[i] - 1], x, y, z, i, v[0]);
+    }
+    R mps, mph, pt[6];
+    mu_pressure<R>(Q, v, (R)phi[n] + dph, P.thermo != 0, mps, mph, pt);
     ((F*)D.mupsi)[n] = (F)mps;
-    // P = [psi mu_psi + phi mu_phi - f - kappa |grad psi|^2/2] I + kappa grad psi grad psi
-    const R f = (R)0.25 * A * ps * ps * ps * ps - (R)0.5 * A * ps * ps + (R)0.5 * Cc * dphi * dphi;
-    const R gg = g0 * g0 + g1 * g1 + g2 * g2;
-    const R piso = ps * mps + ph * mph - f - (R)0.5 * kap * gg;
-    F* pt = (F*)D.pt;
-    pt[n] = (F)(piso + kap * g0 * g0);
-    pt[N + n] = (F)(piso + kap * g1 * g1);
-    pt[2 * N + n] = (F)(piso + kap * g2 * g2);
-    pt[3 * N + n] = (F)(kap * g0 * g1);
-    pt[4 * N + n] = (F)(kap * g0 * g2);
-    pt[5 * N + n] = (F)(kap * g1 * g2);
+    ((F*)D.muphi)[n] = (F)mph;
+    if (P.thermo) {
+        F* ptg = (F*)D.pt;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ptg[k * N + n] = (F)pt[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// S2: force on the fluid, F = g - div P in the link form
+//   -6 sum_i w_i [(P(x) + P~_i)/2] . c_i = -3 sum_i w_i P~_i . c_i
+// (sum_i w_i c_i = 0), with P~_i = P(x) at solid and wall neighbours.
+// ---------------------------------------------------------------------------
+template <class C>
+__global__ void __launch_bounds__(kRowThreads) k_fdiv(DevParams P, DevPtrs D)
+{
+    using R = typename C::real;
+    using F = typename C::fld_t;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= P.nx) return;
+    const int n = x + P.nx * (y + P.ny * z);
+    if (D.mask[n]) return;
+    const PrmR<R>& Q = prm<R>(P);
+    const size_t N = (size_t)P.N;
+    R Fx = Q.g[0], Fy = Q.g[1], Fz = Q.g[2];
+    if (P.thermo) {
+        const F* pt = (const F*)D.pt;
+        int nb[19];
+        neighbours(P, x, y, z, nb);
+        const R o0 = (R)pt[n], o1 = (R)pt[N + n], o2 = (R)pt[2 * N + n];
+        const R o3 = (R)pt[3 * N + n], o4 = (R)pt[4 * N + n], o5 = (R)pt[5 * N + n];
+        R d0 = 0, d1 = 0, d2 = 0;
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const int m = nb[i] >= 0 ? nb[i] : n;
+            const bool own = nb[i] < 0 || D.mask[m];
+            // components multiplied by a zero velocity component are never
+            // loaded (the unrolled cdot drops them)
+            const R xx = own ? o0 : (R)pt[m], yy = own ? o1 : (R)pt[N + m], zz = own ? o2 : (R)pt[2 * N + m];
+            const R xy = own ? o3 : (R)pt[3 * N + m], xz = own ? o4 : (R)pt[4 * N + m];
+            const R yz = own ? o5 : (R)pt[5 * N + m];
+            const R w = wgt_r<R>(i);
+            d0 += w * cdot<R>(i, xx, xy, xz);
+            d1 += w * cdot<R>(i, xy, yy, yz);
+            d2 += w * cdot<R>(i, xz, yz, zz);
+        }
+        Fx -= (R)3 * d0;
+        Fy -= (R)3 * d1;
+        Fz -= (R)3 * d2;
+    }
+    F* force = (F*)D.force;
+    force[n] = (F)Fx;
+    force[N + n] = (F)Fy;
+    force[2 * N + n] = (F)Fz;
 }
 
 // ---------------------------------------------------------------------------
@@ -257,32 +496,36 @@ __global__ void __launch_bounds__(kRowThreads) k_mu(DevParams P, DevPtrs D)
 // blocks of a particle split its link box; the last block of the particle (a
 // ticket counter) sums the partials in block order and solves
 //   (Mdiag + zeta) V(t+1) = Mdiag V(t) + [F0; T0]
-// then stores the new velocity and the position/orientation after the step.
+// (symmetric positive definite: Cholesky), then stores the new velocity and
+// the position/orientation after the step.
 // ---------------------------------------------------------------------------
 template <class C>
-__global__ void __launch_bounds__(kPartThreads) k_links(DevParams P, DevPtrs D)
+__global__ void __launch_bounds__(kPartThreads, 1) k_links(DevParams P, DevPtrs D)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
     using S = typename C::pop_t;
     constexpr int K = kLinkK;
-    __shared__ double smem[32 * K];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* smem = (double*)smem_raw;   // block_sum_t_bytes<K>(kPartThreads)
     __shared__ DevPart sp;
     __shared__ bool last;
     const int p = blockIdx.y;
     if (threadIdx.x == 0) sp = D.parts[p];
     __syncthreads();
     const DevPart& q = sp;
+    const PrmR<R>& Q = prm<R>(P);
     const size_t N = (size_t)P.N;
     const S* fs = (const S*)D.f_src;
+    const F* psi = (const F*)D.psi_src;
     const F* phi = (const F*)D.phi_src;
-    const F* pt = (const F*)D.pt;
+    const R dph = corr_r<R>(D, 1);
     const int o[3] = {(int)floor(q.X[0] - q.R) - 2, (int)floor(q.X[1] - q.R) - 2, (int)floor(q.X[2] - q.R) - 2};
     const int tot = P.side1[0] * P.side1[1] * P.side1[2];
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
-    const double zc0 = 6.0 * P.rho0;
+    const R zc0 = (R)6 * Q.rho0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
         int x, y, z;
         if (!box_node(P, o, P.side1, t, x, y, z)) continue;
@@ -290,46 +533,67 @@ __global__ void __launch_bounds__(kPartThreads) k_links(DevParams P, DevPtrs D)
         if (D.mask[n]) continue;
         int nb[19];
         neighbours(P, x, y, z, nb);
-        bool have_g = false;
-        double gphi[3] = {0.0, 0.0, 0.0};
+        // issue every mask load before deciding anything
+        bool lk[19];
+        bool have = false;
+#pragma unroll
         for (int i = 1; i < 19; ++i) {
-            const int m = nb[i];
-            if (m < 0 || D.mask[m] != p + 1) continue;
-            if (!have_g) {
-                grad_phi_at(nb, phi, D.mask, (double)phi[n] + D.corr[1], D.corr[1], gphi);
-                have_g = true;
-            }
-            double r[3], ub[3], vs[3];
-            link_velocity(P, q, x, y, z, i, gphi, r, ub, vs);
-            const double fi = (double)PopStore<S>::load(fs, (size_t)i * N + n, i, (R)P.rho0);
-            const double w = wgt(i);
-            const double c[3] = {(double)cx(i), (double)cy(i), (double)cz(i)};
-            const double cvs = c[0] * vs[0] + c[1] * vs[1] + c[2] * vs[2];
-            const double mag = 2.0 * fi - 6.0 * w * P.rho0 * cvs;
-            double dP[3] = {c[0] * mag, c[1] * mag, c[2] * mag};
+            lk[i] = nb[i] >= 0 && D.mask[nb[i] >= 0 ? nb[i] : n] == p + 1;
+            have = have || lk[i];
+        }
+        if (!have) continue;
+        // this node has links into particle p: load everything it needs at once
+        R fv[19];
+#pragma unroll
+        for (int i = 1; i < 19; ++i) fv[i] = (R)PopStore<S>::load(fs, (size_t)i * N + n, i, Q.rho0);
+        R gphi[3];
+        grad_phi_at<R, F>(nb, phi, D.mask, (R)phi[n] + dph, dph, gphi);
+        R pt[6] = {0, 0, 0, 0, 0, 0};
+        if (P.thermo) {
+            // the pressure tensor the fluid's force used this step
+            const F* ptg = (const F*)D.pt;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) pt[k] = (R)ptg[k * N + n];
+        }
+        R nacc[K];   // this node's links, added to the FP64 sums once
+#pragma unroll
+        for (int k = 0; k < K; ++k) nacc[k] = (R)0;
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            if (!lk[i]) continue;
+            R r[3], ub[3], vs[3];
+            link_velocity<R>(P, q, x, y, z, i, gphi, r, ub, vs);
+            const R fi = fv[i];
+            const R w = wgt_r<R>(i);
+            const R c[3] = {(R)cx(i), (R)cy(i), (R)cz(i)};
+            const R cvs = c[0] * vs[0] + c[1] * vs[1] + c[2] * vs[2];
+            const R mag = (R)2 * fi - (R)6 * w * Q.rho0 * cvs;
+            R dP[3] = {c[0] * mag, c[1] * mag, c[2] * mag};
             if (P.thermo) {
                 // chemical stress flux through the link, 6 w_i P(x) . c_i
-                double pc[3];
-                pt_dot<F, double>(pt, N, n, i, pc);
-                for (int a = 0; a < 3; ++a) dP[a] += 6.0 * w * pc[a];
+                dP[0] += (R)6 * w * (pt[0] * c[0] + pt[3] * c[1] + pt[4] * c[2]);
+                dP[1] += (R)6 * w * (pt[3] * c[0] + pt[1] * c[1] + pt[5] * c[2]);
+                dP[2] += (R)6 * w * (pt[4] * c[0] + pt[5] * c[1] + pt[2] * c[2]);
             }
-            acc[0] += dP[0];
-            acc[1] += dP[1];
-            acc[2] += dP[2];
-            acc[3] += r[1] * dP[2] - r[2] * dP[1];
-            acc[4] += r[2] * dP[0] - r[0] * dP[2];
-            acc[5] += r[0] * dP[1] - r[1] * dP[0];
-            const double g6[6] = {c[0], c[1], c[2], r[1] * c[2] - r[2] * c[1], r[2] * c[0] - r[0] * c[2],
-                                  r[0] * c[1] - r[1] * c[0]};
-            const double zc = zc0 * w;
+            nacc[0] += dP[0];
+            nacc[1] += dP[1];
+            nacc[2] += dP[2];
+            nacc[3] += r[1] * dP[2] - r[2] * dP[1];
+            nacc[4] += r[2] * dP[0] - r[0] * dP[2];
+            nacc[5] += r[0] * dP[1] - r[1] * dP[0];
+            const R g6[6] = {c[0], c[1], c[2], r[1] * c[2] - r[2] * c[1], r[2] * c[0] - r[0] * c[2],
+                             r[0] * c[1] - r[1] * c[0]};
+            const R zc = zc0 * w;
             int k = 6;
 #pragma unroll
             for (int a = 0; a < 6; ++a)
 #pragma unroll
-                for (int b = a; b < 6; ++b) acc[k++] += zc * g6[a] * g6[b];
+                for (int b = a; b < 6; ++b) nacc[k++] += zc * g6[a] * g6[b];
         }
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] += (double)nacc[k];
     }
-    block_sum<K>(acc, smem);
+    block_sum_t<K>(acc, smem);
     double* part = D.link_part + ((size_t)p * kMaxPartBlocks + blockIdx.x) * K;
     if (threadIdx.x == 0) {
         for (int k = 0; k < K; ++k) part[k] = acc[k];
@@ -337,21 +601,29 @@ __global__ void __launch_bounds__(kPartThreads) k_links(DevParams P, DevPtrs D)
         last = (atomicAdd(D.link_ticket + p, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
+    // last block of this particle: thread b loads block b's partials; the
+    // block reduction adds them in a fixed order
     __threadfence();
     double sum[K];
+#pragma unroll
     for (int k = 0; k < K; ++k) sum[k] = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-        volatile const double* pb = D.link_part + ((size_t)p * kMaxPartBlocks + b) * K;
-        for (int k = 0; k < K; ++k) sum[k] += pb[k];
+    if (threadIdx.x < gridDim.x) {
+        const double* pb = D.link_part + ((size_t)p * kMaxPartBlocks + threadIdx.x) * K;
+#pragma unroll
+        for (int k = 0; k < K; ++k) sum[k] = __ldcg(pb + k);
     }
+    block_sum_t<K>(sum, smem);
+    if (threadIdx.x != 0) return;
     D.link_ticket[p] = 0u;
 
     DevPart& dp = D.parts[p];
     double zeta[6][6];
     {
         int k = 6;
+#pragma unroll
         for (int a = 0; a < 6; ++a)
+#pragma unroll
             for (int b = a; b < 6; ++b) {
                 zeta[a][b] = sum[k];
                 zeta[b][a] = sum[k];
@@ -359,6 +631,7 @@ __global__ void __launch_bounds__(kPartThreads) k_links(DevParams P, DevPtrs D)
             }
     }
     double F0[6];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
         F0[a] = sum[a] + q.imp_f[a] + q.ext_f[a];
         F0[3 + a] = sum[3 + a] + q.imp_t[a] + q.ext_t[a];
@@ -366,17 +639,55 @@ __global__ void __launch_bounds__(kPartThreads) k_links(DevParams P, DevPtrs D)
     double V[6] = {q.U[0], q.U[1], q.U[2], q.W[0], q.W[1], q.W[2]};
     if (!q.fixed) {
         const double Mm[6] = {q.M, q.M, q.M, q.I, q.I, q.I};
-        double A[6][6], b[6], Vn[6];
+        double A[6][6], b[6], dinv[6];
+#pragma unroll
         for (int a = 0; a < 6; ++a) {
+#pragma unroll
             for (int c = 0; c < 6; ++c) A[a][c] = zeta[a][c];
             A[a][a] += Mm[a];
             b[a] = Mm[a] * V[a] + F0[a];
         }
-        if (solve6(A, b, Vn) != 0) atomicOr(D.err, kErrSolve);
-        for (int a = 0; a < 6; ++a) V[a] = Vn[a];
+        // Cholesky A = L L^T (in place, lower triangle), then two triangular
+        // solves with the reciprocal diagonal
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            double s = A[j][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= A[j][k] * A[j][k];
+            ok = ok && (s > 0.0);
+            const double d = sqrt(fmax(s, 1e-300));
+            dinv[j] = 1.0 / d;
+#pragma unroll
+            for (int i = j + 1; i < 6; ++i) {
+                double t = A[i][j];
+#pragma unroll
+                for (int k = 0; k < j; ++k) t -= A[i][k] * A[j][k];
+                A[i][j] = t * dinv[j];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            double t = b[i];
+#pragma unroll
+            for (int k = 0; k < i; ++k) t -= A[i][k] * b[k];
+            b[i] = t * dinv[i];
+        }
+#pragma unroll
+        for (int i = 5; i >= 0; --i) {
+            double t = b[i];
+#pragma unroll
+            for (int k = i + 1; k < 6; ++k) t -= A[k][i] * b[k];
+            b[i] = t * dinv[i];
+        }
+        if (!ok) atomicOr(D.err, kErrSolve);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) V[a] = b[a];
     }
+#pragma unroll
     for (int a = 0; a < 6; ++a) {
         double zv = 0.0;
+#pragma unroll
         for (int c = 0; c < 6; ++c) zv += zeta[a][c] * V[c];
         if (a < 3)
             dp.force[a] = F0[a] - zv;
@@ -384,9 +695,12 @@ __global__ void __launch_bounds__(kPartThreads) k_links(DevParams P, DevPtrs D)
             dp.torque[a - 3] = F0[a] - zv;
     }
     const int L[3] = {P.nx, P.ny, P.nz};
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
         dp.U[a] = V[a];
         dp.W[a] = V[3 + a];
+        dp.Uf[a] = (float)V[a];
+        dp.Wf[a] = (float)V[3 + a];
         dp.imp_f[a] = 0.0;
         dp.imp_t[a] = 0.0;
         double X = q.X[a] + V[a];
@@ -411,17 +725,25 @@ __global__ void __launch_bounds__(kPartThreads) k_links(DevParams P, DevPtrs D)
                                k3[0] * m[1] - k3[1] * m[0]};
         const double km = k3[0] * m[0] + k3[1] * m[1] + k3[2] * m[2];
         double mn[3];
+#pragma unroll
         for (int a = 0; a < 3; ++a) mn[a] = m[a] * c + kxm[a] * sn + k3[a] * km * (1.0 - c);
         const double nn = sqrt(mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]);
+#pragma unroll
         for (int a = 0; a < 3; ++a) dp.mn[a] = mn[a] / nn;
     }
 }
 
 // ---------------------------------------------------------------------------
-// S2 + S3: force, streaming with bounce-back, BGK collision with Guo forcing
+// S3: streaming with bounce-back, BGK collision with Guo forcing
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ bool near_wall(const DevParams& P, int x, int y, int z)
+{
+    return (!P.per[0] && (x == 0 || x == P.nx - 1)) || (!P.per[1] && (y == 0 || y == P.ny - 1)) ||
+           (!P.per[2] && (z == 0 || z == P.nz - 1));
+}
+
 template <class C>
-__global__ void __launch_bounds__(kRowThreads) k_collide(DevParams P, DevPtrs D)
+__global__ void __launch_bounds__(kRowThreads, 6) k_collide(DevParams P, DevPtrs D)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
@@ -431,69 +753,51 @@ __global__ void __launch_bounds__(kRowThreads) k_collide(DevParams P, DevPtrs D)
     if (x >= P.nx) return;
     const int n = x + P.nx * (y + P.ny * z);
     if (D.mask[n]) return;
+    const PrmR<R>& Q = prm<R>(P);
     const size_t N = (size_t)P.N;
     const S* fs = (const S*)D.f_src;
     S* fd = (S*)D.f_dst;
-    const F* phi = (const F*)D.phi_src;
-    const F* pt = (const F*)D.pt;
-    const R rho0 = (R)P.rho0;
+    const F* force = (const F*)D.force;
+    const R rho0 = Q.rho0;
     int nb[19];
     neighbours(P, x, y, z, nb);
-
-    // F = g - div P in the link form -6 sum_i w_i [(P(x) + P(x+c_i))/2] . c_i,
-    // P(x) standing in for solid and wall neighbours
-    R Fx = (R)P.g[0], Fy = (R)P.g[1], Fz = (R)P.g[2];
-    if (P.thermo) {
-        R d0 = 0, d1 = 0, d2 = 0;
-#pragma unroll
-        for (int i = 1; i < 19; ++i) {
-            const int m = nb[i];
-            R a[3], b[3];
-            pt_dot<F, R>(pt, N, n, i, a);
-            if (m < 0 || D.mask[m]) {
-                b[0] = a[0];
-                b[1] = a[1];
-                b[2] = a[2];
-            } else {
-                pt_dot<F, R>(pt, N, m, i, b);
-            }
-            const R w = (R)wgt(i);
-            d0 += w * ((R)0.5 * (a[0] + b[0]));
-            d1 += w * ((R)0.5 * (a[1] + b[1]));
-            d2 += w * ((R)0.5 * (a[2] + b[2]));
-        }
-        Fx -= (R)6 * d0;
-        Fy -= (R)6 * d1;
-        Fz -= (R)6 * d2;
-    }
+    const R Fx = (R)force[n], Fy = (R)force[N + n], Fz = (R)force[2 * N + n];
 
     R fl[19];
-    bool have_g = false;
-    double gphi[3] = {0.0, 0.0, 0.0};
+    if (!D.bflag[n] && !near_wall(P, x, y, z)) {
+        // every source x - c_j is a fluid node: plain pull
 #pragma unroll
-    for (int j = 0; j < 19; ++j) {
-        if (j == 0) {
-            fl[0] = (R)PopStore<S>::load(fs, n, 0, rho0);
-            continue;
-        }
-        const int i = opp(j);
-        const int m = nb[i];   // source x - c_j = x + c_i
-        if (m < 0) {
-            fl[j] = (R)PopStore<S>::load(fs, (size_t)i * N + n, i, rho0);
-        } else {
-            const uint8_t q = D.mask[m];
-            if (q) {
-                if (!have_g) {
-                    grad_phi_at(nb, phi, D.mask, (double)phi[n] + D.corr[1], D.corr[1], gphi);
-                    have_g = true;
-                }
-                double r[3], ub[3], vs[3];
-                link_velocity(P, D.parts[q - 1], x, y, z, i, gphi, r, ub, vs);
-                const double cub = cx(i) * ub[0] + cy(i) * ub[1] + cz(i) * ub[2];
-                const R fi = (R)PopStore<S>::load(fs, (size_t)i * N + n, i, rho0);
-                fl[j] = fi - (R)(6.0 * wgt(i) * P.rho0 * cub);
+        for (int j = 0; j < 19; ++j) fl[j] = (R)PopStore<S>::load(fs, (size_t)j * N + nb[opp(j)], j, rho0);
+    } else {
+        const F* phi = (const F*)D.phi_src;
+        const R dph = corr_r<R>(D, 1);
+        bool have_g = false;
+        R gphi[3] = {0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < 19; ++j) {
+            if (j == 0) {
+                fl[0] = (R)PopStore<S>::load(fs, n, 0, rho0);
+                continue;
+            }
+            const int i = opp(j);
+            const int m = nb[i];   // source x - c_j = x + c_i
+            if (m < 0) {
+                fl[j] = (R)PopStore<S>::load(fs, (size_t)i * N + n, i, rho0);
             } else {
-                fl[j] = (R)PopStore<S>::load(fs, (size_t)j * N + m, j, rho0);
+                const uint8_t q = D.mask[m];
+                if (q) {
+                    if (!have_g) {
+                        grad_phi_at<R, F>(nb, phi, D.mask, (R)phi[n] + dph, dph, gphi);
+                        have_g = true;
+                    }
+                    R r[3], ub[3], vs[3];
+                    link_velocity<R>(P, D.parts[q - 1], x, y, z, i, gphi, r, ub, vs);
+                    const R cub = (R)cx(i) * ub[0] + (R)cy(i) * ub[1] + (R)cz(i) * ub[2];
+                    const R fi = (R)PopStore<S>::load(fs, (size_t)i * N + n, i, rho0);
+                    fl[j] = fi - (R)6 * wgt_r<R>(i) * rho0 * cub;
+                } else {
+                    fl[j] = (R)PopStore<S>::load(fs, (size_t)j * N + m, j, rho0);
+                }
             }
         }
     }
@@ -501,23 +805,24 @@ __global__ void __launch_bounds__(kRowThreads) k_collide(DevParams P, DevPtrs D)
 #pragma unroll
     for (int j = 0; j < 19; ++j) {
         rho += fl[j];
-        jx += (R)cx(j) * fl[j];
-        jy += (R)cy(j) * fl[j];
-        jz += (R)cz(j) * fl[j];
+        if (cx(j) != 0) jx += cx(j) > 0 ? fl[j] : -fl[j];
+        if (cy(j) != 0) jy += cy(j) > 0 ? fl[j] : -fl[j];
+        if (cz(j) != 0) jz += cz(j) > 0 ? fl[j] : -fl[j];
     }
     const R ux = (jx + (R)0.5 * Fx) / rho;
     const R uy = (jy + (R)0.5 * Fy) / rho;
     const R uz = (jz + (R)0.5 * Fz) / rho;
-    const R itau = (R)(1.0 / P.tau);
-    const R omf = (R)(1.0 - 0.5 / P.tau);
+    const R itau = Q.itau, omf = Q.omf;
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R uF = ux * Fx + uy * Fy + uz * Fz;
 #pragma unroll
     for (int j = 0; j < 19; ++j) {
-        const R c0 = (R)cx(j), c1 = (R)cy(j), c2 = (R)cz(j);
-        const R cu = c0 * ux + c1 * uy + c2 * uz;
-        R Sg = ((R)3 * (c0 - ux) + (R)9 * cu * c0) * Fx + ((R)3 * (c1 - uy) + (R)9 * cu * c1) * Fy +
-               ((R)3 * (c2 - uz) + (R)9 * cu * c2) * Fz;
-        Sg *= (R)wgt(j);
-        const R fe = feq_i<R>(j, rho, ux, uy, uz);
+        const R cu = cdot<R>(j, ux, uy, uz);
+        const R cF = cdot<R>(j, Fx, Fy, Fz);
+        const R w = wgt_r<R>(j);
+        // Guo source w [3 (c - u) + 9 (c.u) c] . F = w [3 (c.F - u.F) + 9 (c.u)(c.F)]
+        const R Sg = w * ((R)3 * (cF - uF) + (R)9 * cu * cF);
+        const R fe = w * rho * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu);
         const R out = fl[j] - (fl[j] - fe) * itau + omf * Sg;
         PopStore<S>::store(fd, (size_t)j * N + n, j, rho0, out);
     }
@@ -528,7 +833,7 @@ __global__ void __launch_bounds__(kRowThreads) k_collide(DevParams P, DevPtrs D)
 }
 
 // ---------------------------------------------------------------------------
-// S4: psi and phi transport, production and sink
+// S4: psi and phi transport, production and sink, one thread per node
 // ---------------------------------------------------------------------------
 template <class C>
 __global__ void __launch_bounds__(kRowThreads) k_scalars(DevParams P, DevPtrs D)
@@ -540,65 +845,72 @@ __global__ void __launch_bounds__(kRowThreads) k_scalars(DevParams P, DevPtrs D)
     if (x >= P.nx) return;
     const int n = x + P.nx * (y + P.ny * z);
     if (D.mask[n]) return;
+    const PrmR<R>& Q = prm<R>(P);
     const size_t N = (size_t)P.N;
     const F* psi = (const F*)D.psi_src;
     const F* phi = (const F*)D.phi_src;
     const F* mps = (const F*)D.mupsi;
     const F* mph = (const F*)D.muphi;
     const F* u = (const F*)D.u;
-    const R dps = (R)D.corr[0], dph = (R)D.corr[1];
+    const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
     const R ps = (R)psi[n] + dps, ph = (R)phi[n] + dph;
     const R a0 = (R)mps[n], b0 = (R)mph[n];
     const R ux = (R)u[n], uy = (R)u[N + n], uz = (R)u[2 * N + n];
-    const R Mps = (R)P.Mpsi, Mph = (R)P.Mphi;
     int nb[19];
     neighbours(P, x, y, z, nb);
     R sps = 0, sph = 0;
-    unsigned long long adj = 0ull;
-    bool have_g = false;
-    double gphi[3] = {0.0, 0.0, 0.0};
+    bool solid_nb = false;
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-        const int m = nb[i];
-        if (m < 0) continue;
-        const uint8_t q = D.mask[m];
-        if (q) {
-            // link into a particle: no diffusive flux; the scalar leaves with
-            // the boundary velocity of the bounce-back rule, c.u_b g(x)
-            adj |= 1ull << (q - 1);
-            if (!have_g) {
-                grad_phi_at(nb, phi, D.mask, (double)phi[n] + D.corr[1], D.corr[1], gphi);
-                have_g = true;
-            }
-            double r[3], ub[3], vs[3];
-            link_velocity(P, D.parts[q - 1], x, y, z, i, gphi, r, ub, vs);
-            const double cub = cx(i) * ub[0] + cy(i) * ub[1] + cz(i) * ub[2];
-            const R w = (R)wgt(i);
-            sps += w * ((R)0 - (R)(cub * (double)ps));
-            sph += w * ((R)0 - (R)(cub * (double)ph));
-            continue;
-        }
-        const R c0 = (R)cx(i), c1 = (R)cy(i), c2 = (R)cz(i);
-        const R cu0 = c0 * ux + c1 * uy + c2 * uz;
-        const R cu1 = c0 * (R)u[m] + c1 * (R)u[N + m] + c2 * (R)u[2 * N + m];
+        const int m = nb[i] >= 0 ? nb[i] : n;
+        const uint8_t mk = nb[i] >= 0 ? D.mask[m] : kWallSlot;
+        const R cu0 = cdot<R>(i, ux, uy, uz);
+        const R cu1 = cdot<R>(i, (R)u[m], (R)u[N + m], (R)u[2 * N + m]);
         const R ub = (R)0.5 * (cu0 + cu1);
         const R psm = (R)psi[m] + dps, phm = (R)phi[m] + dph;
         const R aps = ub > (R)0 ? ub * ps : ub * psm;
         const R aph = ub > (R)0 ? ub * ph : ub * phm;
-        const R w = (R)wgt(i);
-        sps += w * (Mps * ((R)mps[m] - a0) - aps);
-        sph += w * (Mph * ((R)mph[m] - b0) - aph);
+        const R w = wgt_r<R>(i);
+        // links to walls and particles carry no flux here (particle links are
+        // handled below)
+        const R on = mk ? (R)0 : (R)1;
+        sps += on * (w * (Q.Mpsi * ((R)mps[m] - a0) - aps));
+        sph += on * (w * (Q.Mphi * ((R)mph[m] - b0) - aph));
+        solid_nb = solid_nb || (mk != 0 && mk != kWallSlot);
+    }
+    R hn_src = 0;
+    if (solid_nb) {
+        // links into particles: no diffusive flux; the scalar leaves with the
+        // boundary velocity of the bounce-back rule, c.u_b g(x); Janus
+        // production on the m.(x - X) <= 0 side of each adjacent particle
+        unsigned long long adj = 0ull;
+        R gphi[3];
+        grad_phi_at<R, F>(nb, phi, D.mask, ph, dph, gphi);
+        for (int i = 1; i < 19; ++i) {
+            const int m = nb[i];
+            if (m < 0) continue;
+            const uint8_t mk = D.mask[m];
+            if (!mk) continue;
+            adj |= 1ull << (mk - 1);
+            R r[3], ubv[3], vs[3];
+            link_velocity<R>(P, D.parts[mk - 1], x, y, z, i, gphi, r, ubv, vs);
+            const R cub = (R)cx(i) * ubv[0] + (R)cy(i) * ubv[1] + (R)cz(i) * ubv[2];
+            const R w = wgt_r<R>(i);
+            sps += w * ((R)0 - cub * ps);
+            sph += w * ((R)0 - cub * ph);
+        }
+        while (adj) {
+            const int k = __ffsll((long long)adj) - 1;
+            adj &= adj - 1;
+            const DevPart& q = D.parts[k];
+            double r[3];
+            node_offset(P, q, x, y, z, r);
+            if (dot3_rn(q.m, r) <= 0.0) hn_src += PartR<R>::alpha(q);
+        }
     }
     const R pn = ps + (R)6 * sps;
-    R hn = ph + (R)6 * sph - (R)P.kd * (ph - ((R)P.phib + (R)P.E * tanh_r(ps)));
-    while (adj) {
-        const int k = __ffsll((long long)adj) - 1;
-        adj &= adj - 1;
-        const DevPart& q = D.parts[k];
-        double r[3];
-        node_offset(P, q, x, y, z, r);
-        if (dot3_rn(q.m, r) <= 0.0) hn += (R)q.alpha;
-    }
+    R hn = ph + (R)6 * sph - Q.kd * (ph - (Q.phib + Q.E * tanh_r(ps)));
+    hn += hn_src;
     ((F*)D.psi_dst)[n] = (F)pn;
     ((F*)D.phi_dst)[n] = (F)hn;
 }
@@ -608,8 +920,8 @@ __global__ void __launch_bounds__(kRowThreads) k_scalars(DevParams P, DevPtrs D)
 // new position with a margin that contains every neighbour of a node that can
 // change.  k_cover_mark writes the new mask of the box (ownership over all
 // particles at their new positions, first match); k_cover_apply moves the
-// fields of the changed nodes and sums what the moving surfaces carried out
-// of the fluid.
+// fields of the changed nodes, refreshes the boundary flags of the box and
+// sums what the moving surfaces carried out of the fluid.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cover_origin(const DevParams& P, const DevPart& q, int o[3])
 {
@@ -651,7 +963,7 @@ __global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPt
     using F = typename C::fld_t;
     using S = typename C::pop_t;
     constexpr int K = kCoverK;
-    __shared__ double smem[32 * K];
+    __shared__ double smem[block_sum_t_bytes<K>(kPartThreads) / sizeof(double)];
     __shared__ bool last;
     const int p = blockIdx.y;
     const DevPart& q = D.parts[p];
@@ -665,7 +977,8 @@ __global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPt
     const F* psi0 = (const F*)D.psi_src;
     const F* phi0 = (const F*)D.phi_src;
     F* u = (F*)D.u;
-    const R rho0 = (R)P.rho0;
+    const R rho0 = prm<R>(P).rho0;
+    const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
@@ -676,24 +989,35 @@ __global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPt
         const uint8_t ob = D.mask[n], nw = D.mask_next[n];
         int nb[19];
         neighbours(P, x, y, z, nb);
-        if (ob == 0) {
+        // boundary flag for the next step (fluid node with a solid neighbour)
+        // and the links of this node into particle p; all mask loads first
+        bool adj = false, lk[19], any = false;
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const int m = nb[i] >= 0 ? nb[i] : n;
+            adj = adj || (nb[i] >= 0 && D.mask_next[m]);
+            lk[i] = ob == 0 && nb[i] >= 0 && D.mask[m] == p + 1;
+            any = any || lk[i];
+        }
+        D.bflag[n] = (!nw && adj) ? 1 : 0;
+        if (any) {
             // psi, phi carried into the surface this step through the links of
             // this node into particle p: 6 w_i c_i.u_b g(x), as in k_scalars
-            bool have_g = false;
-            double gphi[3] = {0.0, 0.0, 0.0};
+            const R ps = (R)psi0[n] + dps, ph = (R)phi0[n] + dph;
+            R gphi[3];
+            grad_phi_at<R, F>(nb, phi0, D.mask, ph, dph, gphi);
+            R a9 = 0, a10 = 0;
+#pragma unroll
             for (int i = 1; i < 19; ++i) {
-                const int m = nb[i];
-                if (m < 0 || D.mask[m] != p + 1) continue;
-                if (!have_g) {
-                    grad_phi_at(nb, phi0, D.mask, (double)phi0[n] + D.corr[1], D.corr[1], gphi);
-                    have_g = true;
-                }
-                double r[3], ub[3], vs[3];
-                link_velocity(P, q, x, y, z, i, gphi, r, ub, vs);
-                const double cub = cx(i) * ub[0] + cy(i) * ub[1] + cz(i) * ub[2];
-                acc[9] += 6.0 * wgt(i) * (cub * ((double)psi0[n] + D.corr[0]));
-                acc[10] += 6.0 * wgt(i) * (cub * ((double)phi0[n] + D.corr[1]));
+                if (!lk[i]) continue;
+                R r[3], ub[3], vs[3];
+                link_velocity<R>(P, q, x, y, z, i, gphi, r, ub, vs);
+                const R cub = cdot<R>(i, ub[0], ub[1], ub[2]);
+                a9 += (R)6 * wgt_r<R>(i) * (cub * ps);
+                a10 += (R)6 * wgt_r<R>(i) * (cub * ph);
             }
+            acc[9] += (double)a9;
+            acc[10] += (double)a10;
         }
         if (ob == nw) continue;
         if (ob == 0 && nw == p + 1) {
@@ -769,7 +1093,7 @@ __global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPt
             atomicOr(D.err, kErrOverlap);   // passed straight into another sphere
         }
     }
-    block_sum<K>(acc, smem);
+    block_sum_t<K>(acc, smem);
     double* part = D.cover_part + ((size_t)p * kMaxPartBlocks + blockIdx.x) * K;
     if (threadIdx.x == 0) {
         for (int k = 0; k < K; ++k) part[k] = acc[k];
@@ -777,33 +1101,42 @@ __global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPt
         last = (atomicAdd(D.cover_ticket, 1u) == gridDim.x * gridDim.y - 1);
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
-    // last block of the grid: impulses to their particles, deficits into the
-    // uniform correction, particles moved to their new positions
+    if (!last) return;
+    // last block of the grid: per particle, thread b loads block b's partials
+    // and the block reduction adds them in a fixed order; impulses go to their
+    // particles, deficits into the uniform correction, particles move
     __threadfence();
-    double dps = 0.0, dph = 0.0, dcnt = 0.0;
+    double dsum_psi = 0.0, dsum_phi = 0.0, dcnt = 0.0;
     for (int k = 0; k < (int)gridDim.y; ++k) {
         double s[K];
+#pragma unroll
         for (int c = 0; c < K; ++c) s[c] = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) {
-            volatile const double* cp = D.cover_part + ((size_t)k * kMaxPartBlocks + b) * K;
-            for (int c = 0; c < K; ++c) s[c] += cp[c];
+        if (threadIdx.x < gridDim.x) {
+            const double* cp = D.cover_part + ((size_t)k * kMaxPartBlocks + threadIdx.x) * K;
+#pragma unroll
+            for (int c = 0; c < K; ++c) s[c] = __ldcg(cp + c);
         }
-        DevPart& dk = D.parts[k];
-        for (int a = 0; a < 3; ++a) {
-            dk.imp_f[a] = s[a];
-            dk.imp_t[a] = s[3 + a];
-            dk.X[a] = dk.Xn[a];
-            dk.m[a] = dk.mn[a];
+        block_sum_t<K>(s, smem);
+        if (threadIdx.x == 0) {
+            DevPart& dk = D.parts[k];
+            for (int a = 0; a < 3; ++a) {
+                dk.imp_f[a] = s[a];
+                dk.imp_t[a] = s[3 + a];
+                dk.X[a] = dk.Xn[a];
+                dk.m[a] = dk.mn[a];
+            }
+            dsum_psi += s[6] + s[9];
+            dsum_phi += s[7] + s[10];
+            dcnt += s[8];
         }
-        dps += s[6] + s[9];
-        dph += s[7] + s[10];
-        dcnt += s[8];
     }
+    if (threadIdx.x != 0) return;
     const long long nf = *D.nfluid + (long long)dcnt;
     *D.nfluid = nf;
-    D.corr[0] = dps / (double)nf;
-    D.corr[1] = dph / (double)nf;
+    D.corr[0] = dsum_psi / (double)nf;
+    D.corr[1] = dsum_phi / (double)nf;
+    D.corr_f[0] = (float)D.corr[0];
+    D.corr_f[1] = (float)D.corr[1];
     *D.cover_ticket = 0u;
 }
 
@@ -822,7 +1155,7 @@ __global__ void k_set_fields(DevParams P, DevPtrs D, const double* rho_in, const
     using F = typename C::fld_t;
     using S = typename C::pop_t;
     const size_t N = (size_t)P.N;
-    const R rho0 = (R)P.rho0;
+    const R rho0 = prm<R>(P).rho0;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
         if (D.mask[n]) continue;
         F* psi = (F*)D.psi_dst;
@@ -852,6 +1185,31 @@ __global__ void k_set_fields(DevParams P, DevPtrs D, const double* rho_in, const
     }
 }
 
+// Chemical potentials of the current fields (for the readout only).
+template <class C>
+__global__ void k_mu_now(DevParams P, DevPtrs D)
+{
+    using R = typename C::real;
+    using F = typename C::fld_t;
+    const size_t N = (size_t)P.N;
+    const F* psi = (const F*)D.psi_src;
+    const F* phi = (const F*)D.phi_src;
+    const R dph = corr_r<R>(D, 1);
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        R mps = 0, mph = 0;
+        if (!D.mask[n]) {
+            const int x = (int)(n % P.nx), y = (int)((n / P.nx) % P.ny), z = (int)(n / ((size_t)P.nx * P.ny));
+            int nb[19];
+            neighbours(P, x, y, z, nb);
+            R v[19], pt[6];
+            gather_psi<R, F>(P, D, psi, x, y, z, nb, v);
+            mu_pressure<R>(prm<R>(P), v, (R)phi[n] + dph, false, mps, mph, pt);
+        }
+        ((F*)D.mupsi)[n] = (F)mps;
+        ((F*)D.muphi)[n] = (F)mph;
+    }
+}
+
 // Fields to FP64 staging (zeros at solid nodes).  which: bit0 rho, bit1 u,
 // bit2 psi, bit3 phi, bit4 mu (mu_psi to out_rho, mu_phi to out_psi).
 template <class C>
@@ -862,7 +1220,7 @@ __global__ void k_get_fields(DevParams P, DevPtrs D, int which, double* out_rho,
     using F = typename C::fld_t;
     using S = typename C::pop_t;
     const size_t N = (size_t)P.N;
-    const R rho0 = (R)P.rho0;
+    const R rho0 = prm<R>(P).rho0;
     const S* f = (const S*)D.f_src;
     const F* psi = (const F*)D.psi_src;
     const F* phi = (const F*)D.phi_src;
@@ -896,7 +1254,7 @@ __global__ void k_get_pops(DevParams P, DevPtrs D, double* out, int i)
     const S* f = (const S*)D.f_src;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
         double v = 0.0;
-        if (!D.mask[n]) v = (double)PopStore<S>::load(f, (size_t)i * N + n, i, (R)P.rho0);
+        if (!D.mask[n]) v = (double)PopStore<S>::load(f, (size_t)i * N + n, i, prm<R>(P).rho0);
         out[n] = v;
     }
 }
@@ -911,7 +1269,7 @@ __global__ void __launch_bounds__(256) k_sums(DevParams P, DevPtrs D, double* pa
     using S = typename C::pop_t;
     __shared__ double smem[32 * 3];
     const size_t N = (size_t)P.N;
-    const R rho0 = (R)P.rho0;
+    const R rho0 = prm<R>(P).rho0;
     const S* f = (const S*)D.f_src;
     const F* psi = (const F*)D.psi_src;
     const F* phi = (const F*)D.phi_src;
@@ -954,6 +1312,22 @@ static __global__ void k_claim(DevParams P, uint8_t* m0, uint8_t* m1, const DevP
             m1[n] = (uint8_t)(p + 1);
             atomicAdd(count, 1ull);
         }
+    }
+}
+
+// Boundary flags of every node from a mask: fluid node with a solid neighbour.
+static __global__ void k_bflag_all(DevParams P, const uint8_t* mask, uint8_t* bflag)
+{
+    const size_t N = (size_t)P.N;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(n % P.nx), y = (int)((n / P.nx) % P.ny), z = (int)(n / ((size_t)P.nx * P.ny));
+        bool adj = false;
+        if (!mask[n]) {
+            int nb[19];
+            neighbours(P, x, y, z, nb);
+            for (int i = 1; i < 19; ++i) adj = adj || (nb[i] >= 0 && mask[nb[i]]);
+        }
+        bflag[n] = adj ? 1 : 0;
     }
 }
 

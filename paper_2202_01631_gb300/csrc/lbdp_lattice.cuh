@@ -44,10 +44,33 @@ __host__ __device__ constexpr double wgt(int i)
     return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
 }
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+// Weights and their reciprocals in a given precision: selecting among
+// constants of that type keeps FP64 out of FP32 code even where a loop over
+// the directions is not unrolled.
+template <class R>
+__host__ __device__ constexpr R wgt_r(int i)
+{
+    return i == 0 ? (R)(1.0 / 3.0) : (i < 7 ? (R)(1.0 / 18.0) : (R)(1.0 / 36.0));
+}
+template <class R>
+__host__ __device__ constexpr R inv_wgt_r(int i)
+{
+    return i == 0 ? (R)3 : (i < 7 ? (R)18 : (R)36);
+}
 
 // ---------------------------------------------------------------------------
 // parameters and particles
 // ---------------------------------------------------------------------------
+// Model parameters in the arithmetic precision of a kernel.  Both copies are
+// filled on the host, so an FP32 kernel never converts from FP64 (GB300 runs
+// FP64, conversions included, on a narrow pipe).
+template <class R>
+struct PrmR {
+    R itau, omf;          // 1/tau, 1 - 1/(2 tau)
+    R rho0, g[3];
+    R A, kappa, Mpsi, C, Mphi, E, phib, kd, inv_kappa;
+};
+
 struct DevParams {
     int nx, ny, nz;
     int per[3];
@@ -57,15 +80,45 @@ struct DevParams {
     double tau, rho0;
     double g[3];
     double A, kappa, Mpsi, C, Mphi, E, phib, kd;
+    PrmR<float> pf;
+    PrmR<double> pd;
     int side1[3];   // link box edge per axis (clamped to the box on periodic axes)
     int side2[3];   // cover box edge per axis
     int nb1, nb2;   // blocks per particle of the link and cover kernels
 };
 
+template <class R>
+__host__ __device__ __forceinline__ const PrmR<R>& prm(const DevParams& P);
+template <>
+__host__ __device__ __forceinline__ const PrmR<float>& prm<float>(const DevParams& P) { return P.pf; }
+template <>
+__host__ __device__ __forceinline__ const PrmR<double>& prm<double>(const DevParams& P) { return P.pd; }
+
+template <class R>
+inline void fill_prm(PrmR<R>& q, const DevParams& P)
+{
+    q.itau = (R)(1.0 / P.tau);
+    q.omf = (R)(1.0 - 0.5 / P.tau);
+    q.rho0 = (R)P.rho0;
+    for (int a = 0; a < 3; ++a) q.g[a] = (R)P.g[a];
+    q.A = (R)P.A;
+    q.kappa = (R)P.kappa;
+    q.Mpsi = (R)P.Mpsi;
+    q.C = (R)P.C;
+    q.Mphi = (R)P.Mphi;
+    q.E = (R)P.E;
+    q.phib = (R)P.phib;
+    q.kd = (R)P.kd;
+    q.inv_kappa = P.kappa > 0.0 ? (R)(1.0 / P.kappa) : (R)0;
+}
+
 struct DevPart {
     double X[3], U[3], W[3], m[3];   // position, velocity, spin, unit vector
     double Xn[3], mn[3];             // position and unit vector after this step
+    float Uf[3], Wf[3];              // U, W in FP32 for the FP32 link arithmetic
+    float alpha_f, mu_pf, mu_mf, Hk_f;
     double R, R2, M, I, alpha, mu_p, mu_m, H;
+    double Hk;                       // H / kappa of the wetting ghost
     double ext_f[3], ext_t[3];
     double imp_f[3], imp_t[3];       // covering impulses, applied in the next step
     double force[3], torque[3];
@@ -96,11 +149,14 @@ struct DevPtrs {
     void* mupsi;
     void* muphi;
     void* pt;             // [6][N] chemical pressure tensor xx yy zz xy xz yz
+    void* force;          // [3][N] force on the fluid, g - div P
     void* u;
     const uint8_t* mask;
     uint8_t* mask_next;
+    uint8_t* bflag;       // [N] 1 = fluid node with a solid neighbour
     DevPart* parts;
     double* corr;         // [2]: uniform psi/phi correction still to be added
+    float* corr_f;        // [2]: the same in FP32
     int* err;
     double* link_part;    // [np][kMaxPartBlocks][kLinkK]
     unsigned* link_ticket;   // [np]
@@ -126,11 +182,11 @@ template <>
 struct PopStore<float> {
     static __device__ __forceinline__ float load(const float* p, size_t k, int i, float rho0)
     {
-        return p[k] + (float)wgt(i) * rho0;
+        return p[k] + wgt_r<float>(i) * rho0;
     }
     static __device__ __forceinline__ void store(float* p, size_t k, int i, float rho0, float f)
     {
-        p[k] = f - (float)wgt(i) * rho0;
+        p[k] = f - wgt_r<float>(i) * rho0;
     }
 };
 
@@ -140,11 +196,11 @@ template <>
 struct PopStore<__half> {
     static __device__ __forceinline__ float load(const __half* p, size_t k, int i, float rho0)
     {
-        return (__half2float(p[k]) + rho0) * (float)wgt(i);
+        return (__half2float(p[k]) + rho0) * wgt_r<float>(i);
     }
     static __device__ __forceinline__ void store(__half* p, size_t k, int i, float rho0, float f)
     {
-        p[k] = __float2half_rn(f * (float)(1.0 / wgt(i)) - rho0);
+        p[k] = __float2half_rn(f * inv_wgt_r<float>(i) - rho0);
     }
 };
 
@@ -152,11 +208,11 @@ template <>
 struct PopStore<__nv_bfloat16> {
     static __device__ __forceinline__ float load(const __nv_bfloat16* p, size_t k, int i, float rho0)
     {
-        return (__bfloat162float(p[k]) + rho0) * (float)wgt(i);
+        return (__bfloat162float(p[k]) + rho0) * wgt_r<float>(i);
     }
     static __device__ __forceinline__ void store(__nv_bfloat16* p, size_t k, int i, float rho0, float f)
     {
-        p[k] = __float2bfloat16_rn(f * (float)(1.0 / wgt(i)) - rho0);
+        p[k] = __float2bfloat16_rn(f * inv_wgt_r<float>(i) - rho0);
     }
 };
 

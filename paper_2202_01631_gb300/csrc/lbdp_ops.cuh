@@ -13,14 +13,35 @@ struct Ops {
     // One time step: mu/P, particle velocities, collide-stream, psi/phi
     // transport, covering.  ev (optional, 6 events) brackets the kernel
     // classes for the per-kernel split.
+    using R = typename C::real;
+
+    static constexpr size_t kLinkSmem = block_sum_t_bytes<kLinkK>(kPartThreads);
+
+    // Opt the kernels that use more than 48 KiB of shared memory in, once per
+    // device.
+    static cudaError_t prepare()
+    {
+        static bool done[64] = {false};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+        e = cudaFuncSetAttribute(k_links<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinkSmem);
+        if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+        return e;
+    }
+
     static cudaError_t launch_step(const DevParams& P, const DevPtrs& D, const RowGrid& g, cudaStream_t s,
                                    cudaEvent_t* ev)
     {
+        cudaError_t e = prepare();
+        if (e != cudaSuccess) return e;
         const dim3 pg1(P.nb1, P.np), pg2(P.nb2, P.np);
         if (ev) cudaEventRecord(ev[0], s);
-        k_mu<C><<<g.grid, g.block, 0, s>>>(P, D);
+        k_mup<C><<<g.grid, g.block, 0, s>>>(P, D);
+        k_fdiv<C><<<g.grid, g.block, 0, s>>>(P, D);
         if (ev) cudaEventRecord(ev[1], s);
-        if (P.np > 0) k_links<C><<<pg1, kPartThreads, 0, s>>>(P, D);
+        if (P.np > 0) k_links<C><<<pg1, kPartThreads, kLinkSmem, s>>>(P, D);
         if (ev) cudaEventRecord(ev[2], s);
         k_collide<C><<<g.grid, g.block, 0, s>>>(P, D);
         if (ev) cudaEventRecord(ev[3], s);
@@ -61,6 +82,7 @@ struct Ops {
     static cudaError_t get_fields(const DevParams& P, const DevPtrs& D, cudaStream_t s, int which, double* a,
                                   double* u, double* b, double* c)
     {
+        if (which & 16) k_mu_now<C><<<grid1d(P), 256, 0, s>>>(P, D);
         k_get_fields<C><<<grid1d(P), 256, 0, s>>>(P, D, which, a, u, b, c);
         return cudaGetLastError();
     }

@@ -185,6 +185,20 @@ def test_full_size_interface_fp32_two_steps():
     assert np.max(np.abs(pg["pos"] - pr["pos"])) / 8.0 < TOL32
 
 
+def test_chemical_potentials_fp64():
+    """mu_psi, mu_phi of the current fields (Eq. chem_potentials, wetting
+    ghosts at the particle) match the oracle."""
+    wl = W.plain_fp64(seed=4)
+    wl.particles[0]["theta_c_deg"] = 65.0
+    box, ref = make_pair(wl.params, wl.fields, wl.particles)
+    box.step(30)
+    ref.step(30)
+    mg, mr = box.mu(), ref.mu()
+    m = ref.mask()
+    assert np.max(np.abs(mg[0] - mr[0])[m == 0]) < TOL64
+    assert np.max(np.abs(mg[1] - mr[1])[m == 0]) < TOL64
+
+
 def test_add_particle_rejections():
     from paper_2202_01631_gb300.lbdp import Box, LbError
     box = Box(precision="fp32", nx=24, ny=24, nz=24, periodic=(1, 1, 0))
