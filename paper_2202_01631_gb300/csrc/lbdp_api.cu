@@ -13,41 +13,6 @@
 
 using namespace lbdp;
 
-struct lb_handle {
-    lb_params prm;
-    DevParams dp;
-    const PrecOps* ops;
-    cudaStream_t stream;
-    bool own_stream;
-    int device;
-    int cur;   // which buffer of each pair holds the current state
-    void* f[2];
-    void* psi[2];
-    void* phi[2];
-    void* mupsi;
-    void* muphi;
-    void* u;
-    uint8_t* mask[2];
-    DevPart* parts;
-    double* corr;   // [2] FP64 followed by [2] FP32 copies (corr_f)
-    int* err;
-    void* pt;
-    void* force;
-    uint8_t* bflag;
-    double* link_part;
-    unsigned* link_ticket;
-    double* cover_part;
-    unsigned* cover_ticket;
-    long long* nfluid;
-    double* staging;   // 6N FP64 for host transfers: rho, u[3], psi, phi
-    double* red_part;
-    double* red_out;
-    unsigned long long* count;
-    int red_blocks;
-    std::vector<DevPart> host_parts;
-    double rmax;
-};
-
 namespace {
 
 const PrecOps* ops_for(int prec)
@@ -75,26 +40,52 @@ int validate(const lb_params* p)
     return LB_OK;
 }
 
-size_t state_bytes(const lb_params* p, const PrecOps* ops, int red_blocks)
-{
-    size_t N = (size_t)p->nx * p->ny * p->nz;
-    size_t b = 0;
-    b += 2 * 19 * N * (size_t)ops->pop_bytes;          // populations
-    b += (4 + 2 + 3) * N * (size_t)ops->fld_bytes;     // psi, phi (x2), mu, u
-    b += 2 * N;                                         // masks
-    b += 6 * N * sizeof(double);                        // staging
-    b += 9 * N * (size_t)ops->fld_bytes + N;            // pressure tensor, force, boundary flags
-    b += kMaxParticles * (sizeof(DevPart) + sizeof(unsigned));
-    b += (size_t)kMaxParticles * kMaxPartBlocks * (kLinkK + kCoverK) * sizeof(double);
-    b += (size_t)red_blocks * 3 * sizeof(double) + 64;
-    return b;
-}
-
 int reduction_blocks(const lb_params* p)
 {
     long long N = (long long)p->nx * p->ny * p->nz;
     long long b = (N + 255) / 256;
     return (int)(b < 152 * 8 ? b : 152 * 8);
+}
+
+// Every array of a box in one region, each start aligned to 256 bytes.  With
+// base == nullptr only the total is computed.
+size_t layout(const lb_params* p, const PrecOps* ops, int red_blocks, lb_handle* h, char* base)
+{
+    const size_t N = (size_t)p->nx * p->ny * p->nz;
+    const size_t pb = (size_t)ops->pop_bytes, fb = (size_t)ops->fld_bytes;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void* {
+        void* r = base ? (void*)(base + off) : nullptr;
+        off += (bytes + 255) & ~(size_t)255;
+        return r;
+    };
+    lb_handle tmp;
+    lb_handle* t = h ? h : &tmp;
+    for (int k = 0; k < 2; ++k) t->f[k] = take(19 * N * pb);
+    for (int k = 0; k < 2; ++k) {
+        t->psi[k] = take(N * fb);
+        t->phi[k] = take(N * fb);
+        t->mask[k] = (uint8_t*)take(N);
+    }
+    t->mupsi = take(N * fb);
+    t->muphi = take(N * fb);
+    t->u = take(3 * N * fb);
+    t->force = take(3 * N * fb);
+    t->pt = take(6 * N * fb);
+    t->bflag = (uint8_t*)take(N);
+    t->parts = (DevPart*)take(kMaxParticles * sizeof(DevPart));
+    t->corr = (double*)take(4 * sizeof(double));
+    t->err = (int*)take(sizeof(int));
+    t->link_part = (double*)take((size_t)kMaxParticles * kMaxPartBlocks * kLinkK * sizeof(double));
+    t->link_ticket = (unsigned*)take(kMaxParticles * sizeof(unsigned));
+    t->cover_part = (double*)take((size_t)kMaxParticles * kMaxPartBlocks * kCoverK * sizeof(double));
+    t->cover_ticket = (unsigned*)take(sizeof(unsigned));
+    t->nfluid = (long long*)take(sizeof(long long));
+    t->staging = (double*)take(6 * N * sizeof(double));
+    t->red_part = (double*)take((size_t)red_blocks * 3 * sizeof(double));
+    t->red_out = (double*)take(3 * sizeof(double));
+    t->count = (unsigned long long*)take(sizeof(unsigned long long));
+    return off;
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? LB_OK : (e == cudaErrorMemoryAllocation ? LB_ERR_NOMEM : LB_ERR_CUDA); }
@@ -180,11 +171,11 @@ void update_sides(lb_handle* h)
 void free_all(lb_handle* h)
 {
     if (h->device >= 0) cudaSetDevice(h->device);
-    void* ptrs_[] = {h->f[0], h->f[1], h->psi[0], h->psi[1], h->phi[0], h->phi[1], h->mupsi, h->muphi,
-                     h->u, h->mask[0], h->mask[1], h->parts, h->corr, h->err, h->pt, h->force, h->bflag, h->link_part,
-                     h->link_ticket, h->cover_part, h->cover_ticket, h->nfluid, h->staging, h->red_part, h->red_out, h->count};
-    for (void* p : ptrs_)
-        if (p) cudaFree(p);
+    if (h->batch)
+        batch_release(h);
+    else if (h->region)
+        cudaFree(h->region);
+    h->region = nullptr;
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -217,133 +208,11 @@ int lb_device_bytes(const lb_params* p, size_t* bytes)
 {
     int st = validate(p);
     if (st != LB_OK || !bytes) return LB_ERR_PARAM;
-    *bytes = state_bytes(p, ops_for(p->precision), reduction_blocks(p));
+    *bytes = handle_region_bytes(p);
     return LB_OK;
 }
 
-int lb_create(const lb_params* p, lb_handle** out)
-{
-    if (!out) return LB_ERR_PARAM;
-    *out = nullptr;
-    int st = validate(p);
-    if (st != LB_OK) return st;
-    lb_handle* h = new (std::nothrow) lb_handle();
-    if (!h) return LB_ERR_NOMEM;
-    h->prm = *p;
-    h->ops = ops_for(p->precision);
-    h->device = -1;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        delete h;
-        return LB_ERR_CUDA;
-    }
-    h->device = dev;
-    DevParams& P = h->dp;
-    memset(&P, 0, sizeof(P));
-    P.nx = p->nx;
-    P.ny = p->ny;
-    P.nz = p->nz;
-    for (int a = 0; a < 3; ++a) {
-        P.per[a] = p->periodic[a];
-        P.g[a] = p->body_force[a];
-    }
-    P.N = (long long)p->nx * p->ny * p->nz;
-    P.np = 0;
-    P.thermo = p->thermo_force;
-    P.tau = p->tau;
-    P.rho0 = p->rho0;
-    P.A = p->A;
-    P.kappa = p->kappa;
-    P.Mpsi = p->M_psi;
-    P.C = p->C;
-    P.Mphi = p->M_phi;
-    P.E = p->E;
-    P.phib = p->phi_b;
-    P.kd = p->k_d;
-    fill_prm(P.pf, P);
-    fill_prm(P.pd, P);
-    h->rmax = 0.0;
-    update_sides(h);
-    h->red_blocks = reduction_blocks(p);
-
-    const size_t N = (size_t)P.N;
-    cudaError_t e = cudaSuccess;
-    if (p->cuda_stream) {
-        h->stream = (cudaStream_t)p->cuda_stream;
-        h->own_stream = false;
-    } else {
-        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-        h->own_stream = true;
-    }
-    const size_t pb = (size_t)h->ops->pop_bytes, fb = (size_t)h->ops->fld_bytes;
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-        e = cudaMalloc(&h->f[k], 19 * N * pb);
-        if (e == cudaSuccess) e = cudaMalloc(&h->psi[k], N * fb);
-        if (e == cudaSuccess) e = cudaMalloc(&h->phi[k], N * fb);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&h->mask[k], N);
-    }
-    if (e == cudaSuccess) e = cudaMalloc(&h->mupsi, N * fb);
-    if (e == cudaSuccess) e = cudaMalloc(&h->muphi, N * fb);
-    if (e == cudaSuccess) e = cudaMalloc(&h->u, 3 * N * fb);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->parts, kMaxParticles * sizeof(DevPart));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->corr, 4 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->err, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&h->force, 3 * N * fb);
-    if (e == cudaSuccess) e = cudaMalloc(&h->pt, 6 * N * fb);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->bflag, N);
-    if (e == cudaSuccess)
-        e = cudaMalloc((void**)&h->link_part, (size_t)kMaxParticles * kMaxPartBlocks * kLinkK * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->link_ticket, kMaxParticles * sizeof(unsigned));
-    if (e == cudaSuccess)
-        e = cudaMalloc((void**)&h->cover_part, (size_t)kMaxParticles * kMaxPartBlocks * kCoverK * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->cover_ticket, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->nfluid, sizeof(long long));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->staging, 6 * N * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->red_part, (size_t)h->red_blocks * 3 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->red_out, 3 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->count, sizeof(unsigned long long));
-    if (e != cudaSuccess) {
-        free_all(h);
-        delete h;
-        cudaGetLastError();
-        return cuda_status(e);
-    }
-    // rest state: rho = rho0, u = 0, psi = phi = 0, all fluid
-    cudaStream_t s = h->stream;
-    long long nf = P.N;
-    e = cudaMemsetAsync(h->mask[0], 0, N, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->mask[1], 0, N, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->corr, 0, 4 * sizeof(double), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->link_ticket, 0, kMaxParticles * sizeof(unsigned), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->cover_ticket, 0, sizeof(unsigned), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->force, 0, 3 * N * fb, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->pt, 0, 6 * N * fb, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->bflag, 0, N, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->u, 0, 3 * N * fb, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->mupsi, 0, N * fb, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->muphi, 0, N * fb, s);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-        e = cudaMemsetAsync(h->psi[k], 0, N * fb, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->phi[k], 0, N * fb, s);
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->nfluid, &nf, sizeof(long long), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) {
-        // populations from rho = rho0 everywhere (staging holds rho0)
-        std::vector<double> ones(N, p->rho0);
-        e = cudaMemcpyAsync(h->staging, ones.data(), N * sizeof(double), cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = h->ops->set_fields(P, cur_ptrs(h), s, h->staging, nullptr, nullptr, nullptr);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    }
-    if (e != cudaSuccess) {
-        free_all(h);
-        delete h;
-        cudaGetLastError();
-        return cuda_status(e);
-    }
-    *out = h;
-    return LB_OK;
-}
+int lb_create(const lb_params* p, lb_handle** out) { return lbdp::lb_create_in(p, nullptr, nullptr, out); }
 
 void lb_destroy(lb_handle* h)
 {
@@ -663,4 +532,127 @@ cudaError_t launch_claim(const DevParams& P, uint8_t* m0, uint8_t* m1, const Dev
     k_claim<<<blocks, 256, 0, s>>>(P, m0, m1, parts, p, count);
     return cudaGetLastError();
 }
+}  // namespace lbdp
+
+namespace lbdp {
+
+size_t handle_region_bytes(const lb_params* p)
+{
+    return layout(p, ops_for(p->precision), reduction_blocks(p), nullptr, nullptr);
+}
+
+DevPtrs handle_ptrs(const lb_handle* h, int src) { return ptrs(h, src); }
+
+// Create a box.  region == nullptr: the box allocates its own region;
+// otherwise region (handle_region_bytes(p) bytes, 256-byte aligned) belongs to
+// batch, which takes it back through batch_release.
+int lb_create_in(const lb_params* p, lbb_batch* batch, void* region, lb_handle** out)
+{
+    if (!out) return LB_ERR_PARAM;
+    *out = nullptr;
+    int st = validate(p);
+    if (st != LB_OK) return st;
+    lb_handle* h = new (std::nothrow) lb_handle();
+    if (!h) return LB_ERR_NOMEM;
+    h->prm = *p;
+    h->ops = ops_for(p->precision);
+    h->device = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        delete h;
+        return LB_ERR_CUDA;
+    }
+    h->device = dev;
+    DevParams& P = h->dp;
+    memset(&P, 0, sizeof(P));
+    P.nx = p->nx;
+    P.ny = p->ny;
+    P.nz = p->nz;
+    for (int a = 0; a < 3; ++a) {
+        P.per[a] = p->periodic[a];
+        P.g[a] = p->body_force[a];
+    }
+    P.N = (long long)p->nx * p->ny * p->nz;
+    P.np = 0;
+    P.thermo = p->thermo_force;
+    P.tau = p->tau;
+    P.rho0 = p->rho0;
+    P.A = p->A;
+    P.kappa = p->kappa;
+    P.Mpsi = p->M_psi;
+    P.C = p->C;
+    P.Mphi = p->M_phi;
+    P.E = p->E;
+    P.phib = p->phi_b;
+    P.kd = p->k_d;
+    fill_prm(P.pf, P);
+    fill_prm(P.pd, P);
+    h->rmax = 0.0;
+    update_sides(h);
+    h->red_blocks = reduction_blocks(p);
+
+    const size_t N = (size_t)P.N;
+    const size_t fb = (size_t)h->ops->fld_bytes;
+    cudaError_t e = cudaSuccess;
+    if (p->cuda_stream) {
+        h->stream = (cudaStream_t)p->cuda_stream;
+        h->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        h->own_stream = true;
+    }
+    h->region_bytes = layout(p, h->ops, h->red_blocks, nullptr, nullptr);
+    if (e == cudaSuccess) {
+        if (region) {
+            h->region = region;
+            h->batch = batch;
+        } else {
+            e = cudaMalloc(&h->region, h->region_bytes);
+        }
+    }
+    if (e != cudaSuccess) {
+        h->region = nullptr;
+        if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+        delete h;
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    layout(p, h->ops, h->red_blocks, h, (char*)h->region);
+    // rest state: rho = rho0, u = 0, psi = phi = 0, all fluid
+    cudaStream_t s = h->stream;
+    long long nf = P.N;
+    e = cudaMemsetAsync(h->mask[0], 0, N, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->mask[1], 0, N, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->corr, 0, 4 * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->link_ticket, 0, kMaxParticles * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->cover_ticket, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->force, 0, 3 * N * fb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->pt, 0, 6 * N * fb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->bflag, 0, N, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->u, 0, 3 * N * fb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->mupsi, 0, N * fb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->muphi, 0, N * fb, s);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMemsetAsync(h->psi[k], 0, N * fb, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->phi[k], 0, N * fb, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->nfluid, &nf, sizeof(long long), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        // populations from rho = rho0 everywhere (staging holds rho0)
+        std::vector<double> ones(N, p->rho0);
+        e = cudaMemcpyAsync(h->staging, ones.data(), N * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = h->ops->set_fields(P, cur_ptrs(h), s, h->staging, nullptr, nullptr, nullptr);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
+        free_all(h);
+        delete h;
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    *out = h;
+    return LB_OK;
+}
+
 }  // namespace lbdp

@@ -1,0 +1,815 @@
+// lbdp_batch.cu -- the extern "C" entry points of include/lbdp_batch.h: the
+// arena that places boxes in one device allocation, batches of boxes that
+// advance together through the persistent kernels of lbdp_batch_kernels.cuh
+// (captured in CUDA graphs, launch shapes picked by an autotuner), and the
+// continuous-batching request loop.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <deque>
+#include <iterator>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "lbdp.h"
+#include "lbdp_batch.h"
+#include "lbdp_batch_kernels.cuh"
+#include "lbdp_internal.h"
+
+using namespace lbdp;
+
+namespace lbdp {
+const BatchCfg kBatchCfgs[kNumBatchCfgs] = {{128, 1, 0, 0}, {128, 1, 0, 1}, {256, 1, 1, 1}, {128, 2, 1, 1}};
+}  // namespace lbdp
+
+// ---------------------------------------------------------------------------
+// arena: first fit over offsets, 256-byte granules, coalescing frees
+// ---------------------------------------------------------------------------
+struct lb_arena {
+    size_t cap = 0;
+    size_t used = 0;
+    std::map<size_t, size_t> free_ranges;   // offset -> bytes
+    std::map<size_t, size_t> held;          // offset -> bytes
+};
+
+namespace {
+
+constexpr size_t kGranule = 256;
+
+size_t round_up(size_t b) { return (b + kGranule - 1) / kGranule * kGranule; }
+
+int cuda_status(cudaError_t e)
+{
+    return e == cudaSuccess ? LB_OK : (e == cudaErrorMemoryAllocation ? LB_ERR_NOMEM : LB_ERR_CUDA);
+}
+
+#define LB_TRY(expr)                                   \
+    do {                                               \
+        cudaError_t e_ = (expr);                       \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+const BatchOps* batch_ops_for(int prec)
+{
+    switch (prec) {
+        case LB_FP64: return &kBatchF64;
+        case LB_FP32: return &kBatchF32;
+        case LB_FP16_SHIFT: return &kBatchF16;
+        case LB_BF16_SHIFT: return &kBatchBF16;
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_arena_create(size_t capacity, lb_arena** out)
+{
+    if (!out) return LB_ERR_PARAM;
+    *out = nullptr;
+    const size_t cap = capacity / kGranule * kGranule;
+    if (cap == 0) return LB_ERR_PARAM;
+    lb_arena* a = new (std::nothrow) lb_arena();
+    if (!a) return LB_ERR_NOMEM;
+    a->cap = cap;
+    a->free_ranges[0] = cap;
+    *out = a;
+    return LB_OK;
+}
+
+int lb_arena_alloc(lb_arena* a, size_t bytes, size_t* offset)
+{
+    if (!a || !offset || bytes == 0) return LB_ERR_PARAM;
+    const size_t need = round_up(bytes);
+    for (auto it = a->free_ranges.begin(); it != a->free_ranges.end(); ++it) {
+        if (it->second < need) continue;
+        const size_t off = it->first, have = it->second;
+        a->free_ranges.erase(it);
+        if (have > need) a->free_ranges[off + need] = have - need;
+        a->held[off] = need;
+        a->used += need;
+        *offset = off;
+        return LB_OK;
+    }
+    return LB_ERR_NOMEM;
+}
+
+int lb_arena_free(lb_arena* a, size_t offset)
+{
+    if (!a) return LB_ERR_PARAM;
+    auto h = a->held.find(offset);
+    if (h == a->held.end()) return LB_ERR_PARAM;
+    size_t off = h->first, len = h->second;
+    a->held.erase(h);
+    a->used -= len;
+    auto next = a->free_ranges.lower_bound(off);
+    if (next != a->free_ranges.end() && next->first == off + len) {
+        len += next->second;
+        next = a->free_ranges.erase(next);
+    }
+    if (next != a->free_ranges.begin()) {
+        auto prev = std::prev(next);
+        if (prev->first + prev->second == off) {
+            prev->second += len;
+            return LB_OK;
+        }
+    }
+    a->free_ranges[off] = len;
+    return LB_OK;
+}
+
+int lb_arena_stats(const lb_arena* a, size_t* used, size_t* largest_free, int* free_ranges)
+{
+    if (!a) return LB_ERR_PARAM;
+    size_t big = 0;
+    for (const auto& r : a->free_ranges) big = std::max(big, r.second);
+    if (used) *used = a->used;
+    if (largest_free) *largest_free = big;
+    if (free_ranges) *free_ranges = (int)a->free_ranges.size();
+    return LB_OK;
+}
+
+void lb_arena_destroy(lb_arena* a) { delete a; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Member {
+    lb_handle* h;
+    size_t off;        // arena offset of the box's region
+    long long left;    // steps still to run (host mirror of the device count)
+    int np_seen;       // particles when the tables were last built
+};
+
+template <class T>
+struct DevArray {
+    T* p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace
+
+struct lbb_batch {
+    int precision = 0;
+    const BatchOps* bops = nullptr;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = -1;
+    int sms = 0;
+    char* base = nullptr;
+    lb_arena* arena = nullptr;
+    int graph_steps = 16;
+    std::vector<Member> mem;
+    bool dirty = true;
+    BatchDev* d_hdr = nullptr;
+    BoxDev* d_boxes = nullptr;
+    int* d_cur = nullptr;
+    long long* d_left = nullptr;
+    DevArray<NodeTile> d_node[kNodeTileSizes];
+    DevArray<PartTile> d_link, d_cover;
+    int cfg[4] = {0, 0, 0, 0};
+    int grid[4] = {0, 0, 0, 0};
+    int part_grid = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+constexpr int kStepLaunches = 8;   // 4 node kernels, 3 particle kernels, the buffer flip
+
+int find_member(const lbb_batch* b, const lb_handle* h)
+{
+    for (size_t i = 0; i < b->mem.size(); ++i)
+        if (b->mem[i].h == h) return (int)i;
+    return -1;
+}
+
+void drop_graph(lbb_batch* b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+}
+
+int set_grids(lbb_batch* b)
+{
+    for (int k = 0; k < 4; ++k) {
+        int bps = 0;
+        LB_TRY(b->bops->node_grid(k, b->cfg[k], &bps));
+        b->grid[k] = b->sms * std::max(bps, 1);
+    }
+    b->part_grid = 2 * b->sms;
+    drop_graph(b);
+    return LB_OK;
+}
+
+template <class T>
+cudaError_t ensure(lbb_batch* b, DevArray<T>& a, size_t n)
+{
+    if (n <= a.cap) return cudaSuccess;
+    size_t cap = std::max<size_t>(n, 2 * a.cap);
+    cudaError_t e = cudaStreamSynchronize(b->stream);   // kernels may still read the old array
+    if (e != cudaSuccess) return e;
+    if (a.p) cudaFree(a.p);
+    a.p = nullptr;
+    a.cap = 0;
+    e = cudaMalloc((void**)&a.p, cap * sizeof(T));
+    if (e == cudaSuccess) a.cap = cap;
+    return e;
+}
+
+// Rebuild the device tables from the member list (boxes, tiles, header).
+int rebuild(lbb_batch* b)
+{
+    const int nb = (int)b->mem.size();
+    std::vector<BoxDev> boxes(nb);
+    std::vector<NodeTile> nt[kNodeTileSizes];
+    std::vector<PartTile> lt, ct;
+    for (int i = 0; i < nb; ++i) {
+        lb_handle* h = b->mem[i].h;
+        BoxDev& bd = boxes[i];
+        bd.P = h->dp;
+        bd.D[0] = handle_ptrs(h, 0);
+        bd.D[1] = handle_ptrs(h, 1);
+        bd.mx = div_magic((unsigned)h->dp.nx);
+        bd.my = div_magic((unsigned)h->dp.ny);
+        const int N = (int)h->dp.N;
+        for (int k = 0; k < kNodeTileSizes; ++k)
+            for (int s = 0; s < N; s += 128 << k) nt[k].push_back({i, s});
+        for (int p = 0; p < h->dp.np; ++p) {
+            for (int j = 0; j < h->dp.nb1; ++j) lt.push_back({i, p, j, h->dp.nb1});
+            for (int j = 0; j < h->dp.nb2; ++j) ct.push_back({i, p, j, h->dp.nb2});
+        }
+        b->mem[i].np_seen = h->dp.np;
+    }
+    BatchDev hdr;
+    memset(&hdr, 0, sizeof(hdr));
+    for (int k = 0; k < kNodeTileSizes; ++k) {
+        LB_TRY(ensure(b, b->d_node[k], std::max<size_t>(nt[k].size(), 1)));
+        hdr.node[k] = b->d_node[k].p;
+        hdr.n_node[k] = (int)nt[k].size();
+    }
+    LB_TRY(ensure(b, b->d_link, std::max<size_t>(lt.size(), 1)));
+    LB_TRY(ensure(b, b->d_cover, std::max<size_t>(ct.size(), 1)));
+    hdr.boxes = b->d_boxes;
+    hdr.cur = b->d_cur;
+    hdr.left = b->d_left;
+    hdr.nbox = nb;
+    hdr.link = b->d_link.p;
+    hdr.n_link = (int)lt.size();
+    hdr.cover = b->d_cover.p;
+    hdr.n_cover = (int)ct.size();
+    cudaStream_t s = b->stream;
+    // pageable sources: each copy has read its source when the call returns
+    if (nb) LB_TRY(cudaMemcpyAsync(b->d_boxes, boxes.data(), nb * sizeof(BoxDev), cudaMemcpyHostToDevice, s));
+    for (int k = 0; k < kNodeTileSizes; ++k)
+        if (!nt[k].empty())
+            LB_TRY(cudaMemcpyAsync(b->d_node[k].p, nt[k].data(), nt[k].size() * sizeof(NodeTile),
+                                   cudaMemcpyHostToDevice, s));
+    if (!lt.empty())
+        LB_TRY(cudaMemcpyAsync(b->d_link.p, lt.data(), lt.size() * sizeof(PartTile), cudaMemcpyHostToDevice, s));
+    if (!ct.empty())
+        LB_TRY(cudaMemcpyAsync(b->d_cover.p, ct.data(), ct.size() * sizeof(PartTile), cudaMemcpyHostToDevice, s));
+    LB_TRY(cudaMemcpyAsync(b->d_hdr, &hdr, sizeof(hdr), cudaMemcpyHostToDevice, s));
+    b->dirty = false;
+    return LB_OK;
+}
+
+bool tables_stale(const lbb_batch* b)
+{
+    if (b->dirty) return true;
+    for (const Member& m : b->mem)
+        if (m.np_seen != m.h->dp.np) return true;
+    return false;
+}
+
+// Upload each box's current buffer and steps to run (all_one: 1 for every
+// box, used while tuning).
+int upload_counts(lbb_batch* b, bool all_one)
+{
+    const int nb = (int)b->mem.size();
+    if (nb == 0) return LB_OK;
+    std::vector<int> cur(nb);
+    std::vector<long long> left(nb);
+    for (int i = 0; i < nb; ++i) {
+        cur[i] = b->mem[i].h->cur;
+        left[i] = all_one ? 1 : b->mem[i].left;
+    }
+    LB_TRY(cudaMemcpyAsync(b->d_cur, cur.data(), nb * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    LB_TRY(cudaMemcpyAsync(b->d_left, left.data(), nb * sizeof(long long), cudaMemcpyHostToDevice, b->stream));
+    return LB_OK;
+}
+
+int capture_graph(lbb_batch* b)
+{
+    if (b->exec) return LB_OK;
+    cudaGraph_t g = nullptr;
+    LB_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < b->graph_steps && e == cudaSuccess; ++t)
+        e = b->bops->step(b->cfg, b->grid, b->part_grid, b->d_hdr, b->stream);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->exec = nullptr;
+        cudaGetLastError();
+    }
+    return cuda_status(e);
+}
+
+}  // namespace
+
+namespace lbdp {
+void batch_release(lb_handle* h)
+{
+    lbb_batch* b = h->batch;
+    const int i = find_member(b, h);
+    if (i >= 0) {
+        lb_arena_free(b->arena, b->mem[i].off);
+        b->mem.erase(b->mem.begin() + i);
+    }
+    b->dirty = true;
+}
+}  // namespace lbdp
+
+extern "C" {
+
+int lbb_create(const lbb_params* p, lbb_batch** out)
+{
+    if (!out) return LB_ERR_PARAM;
+    *out = nullptr;
+    if (!p || !batch_ops_for(p->precision) || p->graph_steps < 0) return LB_ERR_PARAM;
+    lbb_batch* b = new (std::nothrow) lbb_batch();
+    if (!b) return LB_ERR_NOMEM;
+    b->precision = p->precision;
+    b->bops = batch_ops_for(p->precision);
+    b->graph_steps = p->graph_steps > 0 ? p->graph_steps : 16;
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) {
+        if (p->cuda_stream) {
+            b->stream = (cudaStream_t)p->cuda_stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+            b->own_stream = e == cudaSuccess;
+        }
+    }
+    size_t cap = p->arena_bytes;
+    if (e == cudaSuccess && cap == 0) {
+        size_t fr = 0, tot = 0;
+        e = cudaMemGetInfo(&fr, &tot);
+        cap = fr / 4 * 3;
+    }
+    cap = cap / kGranule * kGranule;
+    if (e == cudaSuccess && lb_arena_create(cap, &b->arena) != LB_OK) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->base, cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_hdr, sizeof(BatchDev));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_boxes, kBatchMaxBoxes * sizeof(BoxDev));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_cur, kBatchMaxBoxes * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_left, kBatchMaxBoxes * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_left, 0, kBatchMaxBoxes * sizeof(long long), b->stream);
+    if (e == cudaSuccess) e = b->bops->prepare();
+    int st = cuda_status(e);
+    if (st == LB_OK) {
+        // default launch shape: 128 threads, one node per thread
+        st = set_grids(b);
+    }
+    if (st == LB_OK) st = rebuild(b);
+    if (st == LB_OK) st = cuda_status(cudaStreamSynchronize(b->stream));
+    if (st != LB_OK) {
+        cudaGetLastError();
+        lbb_destroy(b);
+        return st;
+    }
+    *out = b;
+    return LB_OK;
+}
+
+void lbb_destroy(lbb_batch* b)
+{
+    if (!b) return;
+    if (b->device >= 0) cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    std::vector<Member> ms = b->mem;
+    for (const Member& m : ms) lb_destroy(m.h);
+    drop_graph(b);
+    for (auto& a : b->d_node)
+        if (a.p) cudaFree(a.p);
+    if (b->d_link.p) cudaFree(b->d_link.p);
+    if (b->d_cover.p) cudaFree(b->d_cover.p);
+    if (b->d_hdr) cudaFree(b->d_hdr);
+    if (b->d_boxes) cudaFree(b->d_boxes);
+    if (b->d_cur) cudaFree(b->d_cur);
+    if (b->d_left) cudaFree(b->d_left);
+    if (b->base) cudaFree(b->base);
+    if (b->arena) lb_arena_destroy(b->arena);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+static int check_box(const lbb_batch* b, const lb_params* p)
+{
+    if (!b || !p) return LB_ERR_PARAM;
+    size_t bytes = 0;
+    if (lb_device_bytes(p, &bytes) != LB_OK) return LB_ERR_PARAM;
+    if (p->precision != b->precision) return LB_ERR_PARAM;
+    if (p->nx > kBatchMaxEdgeXY || p->ny > kBatchMaxEdgeXY) return LB_ERR_PARAM;
+    if ((long long)p->nx * p->ny * p->nz >= kBatchMaxNodes) return LB_ERR_PARAM;
+    return LB_OK;
+}
+
+int lbb_box_bytes(const lbb_batch* b, const lb_params* p, size_t* bytes)
+{
+    if (!bytes) return LB_ERR_PARAM;
+    const int st = check_box(b, p);
+    if (st != LB_OK) return st;
+    *bytes = round_up(handle_region_bytes(p));
+    return LB_OK;
+}
+
+int lbb_memory(const lbb_batch* b, size_t* capacity, size_t* used, size_t* largest_free)
+{
+    if (!b) return LB_ERR_PARAM;
+    if (capacity) *capacity = b->arena->cap;
+    return lb_arena_stats(b->arena, used, largest_free, nullptr);
+}
+
+int lbb_add_box(lbb_batch* b, const lb_params* p, lb_handle** out)
+{
+    if (!out) return LB_ERR_PARAM;
+    *out = nullptr;
+    int st = check_box(b, p);
+    if (st != LB_OK) return st;
+    if ((int)b->mem.size() >= kBatchMaxBoxes) return LB_ERR_NOMEM;
+    cudaSetDevice(b->device);
+    size_t off = 0;
+    st = lb_arena_alloc(b->arena, handle_region_bytes(p), &off);
+    if (st != LB_OK) return st;
+    lb_params q = *p;
+    q.cuda_stream = (void*)b->stream;
+    lb_handle* h = nullptr;
+    st = lb_create_in(&q, b, b->base + off, &h);
+    if (st != LB_OK) {
+        lb_arena_free(b->arena, off);
+        return st;
+    }
+    b->mem.push_back({h, off, 0, 0});
+    b->dirty = true;
+    *out = h;
+    return LB_OK;
+}
+
+int lbb_num_boxes(const lbb_batch* b) { return b ? (int)b->mem.size() : 0; }
+
+int lbb_set_steps(lbb_batch* b, lb_handle* h, long long nsteps)
+{
+    if (!b || !h || nsteps < 0) return LB_ERR_PARAM;
+    const int i = find_member(b, h);
+    if (i < 0) return LB_ERR_PARAM;
+    b->mem[i].left = nsteps;
+    return LB_OK;
+}
+
+int lbb_get_steps(const lbb_batch* b, const lb_handle* h, long long* left)
+{
+    if (!b || !h || !left) return LB_ERR_PARAM;
+    const int i = find_member(b, h);
+    if (i < 0) return LB_ERR_PARAM;
+    *left = b->mem[i].left;
+    return LB_OK;
+}
+
+int lbb_run(lbb_batch* b, int nsteps, long long* launches)
+{
+    if (launches) *launches = 0;
+    if (!b || nsteps < 0) return LB_ERR_PARAM;
+    cudaSetDevice(b->device);
+    long long most = 0;
+    for (const Member& m : b->mem) most = std::max(most, m.left);
+    const int n = (int)std::min<long long>(nsteps, most);
+    if (n == 0) return LB_OK;
+    if (tables_stale(b)) {
+        const int st = rebuild(b);
+        if (st != LB_OK) return st;
+    }
+    int st = upload_counts(b, false);
+    if (st != LB_OK) return st;
+    const int full = n / b->graph_steps, rest = n % b->graph_steps;
+    if (full > 0) {
+        st = capture_graph(b);
+        if (st != LB_OK) return st;
+        for (int k = 0; k < full; ++k) LB_TRY(cudaGraphLaunch(b->exec, b->stream));
+    }
+    for (int k = 0; k < rest; ++k) LB_TRY(b->bops->step(b->cfg, b->grid, b->part_grid, b->d_hdr, b->stream));
+    for (Member& m : b->mem) {
+        const long long ran = std::min<long long>(m.left, n);
+        m.left -= ran;
+        m.h->cur ^= (int)(ran & 1);
+    }
+    if (launches) *launches = (long long)n * kStepLaunches;
+    return LB_OK;
+}
+
+int lbb_num_configs(void) { return kNumBatchCfgs; }
+
+int lbb_config_shape(int k, int* threads, int* cells, int* regs)
+{
+    if (k < 0 || k >= kNumBatchCfgs) return LB_ERR_PARAM;
+    if (threads) *threads = kBatchCfgs[k].threads;
+    if (cells) *cells = kBatchCfgs[k].cells;
+    if (regs) *regs = kBatchCfgs[k].regs;
+    return LB_OK;
+}
+
+int lbb_set_config(lbb_batch* b, const int cfg[4])
+{
+    if (!b || !cfg) return LB_ERR_PARAM;
+    for (int k = 0; k < 4; ++k)
+        if (cfg[k] < 0 || cfg[k] >= kNumBatchCfgs) return LB_ERR_PARAM;
+    cudaSetDevice(b->device);
+    for (int k = 0; k < 4; ++k) b->cfg[k] = cfg[k];
+    return set_grids(b);
+}
+
+int lbb_tune(lbb_batch* b, int reps, int cfg_out[4], double ms_out[4])
+{
+    if (!b || reps < 1) return LB_ERR_PARAM;
+    if (b->mem.empty()) return LB_ERR_STATE;
+    cudaSetDevice(b->device);
+    cudaStream_t s = b->stream;
+    if (tables_stale(b)) {
+        const int st = rebuild(b);
+        if (st != LB_OK) return st;
+    }
+    // collide-stream rewrites the stored velocity: keep a copy in staging
+    for (const Member& m : b->mem) {
+        const size_t ub = 3 * (size_t)m.h->dp.N * m.h->ops->fld_bytes;
+        LB_TRY(cudaMemcpyAsync(m.h->staging, m.h->u, ub, cudaMemcpyDeviceToDevice, s));
+    }
+    int st = upload_counts(b, true);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == LB_OK) st = cuda_status(cudaEventCreate(&e0));
+    if (st == LB_OK) st = cuda_status(cudaEventCreate(&e1));
+    int best[4] = {0, 0, 0, 0};
+    double best_ms[4] = {0, 0, 0, 0};
+    for (int nc = 0; nc < 4 && st == LB_OK; ++nc) {
+        best_ms[nc] = 1e300;
+        for (int k = 0; k < kNumBatchCfgs && st == LB_OK; ++k) {
+            int bps = 0;
+            st = cuda_status(b->bops->node_grid(nc, k, &bps));
+            const int grid = b->sms * std::max(bps, 1);
+            for (int w = 0; w < 2 && st == LB_OK; ++w) st = cuda_status(b->bops->node(nc, k, grid, b->d_hdr, s));
+            if (st == LB_OK) st = cuda_status(cudaEventRecord(e0, s));
+            for (int r = 0; r < reps && st == LB_OK; ++r) st = cuda_status(b->bops->node(nc, k, grid, b->d_hdr, s));
+            if (st == LB_OK) st = cuda_status(cudaEventRecord(e1, s));
+            if (st == LB_OK) st = cuda_status(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            if (st == LB_OK) st = cuda_status(cudaEventElapsedTime(&ms, e0, e1));
+            if (st == LB_OK && ms / reps < best_ms[nc]) {
+                best_ms[nc] = ms / reps;
+                best[nc] = k;
+            }
+        }
+    }
+    for (const Member& m : b->mem) {
+        const size_t ub = 3 * (size_t)m.h->dp.N * m.h->ops->fld_bytes;
+        cudaError_t e = cudaMemcpyAsync(m.h->u, m.h->staging, ub, cudaMemcpyDeviceToDevice, s);
+        if (st == LB_OK) st = cuda_status(e);
+    }
+    if (st == LB_OK) st = upload_counts(b, false);
+    if (st == LB_OK) st = cuda_status(cudaStreamSynchronize(s));
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != LB_OK) return st;
+    for (int k = 0; k < 4; ++k) {
+        b->cfg[k] = best[k];
+        if (cfg_out) cfg_out[k] = best[k];
+        if (ms_out) ms_out[k] = best_ms[k];
+    }
+    return set_grids(b);
+}
+
+int lbb_sync(lbb_batch* b)
+{
+    if (!b) return LB_ERR_PARAM;
+    cudaSetDevice(b->device);
+    LB_TRY(cudaStreamSynchronize(b->stream));
+    int worst = LB_OK;
+    for (const Member& m : b->mem) {
+        const int st = lb_sync(m.h);
+        if (st != LB_OK && worst == LB_OK) worst = st;
+    }
+    return worst;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// continuous batching
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Pending {
+    long long id;
+    lbs_request r;
+    std::vector<double> psi, phi;
+};
+
+struct Live {
+    Pending q;
+    lb_handle* h;
+    double admitted;
+};
+
+}  // namespace
+
+struct lbs_server {
+    lbb_batch* batch = nullptr;
+    int precision = 0;
+    int chunk = 64;
+    int max_boxes = 0;
+    long long next_id = 0;
+    std::deque<Pending> queue;
+    std::vector<Live> live;
+    std::deque<lbs_result> done;
+};
+
+namespace {
+
+void finish(lbs_server* s, Live& L, int status, double t_done)
+{
+    lbs_result res;
+    memset(&res, 0, sizeof(res));
+    res.id = L.q.id;
+    res.arrival = L.q.r.arrival;
+    res.admitted = L.admitted;
+    res.status = status;
+    if (L.h) {
+        int n = 0;
+        int st = lb_read_particles(L.h, res.particles, 4, &n);
+        res.n_particles = n < 4 ? n : 4;
+        if (st == LB_OK) st = lb_conservation(L.h, res.sums);
+        if (st == LB_OK && (L.q.r.out_psi || L.q.r.out_phi))
+            st = lb_read_fields(L.h, nullptr, nullptr, L.q.r.out_psi, L.q.r.out_phi);
+        if (res.status == LB_OK) res.status = st;
+        lb_destroy(L.h);
+        L.h = nullptr;
+    }
+    res.done = t_done;
+    s->done.push_back(res);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbs_create(const lbs_params* p, lbs_server** out)
+{
+    if (!out) return LB_ERR_PARAM;
+    *out = nullptr;
+    if (!p || p->chunk_steps < 0 || p->max_boxes < 0) return LB_ERR_PARAM;
+    lbs_server* s = new (std::nothrow) lbs_server();
+    if (!s) return LB_ERR_NOMEM;
+    lbb_params bp;
+    memset(&bp, 0, sizeof(bp));
+    bp.precision = p->precision;
+    bp.arena_bytes = p->arena_bytes;
+    bp.cuda_stream = p->cuda_stream;
+    const int st = lbb_create(&bp, &s->batch);
+    if (st != LB_OK) {
+        delete s;
+        return st;
+    }
+    s->precision = p->precision;
+    s->chunk = p->chunk_steps > 0 ? p->chunk_steps : 64;
+    s->max_boxes = p->max_boxes;
+    *out = s;
+    return LB_OK;
+}
+
+void lbs_destroy(lbs_server* s)
+{
+    if (!s) return;
+    lbb_destroy(s->batch);   // destroys the live boxes
+    delete s;
+}
+
+lbb_batch* lbs_batch(lbs_server* s) { return s ? s->batch : nullptr; }
+
+int lbs_submit(lbs_server* s, const lbs_request* r, long long* id)
+{
+    if (!s || !r || r->steps <= 0 || r->n_particles < 0 || r->n_particles > 4) return LB_ERR_PARAM;
+    size_t bytes = 0, cap = 0;
+    int st = lbb_box_bytes(s->batch, &r->box, &bytes);
+    if (st != LB_OK) return st;
+    lbb_memory(s->batch, &cap, nullptr, nullptr);
+    if (bytes > cap) return LB_ERR_PARAM;   // can never be admitted
+    Pending q;
+    q.id = s->next_id++;
+    q.r = *r;
+    const size_t N = (size_t)r->box.nx * r->box.ny * r->box.nz;
+    if (r->psi) q.psi.assign(r->psi, r->psi + N);
+    if (r->phi) q.phi.assign(r->phi, r->phi + N);
+    q.r.psi = nullptr;
+    q.r.phi = nullptr;
+    s->queue.push_back(std::move(q));
+    if (id) *id = s->queue.back().id;
+    return LB_OK;
+}
+
+int lbs_pump(lbs_server* s, double now, int* active, int* queued)
+{
+    if (!s) return LB_ERR_PARAM;
+    const auto t0 = std::chrono::steady_clock::now();
+    auto clock = [&]() {
+        return now + std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    };
+    // admission, in arrival order; a request that does not fit is passed over
+    for (auto it = s->queue.begin(); it != s->queue.end();) {
+        if (s->max_boxes > 0 && (int)s->live.size() >= s->max_boxes) break;
+        size_t bytes = 0, largest = 0;
+        lbb_box_bytes(s->batch, &it->r.box, &bytes);
+        lbb_memory(s->batch, nullptr, nullptr, &largest);
+        if (bytes > largest) {
+            ++it;
+            continue;
+        }
+        Live L;
+        L.h = nullptr;
+        int st = lbb_add_box(s->batch, &it->r.box, &L.h);
+        if (st == LB_ERR_NOMEM) {
+            ++it;
+            continue;
+        }
+        L.q = std::move(*it);
+        it = s->queue.erase(it);
+        L.admitted = clock();
+        if (st == LB_OK && (!L.q.psi.empty() || !L.q.phi.empty()))
+            st = lb_set_fields(L.h, nullptr, nullptr, L.q.psi.empty() ? nullptr : L.q.psi.data(),
+                               L.q.phi.empty() ? nullptr : L.q.phi.data());
+        for (int k = 0; k < L.q.r.n_particles && st == LB_OK; ++k)
+            st = lb_add_particle(L.h, &L.q.r.particles[k], nullptr);
+        if (st == LB_OK) st = lbb_set_steps(s->batch, L.h, L.q.r.steps);
+        L.q.psi.clear();
+        L.q.psi.shrink_to_fit();
+        L.q.phi.clear();
+        L.q.phi.shrink_to_fit();
+        if (st != LB_OK) {
+            finish(s, L, st, clock());
+            continue;
+        }
+        s->live.push_back(std::move(L));
+    }
+    // run until the first resident box finishes, at most one chunk
+    long long n = s->chunk;
+    for (const Live& L : s->live) {
+        long long left = 0;
+        lbb_get_steps(s->batch, L.h, &left);
+        if (left > 0) n = std::min(n, left);
+    }
+    int st = LB_OK;
+    if (!s->live.empty()) {
+        st = lbb_run(s->batch, (int)n, nullptr);
+        if (st == LB_OK) {
+            cudaError_t e = cudaStreamSynchronize(s->live.front().h->stream);
+            if (e != cudaSuccess) st = LB_ERR_CUDA;
+        }
+    }
+    // retire the boxes that have run all their steps
+    for (size_t i = 0; i < s->live.size();) {
+        long long left = 0;
+        lbb_get_steps(s->batch, s->live[i].h, &left);
+        if (left > 0 && st == LB_OK) {
+            ++i;
+            continue;
+        }
+        finish(s, s->live[i], st, clock());
+        s->live.erase(s->live.begin() + i);
+    }
+    if (active) *active = (int)s->live.size();
+    if (queued) *queued = (int)s->queue.size();
+    return st;
+}
+
+int lbs_poll(lbs_server* s, lbs_result* out, int cap, int* n)
+{
+    if (!s || cap < 0 || (cap > 0 && !out)) return LB_ERR_PARAM;
+    int k = 0;
+    while (k < cap && !s->done.empty()) {
+        out[k++] = s->done.front();
+        s->done.pop_front();
+    }
+    if (n) *n = k;
+    return LB_OK;
+}
+
+}  // extern "C"

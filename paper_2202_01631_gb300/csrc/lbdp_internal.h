@@ -1,10 +1,15 @@
-// lbdp_internal.h -- interface between the C ABI (lbdp_api.cu) and the
-// per-precision kernel launchers (lbdp_prec_*.cu).
+// lbdp_internal.h -- interface between the C ABI (lbdp_api.cu,
+// lbdp_batch.cu) and the per-precision kernel launchers (lbdp_prec_*.cu).
 #pragma once
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
+#include "lbdp.h"
 #include "lbdp_lattice.cuh"
+
+struct lbb_batch;
 
 namespace lbdp {
 
@@ -36,13 +41,86 @@ struct PrecOps {
                         double* out);
 };
 
+// One batched step over the boxes of a batch (see lbdp_batch_kernels.cuh):
+// node kernels in launch configuration cfg[class], particle kernels with the
+// single-box split, then the buffer flip of every box that ran.
+struct BatchDev;
+constexpr int kNumBatchCfgs = 4;   // node kernel configurations
+struct BatchCfg {
+    int threads, cells, tile_index;   // tile = threads * cells = 128 << tile_index nodes
+    int regs;                         // register budget: 0 tight, 1 loose
+};
+extern const BatchCfg kBatchCfgs[kNumBatchCfgs];
+
+struct BatchOps {
+    // per-device kernel attributes (call once before the first launch or capture)
+    cudaError_t (*prepare)();
+    // grid: resident blocks per SM * SMs for a node kernel of class nc in cfg
+    cudaError_t (*node_grid)(int nc, int cfg, int* blocks_per_sm);
+    cudaError_t (*node)(int nc, int cfg, int grid, const BatchDev* B, cudaStream_t s);
+    // the whole step: node kernels in cfg[4], particle kernels on part_grid blocks
+    cudaError_t (*step)(const int cfg[4], const int grid[4], int part_grid, const BatchDev* B, cudaStream_t s);
+};
+
 extern const PrecOps kOpsF64;
 extern const PrecOps kOpsF32;
 extern const PrecOps kOpsF16;
 extern const PrecOps kOpsBF16;
 
+extern const BatchOps kBatchF64;
+extern const BatchOps kBatchF32;
+extern const BatchOps kBatchF16;
+extern const BatchOps kBatchBF16;
+
 cudaError_t launch_bflag(const DevParams& P, const uint8_t* mask, uint8_t* bflag, cudaStream_t s);
 cudaError_t launch_claim(const DevParams& P, uint8_t* m0, uint8_t* m1, const DevPart* parts, int p,
                          unsigned long long* count, cudaStream_t s);
 
+// Placement of a handle's device state: one region from cudaMalloc, or from
+// the arena of the batch that owns the handle.
+size_t handle_region_bytes(const lb_params* p);
+DevPtrs handle_ptrs(const lb_handle* h, int src);
+int lb_create_in(const lb_params* p, lbb_batch* batch, void* region, lb_handle** out);
+// Return a member box's region to its batch and drop it from the batch.
+void batch_release(lb_handle* h);
+
 }  // namespace lbdp
+
+// The state of one box (the lb_handle of the C ABI).
+struct lb_handle {
+    lb_params prm;
+    lbdp::DevParams dp;
+    const lbdp::PrecOps* ops;
+    cudaStream_t stream;
+    bool own_stream;
+    int device;
+    int cur;   // which buffer of each pair holds the current state
+    lbb_batch* batch;   // owning batch, or NULL for a standalone box
+    void* region;       // the single device allocation holding every array below
+    size_t region_bytes;
+    void* f[2];
+    void* psi[2];
+    void* phi[2];
+    void* mupsi;
+    void* muphi;
+    void* u;
+    uint8_t* mask[2];
+    lbdp::DevPart* parts;
+    double* corr;   // [2] FP64 followed by [2] FP32 copies (corr_f)
+    int* err;
+    void* pt;
+    void* force;
+    uint8_t* bflag;
+    double* link_part;
+    unsigned* link_ticket;
+    double* cover_part;
+    unsigned* cover_ticket;
+    long long* nfluid;
+    double* staging;   // 6N FP64 for host transfers: rho, u[3], psi, phi
+    double* red_part;
+    double* red_out;
+    unsigned long long* count;
+    int red_blocks;
+    std::vector<lbdp::DevPart> host_parts;
+    double rmax;
+};

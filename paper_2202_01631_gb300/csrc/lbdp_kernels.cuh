@@ -1,9 +1,9 @@
 // lbdp_kernels.cuh -- the per-step kernels of the lattice update, templated on
 // the precision configuration.  One step is
-//   k_force        tiled: psi, phi staged in shared memory with a two-node
-//                  halo; chemical potentials (Eq. chem_potentials, wetting
-//                  ghosts) and pressure tensor P (Eq. free_energy) on the tile
-//                  plus one node; force F = g - div P on the tile
+//   k_mup          one thread per node: chemical potentials (Eq.
+//                  chem_potentials, wetting ghosts) and the chemical pressure
+//                  tensor P (Eq. free_energy)
+//   k_fdiv         one thread per node: force on the fluid F = g - div P
 //   k_links        per particle: bounce-back and chemical-stress momentum sums
 //                  over its boundary links, implicit velocity update, new
 //                  position and orientation (Sec. "Particles")
@@ -11,14 +11,17 @@
 //                  bounce-back plus phoretic slip on particle links, BGK + Guo
 //                  with F; nodes away from walls and particles take a
 //                  branch-free path
-//   k_scalars      tiled: psi/phi transport (Eq. diffusion_reaction) with mu
-//                  recomputed in shared memory, Janus production (Eq. activity)
-//                  and the k_d sink
+//   k_scalars      one thread per node: psi/phi transport (Eq.
+//                  diffusion_reaction), Janus production (Eq. activity) and the
+//                  k_d sink
 //   k_cover_mark   per particle: solid mask at the new positions
 //   k_cover_apply  per particle: covering/uncovering and boundary flags; the
 //                  last block folds the psi/phi deficits into the uniform
 //                  correction and moves the particles
-// Every kernel is HBM-bound stencil or streaming work: no tensor cores.
+// Every kernel is stencil or streaming work: no tensor cores.  Each body is a
+// __device__ function of (parameters, pointers, node), so the single-box
+// kernels (grid over the box) and the batched kernels (persistent loop over a
+// tile list of many boxes) run the same arithmetic.
 //
 // Precision: node and link arithmetic runs in the mode's real type R.  FP64
 // is kept where the method needs it in every mode -- the solid/fluid and
@@ -46,31 +49,7 @@ using CfgBF16 = Cfg<__nv_bfloat16, float, float>;
 constexpr int kRowThreads = 128;
 constexpr int kPartThreads = 256;
 
-// Tiles of the shared-memory stencil kernels: TX x TY x TZ output nodes, a
-// two-node halo for psi/phi (the pressure tensor of a halo node needs the
-// Laplacian of psi there), a one-node halo for mu, P and u.
-constexpr int TX = 32, TY = 4, TZ = 4;
-constexpr int H2X = TX + 4, H2Y = TY + 4, H2Z = TZ + 4;
-constexpr int H1X = TX + 2, H1Y = TY + 2, H1Z = TZ + 2;
-constexpr int kN2 = H2X * H2Y * H2Z;   // 2304 slots
-constexpr int kN1 = H1X * H1Y * H1Z;   // 1224 slots
-constexpr int kNT = TX * TY * TZ;      // 512 nodes
-constexpr int kTileThreads = 256;
 constexpr uint8_t kWallSlot = 0xFF;    // slot beyond a non-periodic wall
-
-__host__ __device__ constexpr int off2(int i) { return cx(i) + H2X * (cy(i) + H2Y * cz(i)); }
-__host__ __device__ constexpr int off1(int i) { return cx(i) + H1X * (cy(i) + H1Y * cz(i)); }
-
-template <class R>
-__host__ __device__ constexpr size_t tile_smem_force()
-{
-    return (size_t)kN2 * (2 * sizeof(R) + 1) + (size_t)kN1 * 6 * sizeof(R) + 64;
-}
-template <class R>
-__host__ __device__ constexpr size_t tile_smem_scalars()
-{
-    return (size_t)kN2 * (2 * sizeof(R) + 1) + (size_t)kN1 * 5 * sizeof(R) + 64;
-}
 
 // ---------------------------------------------------------------------------
 // precision accessors
@@ -107,6 +86,18 @@ struct PartR<double> {
 // shared device helpers
 // ---------------------------------------------------------------------------
 
+// c_i . (a, b, c) with the zero components of c_i dropped at compile time
+// once the direction loop is unrolled (x + (-0) folds to x; a product with 0
+// could not be removed because of NaN and signed-zero rules).
+template <class R>
+__device__ __forceinline__ R cdot(int i, R a, R b, R c)
+{
+    const R ta = cx(i) == 0 ? (R)-0.0 : (cx(i) > 0 ? a : -a);
+    const R tb = cy(i) == 0 ? (R)-0.0 : (cy(i) > 0 ? b : -b);
+    const R tc = cz(i) == 0 ? (R)-0.0 : (cz(i) > 0 ? c : -c);
+    return ta + tb + tc;
+}
+
 // Isotropic gradient of phi at a fluid node, 3 sum_i w_i c_i phi(x+c_i), with
 // the node's own value standing in for solid and wall neighbours.
 template <class R, class Fld>
@@ -118,13 +109,14 @@ __device__ __forceinline__ void grad_phi_at(const int nb[19], const Fld* phi, co
     for (int i = 1; i < 19; ++i) {
         int m = nb[i];
         R v = (m < 0 || mask[m]) ? own : (R)phi[m] + dphi;
-        g[0] += wgt_r<R>(i) * (R)cx(i) * v;
-        g[1] += wgt_r<R>(i) * (R)cy(i) * v;
-        g[2] += wgt_r<R>(i) * (R)cz(i) * v;
+        const R w = wgt_r<R>(i);
+        if (cx(i) != 0) g[0] = fma_x(cx(i) > 0 ? w : -w, v, g[0]);
+        if (cy(i) != 0) g[1] = fma_x(cy(i) > 0 ? w : -w, v, g[1]);
+        if (cz(i) != 0) g[2] = fma_x(cz(i) > 0 ? w : -w, v, g[2]);
     }
-    g[0] *= (R)3;
-    g[1] *= (R)3;
-    g[2] *= (R)3;
+    g[0] = mul_x(g[0], (R)3);
+    g[1] = mul_x(g[1], (R)3);
+    g[2] = mul_x(g[2], (R)3);
 }
 
 // Midpoint offset r_b = (x - X) + c_i/2 of link x -> x + c_i (FP64, exact
@@ -152,16 +144,16 @@ __device__ __forceinline__ void link_velocity(const DevParams& P, const DevPart&
     r[0] = (R)rd[0];
     r[1] = (R)rd[1];
     r[2] = (R)rd[2];
-    const R rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    const R rn = sqrt(dot_x(r[0], r[1], r[2], r[0], r[1], r[2]));
     const R nh[3] = {r[0] / rn, r[1] / rn, r[2] / rn};
-    const R ng = nh[0] * gphi[0] + nh[1] * gphi[1] + nh[2] * gphi[2];
+    const R ng = dot_x(nh[0], nh[1], nh[2], gphi[0], gphi[1], gphi[2]);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) vs[a] = mu * (gphi[a] - nh[a] * ng);
+    for (int a = 0; a < 3; ++a) vs[a] = mul_x(mu, fma_x(-nh[a], ng, gphi[a]));
     const R U0 = PartR<R>::U(q, 0), U1 = PartR<R>::U(q, 1), U2 = PartR<R>::U(q, 2);
     const R W0 = PartR<R>::W(q, 0), W1 = PartR<R>::W(q, 1), W2 = PartR<R>::W(q, 2);
-    ub[0] = U0 + (W1 * r[2] - W2 * r[1]) + vs[0];
-    ub[1] = U1 + (W2 * r[0] - W0 * r[2]) + vs[1];
-    ub[2] = U2 + (W0 * r[1] - W1 * r[0]) + vs[2];
+    ub[0] = add_x(add_x(U0, cross_x(W1, r[2], W2, r[1])), vs[0]);
+    ub[1] = add_x(add_x(U1, cross_x(W2, r[0], W0, r[2])), vs[1]);
+    ub[2] = add_x(add_x(U2, cross_x(W0, r[1], W1, r[0])), vs[2]);
 }
 
 // Wetting ghost of psi at the solid neighbour x + c_i of fluid node x:
@@ -173,29 +165,20 @@ __device__ __forceinline__ R psi_ghost(const DevParams& P, const DevPart& q, int
     double rd[3];
     link_offset(P, q, x, y, z, i, rd);
     const R r0 = (R)rd[0], r1 = (R)rd[1], r2 = (R)rd[2];
-    const R rn = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
-    const R cn = ((R)cx(i) * r0 + (R)cy(i) * r1 + (R)cz(i) * r2) / rn;
-    return ps + PartR<R>::Hk(q) * cn;
+    const R rn = sqrt(dot_x(r0, r1, r2, r0, r1, r2));
+    const R cn = cdot<R>(i, r0, r1, r2) / rn;
+    return fma_x(PartR<R>::Hk(q), cn, ps);
 }
 
-// c_i . (a, b, c) with the zero components of c_i dropped at compile time
-// once the direction loop is unrolled (x + (-0) folds to x; a product with 0
-// could not be removed because of NaN and signed-zero rules).
-template <class R>
-__device__ __forceinline__ R cdot(int i, R a, R b, R c)
-{
-    const R ta = cx(i) == 0 ? (R)-0.0 : (cx(i) > 0 ? a : -a);
-    const R tb = cy(i) == 0 ? (R)-0.0 : (cy(i) > 0 ? b : -b);
-    const R tc = cz(i) == 0 ? (R)-0.0 : (cz(i) > 0 ? c : -c);
-    return ta + tb + tc;
-}
-
+// Equilibrium population i of (rho, u) (refill of uncovered nodes and the
+// host-set state), rounding written out.
 template <class Real>
 __device__ __forceinline__ Real feq_i(int i, Real rho, Real ux, Real uy, Real uz)
 {
-    Real cu = (Real)cx(i) * ux + (Real)cy(i) * uy + (Real)cz(i) * uz;
-    Real uu = ux * ux + uy * uy + uz * uz;
-    return wgt_r<Real>(i) * rho * ((Real)1 + (Real)3 * cu + (Real)4.5 * cu * cu - (Real)1.5 * uu);
+    const Real cu = cdot<Real>(i, ux, uy, uz);
+    const Real uu = dot_x(ux, uy, uz, ux, uy, uz);
+    const Real t = fma_x((Real)-1.5, uu, fma_x(mul_x((Real)4.5, cu), cu, fma_x((Real)3, cu, (Real)1)));
+    return mul_x(mul_x(wgt_r<Real>(i), rho), t);
 }
 
 __device__ __forceinline__ float tanh_r(float v) { return tanhf(v); }
@@ -344,68 +327,16 @@ __device__ __forceinline__ bool box_node(const DevParams& P, const int o[3], con
     return x >= 0 && y >= 0 && z >= 0;
 }
 
-// Stage psi, phi (with the uniform correction) and the mask of the tile plus a
-// two-node halo into shared memory; solid and wall slots hold 0.
-template <class R, class F>
-__device__ __forceinline__ void stage_tile(const DevParams& P, const DevPtrs& D, int bx0, int by0, int bz0, R* s_psi,
-                                           R* s_phi, uint8_t* s_mask)
-{
-    const F* psi = (const F*)D.psi_src;
-    const F* phi = (const F*)D.phi_src;
-    const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
-    for (int s = threadIdx.x; s < kN2; s += blockDim.x) {
-        const int lx = s % H2X - 2, ly = (s / H2X) % H2Y - 2, lz = s / (H2X * H2Y) - 2;
-        const int gx = wrap_coord(bx0 + lx, P.nx, P.per[0]);
-        const int gy = wrap_coord(by0 + ly, P.ny, P.per[1]);
-        const int gz = wrap_coord(bz0 + lz, P.nz, P.per[2]);
-        uint8_t mk = kWallSlot;
-        R a = 0, b = 0;
-        if (gx >= 0 && gy >= 0 && gz >= 0) {
-            const int n = gx + P.nx * (gy + P.ny * gz);
-            mk = D.mask[n];
-            if (!mk) {
-                a = (R)psi[n] + dps;
-                b = (R)phi[n] + dph;
-            }
-        }
-        s_mask[s] = mk;
-        s_psi[s] = a;
-        s_phi[s] = b;
-    }
-}
-
-// Ghost-resolved psi values around slot s (fluid) of the staged tile.
-template <class R>
-__device__ __forceinline__ void gather_psi_tile(const DevParams& P, const DevPtrs& D, const R* s_psi,
-                                                const uint8_t* s_mask, int s, int gx, int gy, int gz, R v[19])
-{
-    v[0] = s_psi[s];
-#pragma unroll
-    for (int i = 1; i < 19; ++i) {
-        const int t = s + off2(i);
-        const uint8_t mk = s_mask[t];
-        if (mk == 0)
-            v[i] = s_psi[t];
-        else if (mk == kWallSlot)
-            v[i] = v[0];
-        else
-            v[i] = psi_ghost<R>(P, D.parts[mk - 1], gx, gy, gz, i, v[0]);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // S1: chemical potentials and pressure tensor, one thread per node.  Every
 // neighbour load is issued before any decision (walls clamp to the node
 // itself), so the loads overlap instead of waiting behind mask branches.
 // ---------------------------------------------------------------------------
 template <class C>
-__global__ void __launch_bounds__(kRowThreads) k_mup(DevParams P, DevPtrs D)
+__device__ __forceinline__ void mup_node(const DevParams& P, const DevPtrs& D, int x, int y, int z)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= P.nx) return;
     const int n = x + P.nx * (y + P.ny * z);
     if (D.mask[n]) return;
     const PrmR<R>& Q = prm<R>(P);
@@ -448,13 +379,10 @@ __global__ void __launch_bounds__(kRowThreads) k_mup(DevParams P, DevPtrs D)
 // (sum_i w_i c_i = 0), with P~_i = P(x) at solid and wall neighbours.
 // ---------------------------------------------------------------------------
 template <class C>
-__global__ void __launch_bounds__(kRowThreads) k_fdiv(DevParams P, DevPtrs D)
+__device__ __forceinline__ void fdiv_node(const DevParams& P, const DevPtrs& D, int x, int y, int z)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= P.nx) return;
     const int n = x + P.nx * (y + P.ny * z);
     if (D.mask[n]) return;
     const PrmR<R>& Q = prm<R>(P);
@@ -499,18 +427,19 @@ __global__ void __launch_bounds__(kRowThreads) k_fdiv(DevParams P, DevPtrs D)
 // (symmetric positive definite: Cholesky), then stores the new velocity and
 // the position/orientation after the step.
 // ---------------------------------------------------------------------------
+//
+// links_block runs block bi of the nbi blocks of particle p; the block split
+// (and with it the summation order) is the same in the single-box and the
+// batched kernels, so both give identical bits.  smem holds
+// block_sum_t_bytes<kLinkK>(blockDim.x) bytes; sp and last are block-shared.
 template <class C>
-__global__ void __launch_bounds__(kPartThreads, 1) k_links(DevParams P, DevPtrs D)
+__device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D, int p, int bi, int nbi,
+                                            double* smem, DevPart& sp, bool& last)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
     using S = typename C::pop_t;
     constexpr int K = kLinkK;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* smem = (double*)smem_raw;   // block_sum_t_bytes<K>(kPartThreads)
-    __shared__ DevPart sp;
-    __shared__ bool last;
-    const int p = blockIdx.y;
     if (threadIdx.x == 0) sp = D.parts[p];
     __syncthreads();
     const DevPart& q = sp;
@@ -526,7 +455,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_links(DevParams P, DevPtrs 
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
     const R zc0 = (R)6 * Q.rho0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+    for (int t = bi * blockDim.x + threadIdx.x; t < tot; t += nbi * blockDim.x) {
         int x, y, z;
         if (!box_node(P, o, P.side1, t, x, y, z)) continue;
         const int n = x + P.nx * (y + P.ny * z);
@@ -564,41 +493,41 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_links(DevParams P, DevPtrs 
             R r[3], ub[3], vs[3];
             link_velocity<R>(P, q, x, y, z, i, gphi, r, ub, vs);
             const R fi = fv[i];
-            const R w = wgt_r<R>(i);
+            const R w6 = (R)6 * wgt_r<R>(i);
             const R c[3] = {(R)cx(i), (R)cy(i), (R)cz(i)};
-            const R cvs = c[0] * vs[0] + c[1] * vs[1] + c[2] * vs[2];
-            const R mag = (R)2 * fi - (R)6 * w * Q.rho0 * cvs;
-            R dP[3] = {c[0] * mag, c[1] * mag, c[2] * mag};
+            const R cvs = cdot<R>(i, vs[0], vs[1], vs[2]);
+            const R mag = fma_x(-mul_x(w6, Q.rho0), cvs, mul_x((R)2, fi));
+            R dP[3] = {mul_x(c[0], mag), mul_x(c[1], mag), mul_x(c[2], mag)};
             if (P.thermo) {
                 // chemical stress flux through the link, 6 w_i P(x) . c_i
-                dP[0] += (R)6 * w * (pt[0] * c[0] + pt[3] * c[1] + pt[4] * c[2]);
-                dP[1] += (R)6 * w * (pt[3] * c[0] + pt[1] * c[1] + pt[5] * c[2]);
-                dP[2] += (R)6 * w * (pt[4] * c[0] + pt[5] * c[1] + pt[2] * c[2]);
+                dP[0] = fma_x(w6, cdot<R>(i, pt[0], pt[3], pt[4]), dP[0]);
+                dP[1] = fma_x(w6, cdot<R>(i, pt[3], pt[1], pt[5]), dP[1]);
+                dP[2] = fma_x(w6, cdot<R>(i, pt[4], pt[5], pt[2]), dP[2]);
             }
-            nacc[0] += dP[0];
-            nacc[1] += dP[1];
-            nacc[2] += dP[2];
-            nacc[3] += r[1] * dP[2] - r[2] * dP[1];
-            nacc[4] += r[2] * dP[0] - r[0] * dP[2];
-            nacc[5] += r[0] * dP[1] - r[1] * dP[0];
-            const R g6[6] = {c[0], c[1], c[2], r[1] * c[2] - r[2] * c[1], r[2] * c[0] - r[0] * c[2],
-                             r[0] * c[1] - r[1] * c[0]};
-            const R zc = zc0 * w;
+            nacc[0] = add_x(nacc[0], dP[0]);
+            nacc[1] = add_x(nacc[1], dP[1]);
+            nacc[2] = add_x(nacc[2], dP[2]);
+            nacc[3] = add_x(nacc[3], cross_x(r[1], dP[2], r[2], dP[1]));
+            nacc[4] = add_x(nacc[4], cross_x(r[2], dP[0], r[0], dP[2]));
+            nacc[5] = add_x(nacc[5], cross_x(r[0], dP[1], r[1], dP[0]));
+            const R g6[6] = {c[0], c[1], c[2], cross_x(r[1], c[2], r[2], c[1]), cross_x(r[2], c[0], r[0], c[2]),
+                             cross_x(r[0], c[1], r[1], c[0])};
+            const R zc = mul_x(zc0, wgt_r<R>(i));
             int k = 6;
 #pragma unroll
             for (int a = 0; a < 6; ++a)
 #pragma unroll
-                for (int b = a; b < 6; ++b) nacc[k++] += zc * g6[a] * g6[b];
+                for (int b = a; b < 6; ++b, ++k) nacc[k] = fma_x(mul_x(zc, g6[a]), g6[b], nacc[k]);
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] += (double)nacc[k];
     }
     block_sum_t<K>(acc, smem);
-    double* part = D.link_part + ((size_t)p * kMaxPartBlocks + blockIdx.x) * K;
+    double* part = D.link_part + ((size_t)p * kMaxPartBlocks + bi) * K;
     if (threadIdx.x == 0) {
         for (int k = 0; k < K; ++k) part[k] = acc[k];
         __threadfence();
-        last = (atomicAdd(D.link_ticket + p, 1u) == gridDim.x - 1);
+        last = (atomicAdd(D.link_ticket + p, 1u) == (unsigned)nbi - 1u);
     }
     __syncthreads();
     if (!last) return;
@@ -608,7 +537,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_links(DevParams P, DevPtrs 
     double sum[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) sum[k] = 0.0;
-    if (threadIdx.x < gridDim.x) {
+    if ((int)threadIdx.x < nbi) {
         const double* pb = D.link_part + ((size_t)p * kMaxPartBlocks + threadIdx.x) * K;
 #pragma unroll
         for (int k = 0; k < K; ++k) sum[k] = __ldcg(pb + k);
@@ -633,8 +562,8 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_links(DevParams P, DevPtrs 
     double F0[6];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        F0[a] = sum[a] + q.imp_f[a] + q.ext_f[a];
-        F0[3 + a] = sum[3 + a] + q.imp_t[a] + q.ext_t[a];
+        F0[a] = add_x(add_x(sum[a], q.imp_f[a]), q.ext_f[a]);
+        F0[3 + a] = add_x(add_x(sum[3 + a], q.imp_t[a]), q.ext_t[a]);
     }
     double V[6] = {q.U[0], q.U[1], q.U[2], q.W[0], q.W[1], q.W[2]};
     if (!q.fixed) {
@@ -644,8 +573,8 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_links(DevParams P, DevPtrs 
         for (int a = 0; a < 6; ++a) {
 #pragma unroll
             for (int c = 0; c < 6; ++c) A[a][c] = zeta[a][c];
-            A[a][a] += Mm[a];
-            b[a] = Mm[a] * V[a] + F0[a];
+            A[a][a] = add_x(A[a][a], Mm[a]);
+            b[a] = fma_x(Mm[a], V[a], F0[a]);
         }
         // Cholesky A = L L^T (in place, lower triangle), then two triangular
         // solves with the reciprocal diagonal
@@ -654,7 +583,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_links(DevParams P, DevPtrs 
         for (int j = 0; j < 6; ++j) {
             double s = A[j][j];
 #pragma unroll
-            for (int k = 0; k < j; ++k) s -= A[j][k] * A[j][k];
+            for (int k = 0; k < j; ++k) s = fma_x(-A[j][k], A[j][k], s);
             ok = ok && (s > 0.0);
             const double d = sqrt(fmax(s, 1e-300));
             dinv[j] = 1.0 / d;
@@ -662,23 +591,23 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_links(DevParams P, DevPtrs 
             for (int i = j + 1; i < 6; ++i) {
                 double t = A[i][j];
 #pragma unroll
-                for (int k = 0; k < j; ++k) t -= A[i][k] * A[j][k];
-                A[i][j] = t * dinv[j];
+                for (int k = 0; k < j; ++k) t = fma_x(-A[i][k], A[j][k], t);
+                A[i][j] = mul_x(t, dinv[j]);
             }
         }
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             double t = b[i];
 #pragma unroll
-            for (int k = 0; k < i; ++k) t -= A[i][k] * b[k];
-            b[i] = t * dinv[i];
+            for (int k = 0; k < i; ++k) t = fma_x(-A[i][k], b[k], t);
+            b[i] = mul_x(t, dinv[i]);
         }
 #pragma unroll
         for (int i = 5; i >= 0; --i) {
             double t = b[i];
 #pragma unroll
-            for (int k = i + 1; k < 6; ++k) t -= A[k][i] * b[k];
-            b[i] = t * dinv[i];
+            for (int k = i + 1; k < 6; ++k) t = fma_x(-A[k][i], b[k], t);
+            b[i] = mul_x(t, dinv[i]);
         }
         if (!ok) atomicOr(D.err, kErrSolve);
 #pragma unroll
@@ -688,11 +617,11 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_links(DevParams P, DevPtrs 
     for (int a = 0; a < 6; ++a) {
         double zv = 0.0;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) zv += zeta[a][c] * V[c];
+        for (int c = 0; c < 6; ++c) zv = fma_x(zeta[a][c], V[c], zv);
         if (a < 3)
-            dp.force[a] = F0[a] - zv;
+            dp.force[a] = add_x(F0[a], -zv);
         else
-            dp.torque[a - 3] = F0[a] - zv;
+            dp.torque[a - 3] = add_x(F0[a], -zv);
     }
     const int L[3] = {P.nx, P.ny, P.nz};
 #pragma unroll
@@ -703,7 +632,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_links(DevParams P, DevPtrs 
         dp.Wf[a] = (float)V[3 + a];
         dp.imp_f[a] = 0.0;
         dp.imp_t[a] = 0.0;
-        double X = q.X[a] + V[a];
+        double X = add_x(q.X[a], V[a]);
         if (P.per[a]) {
             if (X >= L[a])
                 X -= L[a];
@@ -716,18 +645,19 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_links(DevParams P, DevPtrs 
         dp.mn[a] = q.m[a];
     }
     // rotate m by the angle |Omega| about Omega (Rodrigues), renormalise
-    const double w = sqrt(V[3] * V[3] + V[4] * V[4] + V[5] * V[5]);
+    const double w = sqrt(dot_x(V[3], V[4], V[5], V[3], V[4], V[5]));
     if (w > 0.0) {
         const double k3[3] = {V[3] / w, V[4] / w, V[5] / w};
         const double c = cos(w), sn = sin(w);
         const double* m = q.m;
-        const double kxm[3] = {k3[1] * m[2] - k3[2] * m[1], k3[2] * m[0] - k3[0] * m[2],
-                               k3[0] * m[1] - k3[1] * m[0]};
-        const double km = k3[0] * m[0] + k3[1] * m[1] + k3[2] * m[2];
+        const double kxm[3] = {cross_x(k3[1], m[2], k3[2], m[1]), cross_x(k3[2], m[0], k3[0], m[2]),
+                               cross_x(k3[0], m[1], k3[1], m[0])};
+        const double km = dot_x(k3[0], k3[1], k3[2], m[0], m[1], m[2]);
         double mn[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) mn[a] = m[a] * c + kxm[a] * sn + k3[a] * km * (1.0 - c);
-        const double nn = sqrt(mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]);
+        for (int a = 0; a < 3; ++a)
+            mn[a] = fma_x(mul_x(k3[a], km), add_x(1.0, -c), fma_x(kxm[a], sn, mul_x(m[a], c)));
+        const double nn = sqrt(dot_x(mn[0], mn[1], mn[2], mn[0], mn[1], mn[2]));
 #pragma unroll
         for (int a = 0; a < 3; ++a) dp.mn[a] = mn[a] / nn;
     }
@@ -743,14 +673,11 @@ __device__ __forceinline__ bool near_wall(const DevParams& P, int x, int y, int 
 }
 
 template <class C>
-__global__ void __launch_bounds__(kRowThreads, 6) k_collide(DevParams P, DevPtrs D)
+__device__ __forceinline__ void collide_node(const DevParams& P, const DevPtrs& D, int x, int y, int z)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
     using S = typename C::pop_t;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= P.nx) return;
     const int n = x + P.nx * (y + P.ny * z);
     if (D.mask[n]) return;
     const PrmR<R>& Q = prm<R>(P);
@@ -836,13 +763,10 @@ __global__ void __launch_bounds__(kRowThreads, 6) k_collide(DevParams P, DevPtrs
 // S4: psi and phi transport, production and sink, one thread per node
 // ---------------------------------------------------------------------------
 template <class C>
-__global__ void __launch_bounds__(kRowThreads) k_scalars(DevParams P, DevPtrs D)
+__device__ __forceinline__ void scalars_node(const DevParams& P, const DevPtrs& D, int x, int y, int z)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= P.nx) return;
     const int n = x + P.nx * (y + P.ny * z);
     if (D.mask[n]) return;
     const PrmR<R>& Q = prm<R>(P);
@@ -936,14 +860,13 @@ __device__ __forceinline__ void cover_origin(const DevParams& P, const DevPart& 
 }
 
 template <class C>
-__global__ void __launch_bounds__(kPartThreads) k_cover_mark(DevParams P, DevPtrs D)
+__device__ __forceinline__ void cover_mark_block(const DevParams& P, const DevPtrs& D, int p, int bi, int nbi)
 {
-    const int p = blockIdx.y;
     const DevPart& q = D.parts[p];
     int o[3];
     cover_origin(P, q, o);
     const int tot = P.side2[0] * P.side2[1] * P.side2[2];
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+    for (int t = bi * blockDim.x + threadIdx.x; t < tot; t += nbi * blockDim.x) {
         int x, y, z;
         if (!box_node(P, o, P.side2, t, x, y, z)) continue;
         uint8_t own = 0;
@@ -956,16 +879,19 @@ __global__ void __launch_bounds__(kPartThreads) k_cover_mark(DevParams P, DevPtr
     }
 }
 
+//
+// cover_apply_block runs block bi of the nbi blocks of particle p; the last of
+// the np * nbi blocks of the box (a ticket) finishes the step for all
+// particles of the box.  smem holds block_sum_t_bytes<kCoverK>(blockDim.x)
+// bytes.
 template <class C>
-__global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPtrs D)
+__device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevPtrs& D, int p, int bi, int nbi,
+                                                  double* smem, bool& last)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
     using S = typename C::pop_t;
     constexpr int K = kCoverK;
-    __shared__ double smem[block_sum_t_bytes<K>(kPartThreads) / sizeof(double)];
-    __shared__ bool last;
-    const int p = blockIdx.y;
     const DevPart& q = D.parts[p];
     const size_t N = (size_t)P.N;
     int o[3];
@@ -982,7 +908,7 @@ __global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPt
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+    for (int t = bi * blockDim.x + threadIdx.x; t < tot; t += nbi * blockDim.x) {
         int x, y, z;
         if (!box_node(P, o, P.side2, t, x, y, z)) continue;
         const int n = x + P.nx * (y + P.ny * z);
@@ -1013,8 +939,9 @@ __global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPt
                 R r[3], ub[3], vs[3];
                 link_velocity<R>(P, q, x, y, z, i, gphi, r, ub, vs);
                 const R cub = cdot<R>(i, ub[0], ub[1], ub[2]);
-                a9 += (R)6 * wgt_r<R>(i) * (cub * ps);
-                a10 += (R)6 * wgt_r<R>(i) * (cub * ph);
+                const R w6 = (R)6 * wgt_r<R>(i);
+                a9 = fma_x(w6, mul_x(cub, ps), a9);
+                a10 = fma_x(w6, mul_x(cub, ph), a10);
             }
             acc[9] += (double)a9;
             acc[10] += (double)a10;
@@ -1036,9 +963,9 @@ __global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPt
             acc[0] += j[0];
             acc[1] += j[1];
             acc[2] += j[2];
-            acc[3] += r[1] * j[2] - r[2] * j[1];
-            acc[4] += r[2] * j[0] - r[0] * j[2];
-            acc[5] += r[0] * j[1] - r[1] * j[0];
+            acc[3] += cross_x(r[1], j[2], r[2], j[1]);
+            acc[4] += cross_x(r[2], j[0], r[0], j[2]);
+            acc[5] += cross_x(r[0], j[1], r[1], j[0]);
             acc[6] += (double)psi[n];
             acc[7] += (double)phi[n];
             acc[8] -= 1.0;
@@ -1069,8 +996,9 @@ __global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPt
             }
             double r[3];
             offset_from(P, q.Xn, x, y, z, r);
-            const double ub[3] = {q.U[0] + (q.W[1] * r[2] - q.W[2] * r[1]), q.U[1] + (q.W[2] * r[0] - q.W[0] * r[2]),
-                                  q.U[2] + (q.W[0] * r[1] - q.W[1] * r[0])};
+            const double ub[3] = {add_x(q.U[0], cross_x(q.W[1], r[2], q.W[2], r[1])),
+                                  add_x(q.U[1], cross_x(q.W[2], r[0], q.W[0], r[2])),
+                                  add_x(q.U[2], cross_x(q.W[0], r[1], q.W[1], r[0]))};
 #pragma unroll
             for (int i = 0; i < 19; ++i)
                 PopStore<S>::store(f, (size_t)i * N + n, i, rho0, (R)feq_i<double>(i, rb, ub[0], ub[1], ub[2]));
@@ -1079,13 +1007,13 @@ __global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPt
             u[2 * N + n] = (F)ub[2];
             psi[n] = (F)pb;
             phi[n] = (F)hb;
-            const double j[3] = {rb * ub[0], rb * ub[1], rb * ub[2]};
+            const double j[3] = {mul_x(rb, ub[0]), mul_x(rb, ub[1]), mul_x(rb, ub[2])};
             acc[0] -= j[0];
             acc[1] -= j[1];
             acc[2] -= j[2];
-            acc[3] -= r[1] * j[2] - r[2] * j[1];
-            acc[4] -= r[2] * j[0] - r[0] * j[2];
-            acc[5] -= r[0] * j[1] - r[1] * j[0];
+            acc[3] -= cross_x(r[1], j[2], r[2], j[1]);
+            acc[4] -= cross_x(r[2], j[0], r[0], j[2]);
+            acc[5] -= cross_x(r[0], j[1], r[1], j[0]);
             acc[6] -= pb;
             acc[7] -= hb;
             acc[8] += 1.0;
@@ -1094,11 +1022,11 @@ __global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPt
         }
     }
     block_sum_t<K>(acc, smem);
-    double* part = D.cover_part + ((size_t)p * kMaxPartBlocks + blockIdx.x) * K;
+    double* part = D.cover_part + ((size_t)p * kMaxPartBlocks + bi) * K;
     if (threadIdx.x == 0) {
         for (int k = 0; k < K; ++k) part[k] = acc[k];
         __threadfence();
-        last = (atomicAdd(D.cover_ticket, 1u) == gridDim.x * gridDim.y - 1);
+        last = (atomicAdd(D.cover_ticket, 1u) == (unsigned)(nbi * P.np) - 1u);
     }
     __syncthreads();
     if (!last) return;
@@ -1107,11 +1035,11 @@ __global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPt
     // particles, deficits into the uniform correction, particles move
     __threadfence();
     double dsum_psi = 0.0, dsum_phi = 0.0, dcnt = 0.0;
-    for (int k = 0; k < (int)gridDim.y; ++k) {
+    for (int k = 0; k < P.np; ++k) {
         double s[K];
 #pragma unroll
         for (int c = 0; c < K; ++c) s[c] = 0.0;
-        if (threadIdx.x < gridDim.x) {
+        if ((int)threadIdx.x < nbi) {
             const double* cp = D.cover_part + ((size_t)k * kMaxPartBlocks + threadIdx.x) * K;
 #pragma unroll
             for (int c = 0; c < K; ++c) s[c] = __ldcg(cp + c);
@@ -1138,6 +1066,61 @@ __global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPt
     D.corr_f[0] = (float)D.corr[0];
     D.corr_f[1] = (float)D.corr[1];
     *D.cover_ticket = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// single-box kernels: a row grid (x blocks, y, z) over the box for the node
+// bodies; grid (blocks per particle, particles) for the particle bodies
+// ---------------------------------------------------------------------------
+template <class C>
+__global__ void __launch_bounds__(kRowThreads) k_mup(DevParams P, DevPtrs D)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < P.nx) mup_node<C>(P, D, x, blockIdx.y, blockIdx.z);
+}
+
+template <class C>
+__global__ void __launch_bounds__(kRowThreads) k_fdiv(DevParams P, DevPtrs D)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < P.nx) fdiv_node<C>(P, D, x, blockIdx.y, blockIdx.z);
+}
+
+template <class C>
+__global__ void __launch_bounds__(kRowThreads, 6) k_collide(DevParams P, DevPtrs D)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < P.nx) collide_node<C>(P, D, x, blockIdx.y, blockIdx.z);
+}
+
+template <class C>
+__global__ void __launch_bounds__(kRowThreads) k_scalars(DevParams P, DevPtrs D)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < P.nx) scalars_node<C>(P, D, x, blockIdx.y, blockIdx.z);
+}
+
+template <class C>
+__global__ void __launch_bounds__(kPartThreads, 1) k_links(DevParams P, DevPtrs D)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];   // block_sum_t_bytes<kLinkK>(kPartThreads)
+    __shared__ DevPart sp;
+    __shared__ bool last;
+    links_block<C>(P, D, blockIdx.y, blockIdx.x, gridDim.x, (double*)smem_raw, sp, last);
+}
+
+template <class C>
+__global__ void __launch_bounds__(kPartThreads) k_cover_mark(DevParams P, DevPtrs D)
+{
+    cover_mark_block<C>(P, D, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
+template <class C>
+__global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPtrs D)
+{
+    __shared__ double smem[block_sum_t_bytes<kCoverK>(kPartThreads) / sizeof(double)];
+    __shared__ bool last;
+    cover_apply_block<C>(P, D, blockIdx.y, blockIdx.x, gridDim.x, smem, last);
 }
 
 // ---------------------------------------------------------------------------

@@ -21,6 +21,30 @@ namespace lbdp {
 
 constexpr int kMaxParticles = 64;
 
+// Arithmetic with its rounding written out.  The particle sums and solve,
+// the boundary velocities and the refill of uncovered nodes are inlined into
+// the single-box and the batched kernels; with every multiply-add fused or
+// not fused in the source the compiler has no choice left, and both give the
+// same bits.
+__device__ __forceinline__ double fma_x(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_x(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double mul_x(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_x(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_x(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_x(float a, float b) { return __fadd_rn(a, b); }
+// a b - c d
+template <class R>
+__device__ __forceinline__ R cross_x(R a, R b, R c, R d)
+{
+    return fma_x(a, b, -mul_x(c, d));
+}
+// a . b of 3-vectors
+template <class R>
+__device__ __forceinline__ R dot_x(R a0, R a1, R a2, R b0, R b1, R b2)
+{
+    return fma_x(a0, b0, fma_x(a1, b1, mul_x(a2, b2)));
+}
+
 // ---------------------------------------------------------------------------
 // D3Q19 (order given in include/lbdp.h)
 // ---------------------------------------------------------------------------
@@ -182,11 +206,11 @@ template <>
 struct PopStore<float> {
     static __device__ __forceinline__ float load(const float* p, size_t k, int i, float rho0)
     {
-        return p[k] + wgt_r<float>(i) * rho0;
+        return fma_x(wgt_r<float>(i), rho0, p[k]);
     }
     static __device__ __forceinline__ void store(float* p, size_t k, int i, float rho0, float f)
     {
-        p[k] = f - wgt_r<float>(i) * rho0;
+        p[k] = fma_x(-wgt_r<float>(i), rho0, f);
     }
 };
 
@@ -200,7 +224,7 @@ struct PopStore<__half> {
     }
     static __device__ __forceinline__ void store(__half* p, size_t k, int i, float rho0, float f)
     {
-        p[k] = __float2half_rn(f * inv_wgt_r<float>(i) - rho0);
+        p[k] = __float2half_rn(fma_x(f, inv_wgt_r<float>(i), -rho0));
     }
 };
 
@@ -212,7 +236,7 @@ struct PopStore<__nv_bfloat16> {
     }
     static __device__ __forceinline__ void store(__nv_bfloat16* p, size_t k, int i, float rho0, float f)
     {
-        p[k] = __float2bfloat16_rn(f * inv_wgt_r<float>(i) - rho0);
+        p[k] = __float2bfloat16_rn(fma_x(f, inv_wgt_r<float>(i), -rho0));
     }
 };
 

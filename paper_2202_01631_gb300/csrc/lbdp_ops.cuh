@@ -3,6 +3,7 @@
 // modes compile in parallel.
 #pragma once
 
+#include "lbdp_batch_kernels.cuh"
 #include "lbdp_internal.h"
 #include "lbdp_kernels.cuh"
 
@@ -112,6 +113,85 @@ struct Ops {
         t.get_fields = &get_fields;
         t.get_pop = &get_pop;
         t.sums = &sums;
+        return t;
+    }
+};
+
+// Launchers of the batched kernels of one precision configuration.
+template <class C>
+struct BOps {
+    using KFn = void (*)(const BatchDev*);
+
+    template <int NC>
+    static KFn node_fn(int cfg)
+    {
+        static_assert(kNumBatchCfgs == 4, "configuration table");
+        switch (cfg) {
+            case 0: return kb_node<C, NC, 128, 1, 0, 0>;
+            case 1: return kb_node<C, NC, 128, 1, 0, 1>;
+            case 2: return kb_node<C, NC, 256, 1, 1, 1>;
+            default: return kb_node<C, NC, 128, 2, 1, 1>;
+        }
+    }
+
+    static KFn fn(int nc, int cfg)
+    {
+        switch (nc) {
+            case kNcMup: return node_fn<kNcMup>(cfg);
+            case kNcFdiv: return node_fn<kNcFdiv>(cfg);
+            case kNcCollide: return node_fn<kNcCollide>(cfg);
+            default: return node_fn<kNcScalars>(cfg);
+        }
+    }
+
+    static cudaError_t prepare()
+    {
+        static bool done[64] = {false};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+        e = cudaFuncSetAttribute(kb_links<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)block_sum_t_bytes<kLinkK>(kPartThreads));
+        if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+        return e;
+    }
+
+    static cudaError_t node_grid(int nc, int cfg, int* blocks_per_sm)
+    {
+        if (nc < 0 || nc >= kNumNodeClasses || cfg < 0 || cfg >= kNumBatchCfgs) return cudaErrorInvalidValue;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn(nc, cfg), kBatchCfgs[cfg].threads, 0);
+    }
+
+    static cudaError_t node(int nc, int cfg, int grid, const BatchDev* B, cudaStream_t s)
+    {
+        if (nc < 0 || nc >= kNumNodeClasses || cfg < 0 || cfg >= kNumBatchCfgs) return cudaErrorInvalidValue;
+        void* args[] = {(void*)&B};
+        return cudaLaunchKernel((const void*)fn(nc, cfg), dim3(grid), dim3(kBatchCfgs[cfg].threads), args, 0, s);
+    }
+
+    static cudaError_t step(const int cfg[4], const int grid[4], int part_grid, const BatchDev* B, cudaStream_t s)
+    {
+        cudaError_t e = prepare();
+        if (e != cudaSuccess) return e;
+        if ((e = node(kNcMup, cfg[0], grid[0], B, s)) != cudaSuccess) return e;
+        if ((e = node(kNcFdiv, cfg[1], grid[1], B, s)) != cudaSuccess) return e;
+        kb_links<C><<<part_grid, kPartThreads, block_sum_t_bytes<kLinkK>(kPartThreads), s>>>(B);
+        if ((e = node(kNcCollide, cfg[2], grid[2], B, s)) != cudaSuccess) return e;
+        if ((e = node(kNcScalars, cfg[3], grid[3], B, s)) != cudaSuccess) return e;
+        kb_cover_mark<C><<<part_grid, kPartThreads, 0, s>>>(B);
+        kb_cover_apply<C><<<part_grid, kPartThreads, 0, s>>>(B);
+        kb_advance<<<(kBatchMaxBoxes + 255) / 256, 256, 0, s>>>(B);
+        return cudaGetLastError();
+    }
+
+    static BatchOps table()
+    {
+        BatchOps t;
+        t.prepare = &prepare;
+        t.node_grid = &node_grid;
+        t.node = &node;
+        t.step = &step;
         return t;
     }
 };

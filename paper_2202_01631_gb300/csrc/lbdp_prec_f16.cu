@@ -1,4 +1,4 @@
-// Kernels and launchers of the CfgF16 precision mode.
+// Single-box kernels and launchers of the CfgF16 precision mode.
 #include "lbdp_ops.cuh"
 
 namespace lbdp {

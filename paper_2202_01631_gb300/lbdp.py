@@ -58,6 +58,29 @@ class LbParticleState(C.Structure):
     _fields_ = [(k, C.c_double * 3) for k in ("pos", "vel", "omega", "m_hat", "force", "torque")]
 
 
+class LbbParams(C.Structure):
+    _fields_ = [("precision", C.c_int), ("arena_bytes", C.c_size_t), ("graph_steps", C.c_int),
+                ("cuda_stream", C.c_void_p)]
+
+
+class LbsParams(C.Structure):
+    _fields_ = [("precision", C.c_int), ("arena_bytes", C.c_size_t), ("chunk_steps", C.c_int),
+                ("max_boxes", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class LbsRequest(C.Structure):
+    _fields_ = [("box", LbParams), ("n_particles", C.c_int), ("particles", LbParticleDesc * 4),
+                ("psi", C.POINTER(C.c_double)), ("phi", C.POINTER(C.c_double)),
+                ("steps", C.c_longlong), ("arrival", C.c_double),
+                ("out_psi", C.POINTER(C.c_double)), ("out_phi", C.POINTER(C.c_double))]
+
+
+class LbsResult(C.Structure):
+    _fields_ = [("id", C.c_longlong), ("status", C.c_int),
+                ("arrival", C.c_double), ("admitted", C.c_double), ("done", C.c_double),
+                ("n_particles", C.c_int), ("particles", LbParticleState * 4), ("sums", C.c_double * 3)]
+
+
 class LbError(RuntimeError):
     def __init__(self, status: int, where: str):
         super().__init__("%s: %s (%s)" % (where, STATUS.get(status, status), _err_string(status)))
@@ -92,6 +115,32 @@ def _load():
         "lb_wetting_h": (C.c_double, [C.c_double]),
         "lb_solubility_E": (C.c_double, [C.c_double, C.c_double]),
         "lb_error_string": (C.c_char_p, [C.c_int]),
+        # batches, arena, server (include/lbdp_batch.h)
+        "lb_arena_create": (C.c_int, [C.c_size_t, P(h)]),
+        "lb_arena_alloc": (C.c_int, [h, C.c_size_t, P(C.c_size_t)]),
+        "lb_arena_free": (C.c_int, [h, C.c_size_t]),
+        "lb_arena_stats": (C.c_int, [h, P(C.c_size_t), P(C.c_size_t), P(C.c_int)]),
+        "lb_arena_destroy": (None, [h]),
+        "lbb_create": (C.c_int, [P(LbbParams), P(h)]),
+        "lbb_destroy": (None, [h]),
+        "lbb_box_bytes": (C.c_int, [h, P(LbParams), P(C.c_size_t)]),
+        "lbb_memory": (C.c_int, [h, P(C.c_size_t), P(C.c_size_t), P(C.c_size_t)]),
+        "lbb_add_box": (C.c_int, [h, P(LbParams), P(h)]),
+        "lbb_num_boxes": (C.c_int, [h]),
+        "lbb_set_steps": (C.c_int, [h, h, C.c_longlong]),
+        "lbb_get_steps": (C.c_int, [h, h, P(C.c_longlong)]),
+        "lbb_run": (C.c_int, [h, C.c_int, P(C.c_longlong)]),
+        "lbb_tune": (C.c_int, [h, C.c_int, P(C.c_int), dp]),
+        "lbb_set_config": (C.c_int, [h, P(C.c_int)]),
+        "lbb_num_configs": (C.c_int, []),
+        "lbb_config_shape": (C.c_int, [C.c_int, P(C.c_int), P(C.c_int), P(C.c_int)]),
+        "lbb_sync": (C.c_int, [h]),
+        "lbs_create": (C.c_int, [P(LbsParams), P(h)]),
+        "lbs_destroy": (None, [h]),
+        "lbs_submit": (C.c_int, [h, P(LbsRequest), P(C.c_longlong)]),
+        "lbs_pump": (C.c_int, [h, C.c_double, P(C.c_int), P(C.c_int)]),
+        "lbs_poll": (C.c_int, [h, P(LbsResult), C.c_int, P(C.c_int)]),
+        "lbs_batch": (h, [h]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -248,6 +297,259 @@ def particle_desc(**kw) -> LbParticleDesc:
     return d
 
 
+def box_params(precision="fp64", stream=None, **params) -> LbParams:
+    """:class:`LbParams` from keyword parameters; ``solubility_ratio`` (if
+    present and ``E`` absent) is mapped to ``E`` by :func:`lb_solubility_E`."""
+    q = dict(params)
+    if "E" not in q and "solubility_ratio" in q:
+        q["E"] = lb_solubility_E(q["solubility_ratio"], q.get("phi_b", 0.0))
+    q.pop("solubility_ratio", None)
+    q["precision"] = precision
+    if stream is not None:
+        q["cuda_stream"] = stream
+    return lb_params(**q)
+
+
+# ---------------------------------------------------------------------------
+# arena, batches, server (include/lbdp_batch.h)
+# ---------------------------------------------------------------------------
+
+def lb_arena_create(capacity: int) -> int:
+    a = C.c_void_p()
+    _check(_lib.lb_arena_create(int(capacity), C.byref(a)), "lb_arena_create")
+    return a.value
+
+
+def lb_arena_alloc(a, nbytes: int) -> int:
+    off = C.c_size_t(0)
+    _check(_lib.lb_arena_alloc(a, int(nbytes), C.byref(off)), "lb_arena_alloc")
+    return int(off.value)
+
+
+def lb_arena_free(a, offset: int) -> None:
+    _check(_lib.lb_arena_free(a, int(offset)), "lb_arena_free")
+
+
+def lb_arena_stats(a):
+    """(used, largest_free, free_ranges)"""
+    u, big, n = C.c_size_t(0), C.c_size_t(0), C.c_int(0)
+    _check(_lib.lb_arena_stats(a, C.byref(u), C.byref(big), C.byref(n)), "lb_arena_stats")
+    return int(u.value), int(big.value), n.value
+
+
+def lb_arena_destroy(a) -> None:
+    _lib.lb_arena_destroy(a)
+
+
+def lbb_create(precision="fp32", arena_bytes=0, graph_steps=0, stream=None) -> int:
+    p = LbbParams()
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    p.arena_bytes = int(arena_bytes)
+    p.graph_steps = int(graph_steps)
+    p.cuda_stream = stream
+    b = C.c_void_p()
+    _check(_lib.lbb_create(C.byref(p), C.byref(b)), "lbb_create")
+    return b.value
+
+
+def lbb_destroy(b) -> None:
+    _lib.lbb_destroy(b)
+
+
+def lbb_add_box(b, params: LbParams) -> int:
+    h = C.c_void_p()
+    _check(_lib.lbb_add_box(b, C.byref(params), C.byref(h)), "lbb_add_box")
+    return h.value
+
+
+def lbb_box_bytes(b, params: LbParams) -> int:
+    n = C.c_size_t(0)
+    _check(_lib.lbb_box_bytes(b, C.byref(params), C.byref(n)), "lbb_box_bytes")
+    return int(n.value)
+
+
+def lbb_memory(b):
+    """(capacity, used, largest_free)"""
+    c, u, big = C.c_size_t(0), C.c_size_t(0), C.c_size_t(0)
+    _check(_lib.lbb_memory(b, C.byref(c), C.byref(u), C.byref(big)), "lbb_memory")
+    return int(c.value), int(u.value), int(big.value)
+
+
+def lbb_set_steps(b, h, nsteps: int) -> None:
+    _check(_lib.lbb_set_steps(b, h, int(nsteps)), "lbb_set_steps")
+
+
+def lbb_get_steps(b, h) -> int:
+    n = C.c_longlong(0)
+    _check(_lib.lbb_get_steps(b, h, C.byref(n)), "lbb_get_steps")
+    return int(n.value)
+
+
+def lbb_run(b, nsteps: int) -> int:
+    """Queue nsteps batch steps; returns the number of kernel launches queued."""
+    n = C.c_longlong(0)
+    _check(_lib.lbb_run(b, int(nsteps), C.byref(n)), "lbb_run")
+    return int(n.value)
+
+
+def lbb_tune(b, reps: int = 10):
+    """Autotune the node kernels; returns (configs[4], ms[4])."""
+    cfg = (C.c_int * 4)()
+    ms = np.zeros(4)
+    _check(_lib.lbb_tune(b, int(reps), cfg, _dptr(ms)), "lbb_tune")
+    return list(cfg), ms.tolist()
+
+
+def lbb_set_config(b, cfg) -> None:
+    _check(_lib.lbb_set_config(b, (C.c_int * 4)(*[int(c) for c in cfg])), "lbb_set_config")
+
+
+def lbb_num_configs() -> int:
+    return int(_lib.lbb_num_configs())
+
+
+def lbb_config_shape(k: int):
+    """(threads, cells per thread, register budget) of candidate k."""
+    t, c, r = C.c_int(0), C.c_int(0), C.c_int(0)
+    _check(_lib.lbb_config_shape(int(k), C.byref(t), C.byref(c), C.byref(r)), "lbb_config_shape")
+    return t.value, c.value, r.value
+
+
+def lbb_sync(b) -> None:
+    _check(_lib.lbb_sync(b), "lbb_sync")
+
+
+class Batch:
+    """Boxes of one precision mode advanced together (:func:`lbb_run`)."""
+
+    def __init__(self, precision="fp32", arena_bytes=0, graph_steps=0, stream=None, _handle=None):
+        self.precision = precision
+        self.own = _handle is None
+        self.h = _handle if _handle is not None else lbb_create(precision, arena_bytes, graph_steps, stream)
+        self.boxes = set()
+
+    def add_box(self, **params) -> Box:
+        b = Box(precision=self.precision, _batch=self, **params)
+        self.boxes.add(b)
+        return b
+
+    def box_bytes(self, **params) -> int:
+        return lbb_box_bytes(self.h, box_params(self.precision, None, **params))
+
+    def memory(self):
+        return lbb_memory(self.h)
+
+    def set_steps(self, box: Box, nsteps: int):
+        lbb_set_steps(self.h, box.h, nsteps)
+
+    def steps_left(self, box: Box) -> int:
+        return lbb_get_steps(self.h, box.h)
+
+    def run(self, nsteps: int) -> int:
+        return lbb_run(self.h, nsteps)
+
+    def tune(self, reps: int = 10):
+        return lbb_tune(self.h, reps)
+
+    def set_config(self, cfg):
+        lbb_set_config(self.h, cfg)
+
+    def sync(self):
+        lbb_sync(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            for b in list(self.boxes):
+                b.h = None   # lbb_destroy destroys the member boxes
+            self.boxes.clear()
+            if self.own:
+                lbb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous batching (:func:`lbs_pump`): requests are admitted into a
+    batch as memory frees up and leave when their steps are done."""
+
+    def __init__(self, precision="fp32", arena_bytes=0, chunk_steps=0, max_boxes=0, stream=None):
+        p = LbsParams()
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p.arena_bytes = int(arena_bytes)
+        p.chunk_steps = int(chunk_steps)
+        p.max_boxes = int(max_boxes)
+        p.cuda_stream = stream
+        self.precision = precision
+        h = C.c_void_p()
+        _check(_lib.lbs_create(C.byref(p), C.byref(h)), "lbs_create")
+        self.h = h.value
+        self.batch = Batch(precision, _handle=_lib.lbs_batch(self.h))
+        self._keep = {}
+
+    def submit(self, box: Dict, particles=(), psi=None, phi=None, steps=1, arrival=0.0,
+               out_psi=None, out_phi=None) -> int:
+        r = LbsRequest()
+        r.box = box_params(self.precision, None, **box)
+        r.n_particles = len(particles)
+        for k, d in enumerate(particles):
+            r.particles[k] = particle_desc(**d)
+        keep = []
+        for name, a in (("psi", psi), ("phi", phi)):
+            if a is not None:
+                a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+                keep.append(a)
+                setattr(r, name, _dptr(a))
+        for name, a in (("out_psi", out_psi), ("out_phi", out_phi)):
+            if a is not None:
+                if not (a.flags.c_contiguous and a.dtype == np.float64):
+                    raise ValueError("%s must be a C-contiguous float64 array" % name)
+                setattr(r, name, _dptr(a))
+        r.steps = int(steps)
+        r.arrival = float(arrival)
+        rid = C.c_longlong(-1)
+        _check(_lib.lbs_submit(self.h, C.byref(r), C.byref(rid)), "lbs_submit")
+        self._keep[rid.value] = (out_psi, out_phi)   # output buffers stay alive until polled
+        return rid.value
+
+    def pump(self, now: float):
+        """One round; returns (active, queued)."""
+        a, q = C.c_int(0), C.c_int(0)
+        _check(_lib.lbs_pump(self.h, float(now), C.byref(a), C.byref(q)), "lbs_pump")
+        return a.value, q.value
+
+    def poll(self, cap: int = 64) -> List[Dict]:
+        out = (LbsResult * cap)()
+        n = C.c_int(0)
+        _check(_lib.lbs_poll(self.h, out, cap, C.byref(n)), "lbs_poll")
+        res = []
+        for k in range(n.value):
+            r = out[k]
+            self._keep.pop(r.id, None)
+            res.append(dict(id=r.id, status=r.status, arrival=r.arrival, admitted=r.admitted, done=r.done,
+                            particles=[{f: np.array(getattr(r.particles[j], f)[:])
+                                        for f in ("pos", "vel", "omega", "m_hat", "force", "torque")}
+                                       for j in range(r.n_particles)],
+                            sums=np.array(r.sums[:])))
+        return res
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.batch.h = None
+            _lib.lbs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------------------
 # convenience wrapper
 # ---------------------------------------------------------------------------
@@ -260,16 +562,10 @@ class Box:
     Arrays use the [nz, ny, nx] shape of the node index x + nx (y + ny z).
     """
 
-    def __init__(self, precision="fp64", stream=None, **params):
-        q = dict(params)
-        if "E" not in q and "solubility_ratio" in q:
-            q["E"] = lb_solubility_E(q["solubility_ratio"], q.get("phi_b", 0.0))
-        q.pop("solubility_ratio", None)
-        q["precision"] = precision
-        if stream is not None:
-            q["cuda_stream"] = stream
-        self.params = lb_params(**q)
-        self.h = lb_create(self.params)
+    def __init__(self, precision="fp64", stream=None, _batch=None, **params):
+        self.params = box_params(precision, stream, **params)
+        self.batch = _batch
+        self.h = lbb_add_box(_batch.h, self.params) if _batch is not None else lb_create(self.params)
         self.shape = (self.params.nz, self.params.ny, self.params.nx)
         self.N = self.params.nx * self.params.ny * self.params.nz
         self.np = 0
@@ -278,6 +574,8 @@ class Box:
         if getattr(self, "h", None):
             lb_destroy(self.h)
             self.h = None
+            if self.batch is not None:
+                self.batch.boxes.discard(self)
 
     def __del__(self):
         try:

@@ -1,6 +1,6 @@
-"""The C ABI library loads and exports every symbol include/lbdp.h declares,
-and the ctypes structures match the C layout (no GPU needed: no compute
-calls are made)."""
+"""The C ABI library loads and exports every symbol include/lbdp.h and
+include/lbdp_batch.h declare, and the ctypes structures match the C layout
+(no GPU needed: no compute calls are made)."""
 import ctypes as C
 import os
 import re
@@ -9,7 +9,7 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HDR = os.path.join(ROOT, "include", "lbdp.h")
+HDRS = [os.path.join(ROOT, "include", h) for h in ("lbdp.h", "lbdp_batch.h")]
 
 
 @pytest.fixture(scope="module")
@@ -19,15 +19,19 @@ def built():
 
 
 def declared_functions():
-    text = open(HDR).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(lb_[a-z_]+)\s*\(", text)))
+    names = set()
+    for hdr in HDRS:
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(lb[bs]?_[a-z_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = declared_functions()
     for need in ("lb_create", "lb_set_fields", "lb_add_particle", "lb_step", "lb_read_fields",
-                 "lb_read_particles", "lb_conservation", "lb_destroy"):
+                 "lb_read_particles", "lb_conservation", "lb_destroy", "lbb_create", "lbb_add_box",
+                 "lbb_run", "lbb_tune", "lbs_submit", "lbs_pump", "lbs_poll", "lb_arena_alloc"):
         assert need in names
 
 
@@ -36,7 +40,7 @@ def test_library_exports_every_declared_symbol(built):
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, missing
     out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True).stdout
-    exported = set(re.findall(r"\bT (lb_[a-z_]+)\b", out))
+    exported = set(re.findall(r"\bT (lb[bs]?_[a-z_]+)\b", out))
     assert set(declared_functions()) <= exported
 
 
@@ -59,12 +63,12 @@ def test_host_only_entry_points(built):
 def test_struct_layout_matches_header(tmp_path, built):
     from paper_2202_01631_gb300 import lbdp
     src = tmp_path / "layout.c"
-    fields = {
-        "lb_params": [f for f, _ in lbdp.LbParams._fields_],
-        "lb_particle_desc": [f for f, _ in lbdp.LbParticleDesc._fields_],
-        "lb_particle_state": [f for f, _ in lbdp.LbParticleState._fields_],
-    }
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbdp.h"', "int main(void){"]
+    structs = (("lb_params", lbdp.LbParams), ("lb_particle_desc", lbdp.LbParticleDesc),
+               ("lb_particle_state", lbdp.LbParticleState), ("lbb_params", lbdp.LbbParams),
+               ("lbs_params", lbdp.LbsParams), ("lbs_request", lbdp.LbsRequest),
+               ("lbs_result", lbdp.LbsResult))
+    fields = {s: [f for f, _ in cls._fields_] for s, cls in structs}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbdp_batch.h"', "int main(void){"]
     for s, fs in fields.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (s, s))
         for f in fs:
@@ -74,8 +78,7 @@ def test_struct_layout_matches_header(tmp_path, built):
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split("\n") if l)
-    for s, cls in (("lb_params", lbdp.LbParams), ("lb_particle_desc", lbdp.LbParticleDesc),
-                   ("lb_particle_state", lbdp.LbParticleState)):
+    for s, cls in structs:
         assert int(got[s]) == C.sizeof(cls)
         for f, _ in cls._fields_:
             assert int(got["%s.%s" % (s, f)]) == getattr(cls, f).offset, (s, f)
