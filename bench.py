@@ -12,6 +12,13 @@ Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle (the
 reference implementation written from the paper) on the host cores instead.
 Multi-GPU runs (torchrun) are independent replicas: the boxes do not share
 data, so there is no collective on the data path.
+
+``--form batched`` times 64 uneven boxes (edges 32..96, one sphere each)
+advanced together through the batched kernels and CUDA graphs after
+autotuning, against the same boxes run one by one with the single-box path;
+``--form served`` replays a seeded Poisson request stream through the
+continuous-batching server and reports p50/p99 time-to-result and sims/hour,
+against a one-by-one FIFO server.  The default form is the single box.
 """
 from __future__ import annotations
 
@@ -52,6 +59,10 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
     ap.add_argument("--edge", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="single", choices=["single", "batched", "served"])
+    ap.add_argument("--boxes", type=int, default=64, help="batched form: number of boxes")
+    ap.add_argument("--requests", type=int, default=32, help="served form: number of requests")
+    ap.add_argument("--rate", type=float, default=20.0, help="served form: mean arrivals per second")
     return ap.parse_args()
 
 
@@ -359,10 +370,238 @@ def run_ours(args):
     return 0
 
 
+def _setup_member(box, wl):
+    box.set_fields(**wl.fields)
+    for p in wl.particles:
+        box.add_particle(**p)
+
+
+def run_batched(args):
+    """64 uneven boxes in one batch vs the same boxes one by one."""
+    import torch
+    world, rank, local, group = dist_setup(args)
+    torch.cuda.set_device(local)
+    from paper_2202_01631_gb300 import build
+    build.build()
+    from paper_2202_01631_gb300 import lbdp
+    from paper_2202_01631_gb300 import workloads as W
+
+    wls = W.batched(seed=0, n_boxes=args.boxes)
+    target = wls[0].steps                        # steps per simulation (5000)
+    nodes = sum(w.nodes for w in wls)
+    stream = torch.cuda.Stream()
+    batch = lbdp.Batch(precision=args.precision, arena_bytes=0, graph_steps=16, stream=stream.cuda_stream)
+    boxes = []
+    for wl in wls:
+        b = batch.add_box(**wl.params)
+        _setup_member(b, wl)
+        boxes.append(b)
+    for b in boxes:
+        batch.set_steps(b, args.warmup)
+    batch.run(args.warmup)
+    cfg, tune_ms = batch.tune(reps=5)
+    for b in boxes:
+        batch.set_steps(b, args.steps)
+    batch.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(group)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        launches = batch.run(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(group)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), group)
+    batch.sync()
+    step_ms = ms / args.steps
+    mlups = nodes * args.steps * world / (ms * 1e-3) / 1e6
+    sims_h = len(wls) * world * 3600.0 / (step_ms * 1e-3 * target)
+    peak, peak_kind = measured_peak()
+    step_gbs = ALG_BYTES_STEP[args.precision] * nodes / (step_ms * 1e-3) / 1e9
+
+    # ---- the same boxes one by one, single-box path -----------------------
+    k1 = min(args.steps, 200)
+    alone_ms = 0.0
+    for wl in wls:
+        b = lbdp.Box(precision=args.precision, stream=stream.cuda_stream, **wl.params)
+        _setup_member(b, wl)
+        b.step(10)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(k1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        alone_ms += e0.elapsed_time(e1) / k1
+        b.close()
+    alone_sims_h = len(wls) * world * 3600.0 / (alone_ms * 1e-3 * target)
+
+    # ---- end to end: host fields in, steps, psi/phi and particles out -----
+    e2e_steps = min(args.steps, 500)
+    host = [{k: torch.from_numpy(np.ascontiguousarray(wl.fields[k], dtype=np.float64)).pin_memory()
+             for k in ("psi", "phi")} for wl in wls]
+    outs = [{k: torch.empty_like(h[k]).pin_memory() for k in h} for h in host]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for b, h in zip(boxes, host):
+        lbdp.lb_set_fields(b.h, None, None, h["psi"].numpy(), h["phi"].numpy())
+        batch.set_steps(b, e2e_steps)
+    batch.run(e2e_steps)
+    for b, o in zip(boxes, outs):
+        lbdp.lb_read_fields(b.h, None, None, o["psi"].numpy(), o["phi"].numpy())
+        b.particles()
+    dt = max_over_ranks(time.perf_counter() - t0, group)
+    h2d = sum(v.numel() * 8 for h in host for v in h.values())
+    d2h = sum(v.numel() * 8 for o in outs for v in o.values()) + len(wls) * 18 * 8
+    e2e = {"value": nodes * e2e_steps * world / dt / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+           "job": "upload psi, phi of every box from pinned host memory, %d batched steps, read back "
+                  "psi, phi and particles" % e2e_steps}
+    shapes = [lbdp.lbb_config_shape(c) for c in cfg]
+    batch.close()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "batched sims/hour", "value": sims_h, "unit": "sims/hour", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+        "config": {"workload": "batched_%d_boxes_32-96" % len(wls), "nodes": nodes, "precision": args.precision,
+                   "steps_per_sim": target, "spheres_per_box": 1,
+                   "tuned": {nc: {"threads": t, "cells": c, "regs": "loose" if r else "tight", "ms": m}
+                             for nc, (t, c, r), m in zip(("mu", "force", "collide", "transport"), shapes,
+                                                         tune_ms)},
+                   "l2": "state %.1f GB > L2 (129 MB); no flush" % (batch_bytes(lbdp, wls, args.precision) / 1e9)},
+        "mlups": mlups,
+        "one_by_one": {"sims_per_hour": alone_sims_h, "ms_per_step_all_boxes": alone_ms,
+                       "speedup": sims_h / alone_sims_h},
+        "step_roofline": {"alg_bytes_per_node": ALG_BYTES_STEP[args.precision], "achieved": step_gbs,
+                          "peak": peak, "unit": "GB/s", "frac": step_gbs / peak, "peak_kind": peak_kind},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def batch_bytes(lbdp, wls, precision):
+    return sum(lbdp.lb_device_bytes(lbdp.box_params(precision, None, **w.params)) for w in wls)
+
+
+def _percentile(v, q):
+    return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if v else None
+
+
+def run_served(args):
+    """A seeded Poisson request stream through the continuous-batching server,
+    against a FIFO server that runs one request at a time."""
+    import torch
+    world, rank, local, group = dist_setup(args)
+    torch.cuda.set_device(local)
+    from paper_2202_01631_gb300 import build
+    build.build()
+    from paper_2202_01631_gb300 import lbdp
+    from paper_2202_01631_gb300 import workloads as W
+
+    reqs = W.serving_requests(seed=rank, n=args.requests, rate=args.rate)
+    stream = torch.cuda.Stream()
+    srv = lbdp.Server(precision=args.precision, arena_bytes=48 << 30, chunk_steps=64,
+                      stream=stream.cuda_stream)
+    # warm the kernels and tune on a small mix first (not timed)
+    warm = W.batched(seed=99, n_boxes=4, edge_range=(32, 48))
+    for wl in warm:
+        b = srv.batch.add_box(**wl.params)
+        _setup_member(b, wl)
+        srv.batch.set_steps(b, 20)
+    srv.batch.run(20)
+    srv.batch.tune(reps=3)
+    for b in list(srv.batch.boxes):
+        b.close()
+    torch.cuda.synchronize()
+
+    outs = {}
+    done = {}
+    nxt = 0
+    rounds = 0
+    barrier(group)
+    t0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        while len(done) < len(reqs):
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and reqs[nxt][0] <= now:
+                t_arr, wl = reqs[nxt]
+                shape = (wl.params["nz"], wl.params["ny"], wl.params["nx"])
+                outs[nxt] = (np.empty(shape), np.empty(shape))
+                srv.submit(wl.params, wl.particles, psi=wl.fields["psi"], phi=wl.fields["phi"], steps=wl.steps,
+                           arrival=t_arr, out_psi=outs[nxt][0], out_phi=outs[nxt][1])
+                nxt += 1
+            active, queued = srv.pump(time.perf_counter() - t0)
+            rounds += 1
+            for r in srv.poll():
+                done[r["id"]] = r
+            if active == 0 and queued == 0 and nxt < len(reqs):
+                time.sleep(max(0.0, reqs[nxt][0] - (time.perf_counter() - t0)))
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = [done[i]["done"] - done[i]["arrival"] for i in done]
+    work = sum(wl.nodes * wl.steps for _, wl in reqs)
+    span = max(done[i]["done"] for i in done) - reqs[0][0]
+    sims_h = len(reqs) * 3600.0 / span
+
+    # ---- one by one: each request alone (service time from a timed sample of
+    # its steps), FIFO queue over the same arrivals --------------------------
+    service = []
+    for _, wl in reqs:
+        b = lbdp.Box(precision=args.precision, stream=stream.cuda_stream, **wl.params)
+        _setup_member(b, wl)
+        k = min(wl.steps, 200)
+        b.step(5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        service.append(e0.elapsed_time(e1) * 1e-3 / k * wl.steps)
+        b.close()
+    t_free, lat1, last = 0.0, [], 0.0
+    for (t_arr, _), sv in zip(reqs, service):
+        start = max(t_arr, t_free)
+        t_free = start + sv
+        lat1.append(t_free - t_arr)
+        last = t_free
+    sims_h1 = len(reqs) * 3600.0 / (last - reqs[0][0])
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "served p99 time-to-result", "value": _percentile(lat, 99), "unit": "s", "n_gpus": world,
+        "steps": int(sum(wl.steps for _, wl in reqs)), "warmup": 20, "ms_per_step": None,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
+        "data": "synthetic",
+        "config": {"workload": "served_poisson_%d_requests_rate_%g" % (len(reqs), args.rate),
+                   "edges": "24..128", "steps": "log-uniform 500..20000", "spheres": "1..4",
+                   "precision": args.precision, "chunk_steps": 64, "arena_gb": 48,
+                   "l2": "resident states exceed L2 (129 MB); no flush"},
+        "p50_s": _percentile(lat, 50), "p99_s": _percentile(lat, 99), "sims_per_hour": sims_h,
+        "mlups": work / wall / 1e6, "wall_s": wall, "rounds": rounds,
+        "one_by_one": {"p50_s": _percentile(lat1, 50), "p99_s": _percentile(lat1, 99), "sims_per_hour": sims_h1,
+                       "method": "each request timed alone on a sample of its steps; FIFO over the same arrivals"},
+        "clocks": clk.summary(),
+        "e2e": {"value": _percentile(lat, 99), "unit": "s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "job": "requests carry host psi/phi in and get host psi/phi and particles back"},
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.form == "batched":
+        return run_batched(args)
+    if args.form == "served":
+        return run_served(args)
     return run_ours(args)
 
 

@@ -16,6 +16,13 @@ Workloads (parameters follow Sec. "Numerical details" unless stated):
   interface z=64; contact angle, solubility ratio and phoretic mobility given.
 * ``precision``   -- 256^3 box, 8 spheres R=6 at seeded positions in the slab
   20 < z < 60 below the interface z=128.
+* ``batched``     -- 64 cubic boxes, edge uniform in 32..96, each with one
+  sphere R in [4, 8] straddling a flat interface at mid-height; contact
+  angle, solubility ratio and mobility uniform in [45, 135] deg, [0.25, 4],
+  [-0.2, 0.2].
+* ``serving_requests`` -- a Poisson stream (mean 20 requests/s) of boxes with
+  edge uniform in 24..128, step counts log-uniform in 500..20000 and 1 to 4
+  spheres, parameters drawn as for ``batched``.
 * ``scaled``      -- any of the above shrunk to a smaller edge for tests.
 """
 from __future__ import annotations
@@ -122,6 +129,63 @@ def precision(seed: int = 0, edge: int = 256, n_spheres: int = 8, R: float = 6.0
                               alpha=1e-3, mu_plus=0.1, mu_minus=0.1, theta_c_deg=90.0,
                               rho_p=1.0))
     return Workload("precision_%d" % edge, params, fields, parts, steps)
+
+
+def _sweep_box(rng: np.random.Generator, edge: int, n_spheres: int, r_range, name: str,
+               steps: int) -> Workload:
+    """A cubic box (periodic x/y, walls in z) with a flat interface at
+    mid-height and n_spheres spheres straddling it, kept 4 nodes apart;
+    contact angle, solubility ratio and mobility drawn uniformly."""
+    theta = float(rng.uniform(45.0, 135.0))
+    ratio = float(rng.uniform(0.25, 4.0))
+    mob = float(rng.uniform(-0.2, 0.2))
+    params = dict(BASE_PARAMS, nx=edge, ny=edge, nz=edge, periodic=(1, 1, 0),
+                  solubility_ratio=ratio, phi_b=1.0)
+    z0 = edge / 2.0
+    fields = flat_interface_fields(edge, edge, edge, z0=z0)
+    parts: List[Dict] = []
+    tries = 0
+    while len(parts) < n_spheres:
+        tries += 1
+        if tries > 100000:
+            raise RuntimeError("could not place the spheres")
+        R = float(rng.uniform(*r_range))
+        pos = np.array([rng.uniform(0, edge), rng.uniform(0, edge), z0 + 0.3 + rng.uniform(-0.5, 0.5) * R])
+        ok = pos[2] - R >= 3.0 and pos[2] + R <= edge - 4.0
+        for q in parts:
+            d = pos - np.array(q["pos"])
+            d[:2] -= edge * np.round(d[:2] / edge)
+            ok = ok and np.linalg.norm(d) >= R + q["R"] + 4.0
+        if ok:
+            parts.append(dict(pos=tuple(pos), R=R, m_hat=tuple(random_unit_vector(rng)), alpha=1e-3,
+                              mu_plus=mob, mu_minus=mob, theta_c_deg=theta, rho_p=1.0))
+    return Workload(name, params, fields, parts, steps)
+
+
+def batched(seed: int = 0, n_boxes: int = 64, edge_range=(32, 96), steps: int = 5000) -> List[Workload]:
+    """Independent boxes for the batched form, one sphere each."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_boxes):
+        edge = int(rng.integers(edge_range[0], edge_range[1] + 1))
+        out.append(_sweep_box(rng, edge, 1, (4.0, 8.0), "batched_%d_%d" % (k, edge), steps))
+    return out
+
+
+def serving_requests(seed: int = 0, n: int = 32, rate: float = 20.0, edge_range=(24, 128),
+                     steps_range=(500, 20000), spheres=(1, 4)):
+    """[(arrival time in s, Workload)] of a seeded Poisson request stream."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for k in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        edge = int(rng.integers(edge_range[0], edge_range[1] + 1))
+        steps = int(round(math.exp(rng.uniform(math.log(steps_range[0]), math.log(steps_range[1])))))
+        ns = int(rng.integers(spheres[0], spheres[1] + 1))
+        rmax = min(8.0, edge / 6.0)
+        out.append((t, _sweep_box(rng, edge, ns, (min(3.0, rmax), rmax), "request_%d_%d" % (k, edge), steps)))
+    return out
 
 
 def uniform_fields(nx: int, ny: int, nz: int, rng: Optional[np.random.Generator] = None,
