@@ -305,6 +305,13 @@ int lb_add_particle(lb_handle* h, const lb_particle_desc* d, int* id_out)
     }
     q.R = d->R;
     q.R2 = d->R * d->R;
+    q.Rc = (int)ceil(d->R);
+    q.R2f = (float)q.R2;
+    q.rmarg = solid_margin(d->R);
+    q.smarg = side_margin(d->R);
+    fill_geo(q.X, q.g);
+    q.gn = q.g;
+    for (int a = 0; a < 3; ++a) q.mf[a] = (float)q.m[a];
     const double rp = d->rho_p > 0.0 ? d->rho_p : 1.0;
     q.M = rp * (4.0 / 3.0) * M_PI * d->R * d->R * d->R;
     q.I = 0.4 * q.M * d->R * d->R;

@@ -119,15 +119,75 @@ __device__ __forceinline__ void grad_phi_at(const int nb[19], const Fld* phi, co
     g[2] = mul_x(g[2], (R)3);
 }
 
-// Midpoint offset r_b = (x - X) + c_i/2 of link x -> x + c_i (FP64, exact
-// roundings) and the side of the Janus cap, m.r_b <= 0.
-__device__ __forceinline__ void link_offset(const DevParams& P, const DevPart& q, int x, int y, int z, int i,
-                                            double r[3])
+// ---------------------------------------------------------------------------
+// geometric decisions.  The oracle takes them in FP64 from exact offsets
+// (|x - X|^2 < R^2 for solid nodes, m . r <= 0 for the cap side).  Here they
+// are taken in FP32 from the integer/fraction split of the centre (Geo) and
+// fall back to the oracle's FP64 arithmetic only when the FP32 value lies
+// within its error bound of the threshold, so every decision is the oracle's
+// while FP64 (a narrow pipe on GB300) is almost never executed.
+// ---------------------------------------------------------------------------
+
+// Integer offsets D of node (x, y, z) from centre g: x - X = D - fr.
+__device__ __forceinline__ void int_offset(const DevParams& P, const Geo& g, int x, int y, int z, int D[3])
 {
-    node_offset(P, q, x, y, z, r);
-    r[0] = __dadd_rn(r[0], 0.5 * cx(i));
-    r[1] = __dadd_rn(r[1], 0.5 * cy(i));
-    r[2] = __dadd_rn(r[2], 0.5 * cz(i));
+    D[0] = min_image_int(x, g.Xi[0], g.fl[0], P.nx, P.per[0]);
+    D[1] = min_image_int(y, g.Xi[1], g.fl[1], P.ny, P.per[1]);
+    D[2] = min_image_int(z, g.Xi[2], g.fl[2], P.nz, P.per[2]);
+}
+
+// FP32 error margins (host and device): the offset d = D - fr in FP32 is off
+// by at most 2^-24 (1 + |d|), so |d|^2 near R^2 is off by less than
+// 2^-24 (6 R^2 + 4 R + 1) including the rounding of R^2; m . r is off by less
+// than 2^-24 (7 |r| + 2) for |r| <= R + 3.  The margins carry 8x of slack.
+__host__ __device__ inline float solid_margin(double R) { return (float)(ldexp(1.0, -21) * (R * R + R + 1.0)); }
+__host__ __device__ inline float side_margin(double R) { return (float)(ldexp(1.0, -21) * (R + 4.0)); }
+
+// |x - X|^2 < R^2, the oracle's decision.
+__device__ __forceinline__ bool solid_test(const Geo& g, const int D[3], float R2f, float marg, double R2)
+{
+    const float d0 = (float)D[0] - g.fr[0], d1 = (float)D[1] - g.fr[1], d2 = (float)D[2] - g.fr[2];
+    const float q = dot_x(d0, d1, d2, d0, d1, d2);
+    if (q < R2f - marg) return true;
+    if (q > R2f + marg) return false;
+    const double e[3] = {__dsub_rn((double)D[0], g.frd[0]), __dsub_rn((double)D[1], g.frd[1]),
+                         __dsub_rn((double)D[2], g.frd[2])};
+    return dot3_rn(e, e) < R2;
+}
+
+// m . r <= 0 for r = (x - X) + c_i/2 (i = 0: the node itself), the oracle's
+// decision (Eq. MuJ, Eq. activity: the cap side takes mu_- and produces).
+__device__ __forceinline__ bool cap_minus(const DevPart& q, const Geo& g, const int D[3], int i)
+{
+    const float r0 = ((float)D[0] + 0.5f * (float)cx(i)) - g.fr[0];
+    const float r1 = ((float)D[1] + 0.5f * (float)cy(i)) - g.fr[1];
+    const float r2 = ((float)D[2] + 0.5f * (float)cz(i)) - g.fr[2];
+    const float sd = dot_x(q.mf[0], q.mf[1], q.mf[2], r0, r1, r2);
+    if (sd < -q.smarg) return true;
+    if (sd > q.smarg) return false;
+    const double e[3] = {__dsub_rn(__dadd_rn((double)D[0], 0.5 * cx(i)), g.frd[0]),
+                         __dsub_rn(__dadd_rn((double)D[1], 0.5 * cy(i)), g.frd[1]),
+                         __dsub_rn(__dadd_rn((double)D[2], 0.5 * cz(i)), g.frd[2])};
+    return dot3_rn(q.m, e) <= 0.0;
+}
+
+// Link midpoint offset r_b = (x - X) + c_i/2 in the arithmetic precision:
+// exact in FP64, within 2^-24 (1 + |r|) in FP32.
+template <class R>
+__device__ __forceinline__ void link_offset_r(const Geo& g, const int D[3], int i, R r[3]);
+template <>
+__device__ __forceinline__ void link_offset_r<float>(const Geo& g, const int D[3], int i, float r[3])
+{
+    r[0] = ((float)D[0] + 0.5f * (float)cx(i)) - g.fr[0];
+    r[1] = ((float)D[1] + 0.5f * (float)cy(i)) - g.fr[1];
+    r[2] = ((float)D[2] + 0.5f * (float)cz(i)) - g.fr[2];
+}
+template <>
+__device__ __forceinline__ void link_offset_r<double>(const Geo& g, const int D[3], int i, double r[3])
+{
+    r[0] = __dsub_rn(__dadd_rn((double)D[0], 0.5 * cx(i)), g.frd[0]);
+    r[1] = __dsub_rn(__dadd_rn((double)D[1], 0.5 * cy(i)), g.frd[1]);
+    r[2] = __dsub_rn(__dadd_rn((double)D[2], 0.5 * cz(i)), g.frd[2]);
 }
 
 // Boundary velocity at the midpoint of link x -> x + c_i of particle q:
@@ -137,13 +197,10 @@ template <class R>
 __device__ __forceinline__ void link_velocity(const DevParams& P, const DevPart& q, int x, int y, int z, int i,
                                               const R gphi[3], R r[3], R ub[3], R vs[3])
 {
-    double rd[3];
-    link_offset(P, q, x, y, z, i, rd);
-    const double side = dot3_rn(q.m, rd);
-    const R mu = (side <= 0.0) ? PartR<R>::mu_m(q) : PartR<R>::mu_p(q);
-    r[0] = (R)rd[0];
-    r[1] = (R)rd[1];
-    r[2] = (R)rd[2];
+    int D[3];
+    int_offset(P, q.g, x, y, z, D);
+    const R mu = cap_minus(q, q.g, D, i) ? PartR<R>::mu_m(q) : PartR<R>::mu_p(q);
+    link_offset_r<R>(q.g, D, i, r);
     const R rn = sqrt(dot_x(r[0], r[1], r[2], r[0], r[1], r[2]));
     const R nh[3] = {r[0] / rn, r[1] / rn, r[2] / rn};
     const R ng = dot_x(nh[0], nh[1], nh[2], gphi[0], gphi[1], gphi[2]);
@@ -161,12 +218,13 @@ __device__ __forceinline__ void link_velocity(const DevParams& P, const DevPart&
 template <class R>
 __device__ __forceinline__ R psi_ghost(const DevParams& P, const DevPart& q, int x, int y, int z, int i, R ps)
 {
-    if (q.H == 0.0) return ps;
-    double rd[3];
-    link_offset(P, q, x, y, z, i, rd);
-    const R r0 = (R)rd[0], r1 = (R)rd[1], r2 = (R)rd[2];
-    const R rn = sqrt(dot_x(r0, r1, r2, r0, r1, r2));
-    const R cn = cdot<R>(i, r0, r1, r2) / rn;
+    if (PartR<R>::Hk(q) == (R)0) return ps;
+    int D[3];
+    int_offset(P, q.g, x, y, z, D);
+    R r[3];
+    link_offset_r<R>(q.g, D, i, r);
+    const R rn = sqrt(dot_x(r[0], r[1], r[2], r[0], r[1], r[2]));
+    const R cn = cdot<R>(i, r[0], r[1], r[2]) / rn;
     return fma_x(PartR<R>::Hk(q), cn, ps);
 }
 
@@ -419,6 +477,150 @@ __device__ __forceinline__ void fdiv_node(const DevParams& P, const DevPtrs& D, 
     force[2 * N + n] = (F)Fz;
 }
 
+// Rotate the unit vector m by the angle |w| about w (Rodrigues):
+//   m' = m cos|w| + (w x m) sin|w|/|w| + w (w . m)(1 - cos|w|)/|w|^2,
+// then renormalise.  For |w| < 0.1 both ratios are their Taylor series in
+// |w|^2, exact to double precision with six terms; the renormalisation is one
+// Newton step of 1/sqrt around 1 (|m'| = 1 up to rounding).
+__device__ __forceinline__ void rotate_unit(const double m[3], const double w[3], double out[3])
+{
+    const double w2 = dot_x(w[0], w[1], w[2], w[0], w[1], w[2]);
+    double s1, c1, cw;
+    if (w2 < 0.01) {
+        s1 = fma_x(-w2 / 6.0, fma_x(-w2 / 20.0, fma_x(-w2 / 42.0, fma_x(-w2 / 72.0, fma_x(-w2 / 110.0, 1.0, 1.0),
+                                                                       1.0), 1.0), 1.0), 1.0);
+        c1 = 0.5 * fma_x(-w2 / 12.0, fma_x(-w2 / 30.0, fma_x(-w2 / 56.0, fma_x(-w2 / 90.0, fma_x(-w2 / 132.0, 1.0,
+                                                                                                  1.0), 1.0), 1.0),
+                                        1.0), 1.0);
+        cw = fma_x(-w2, c1, 1.0);
+    } else {
+        const double wn = sqrt(w2);
+        s1 = sin(wn) / wn;
+        cw = cos(wn);
+        c1 = (1.0 - cw) / w2;
+    }
+    const double wxm[3] = {cross_x(w[1], m[2], w[2], m[1]), cross_x(w[2], m[0], w[0], m[2]),
+                           cross_x(w[0], m[1], w[1], m[0])};
+    const double wm = mul_x(dot_x(w[0], w[1], w[2], m[0], m[1], m[2]), c1);
+    double r[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) r[a] = fma_x(w[a], wm, fma_x(wxm[a], s1, mul_x(m[a], cw)));
+    const double nn2 = dot_x(r[0], r[1], r[2], r[0], r[1], r[2]);
+    const double sc = fma_x(-0.5, nn2, 1.5);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[a] = mul_x(r[a], sc);
+}
+
+// Implicit particle update of particle p by warp 0 of the last block, from
+// the link totals tot[0..26] (F0[3], T0[3], zeta upper triangle):
+//   (Mdiag + zeta) V(t+1) = Mdiag V(t) + [F0 + impulses + loads; T0 + ...]
+// (symmetric positive definite: Cholesky with lane a holding row a), force
+// and torque F0 - zeta V, then the position and orientation after the step.
+// FP64 throughout; the work is spread over lanes because GB300 issues FP64
+// at a low rate.  Ls is scratch for 36 doubles.
+static __device__ __noinline__ void particle_update(int3 L3, int3 per3, DevPart* parts, unsigned* ticket, int* err, int p,
+                                             const DevPart& q, const double* tot, double* Ls)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    if (lane == 0) ticket[p] = 0u;
+    const int a = lane < 6 ? lane : 5;   // lanes >= 6 shadow row 5
+    double zrow[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const int lo = min(a, c), hi = max(a, c);
+        zrow[c] = tot[6 + lo * 6 - (lo * (lo - 1)) / 2 + (hi - lo)];
+    }
+    const double Ma = a < 3 ? q.M : q.I;
+    const double F0a = a < 3 ? add_x(add_x(tot[a], q.imp_f[a]), q.ext_f[a])
+                             : add_x(add_x(tot[a], q.imp_t[a - 3]), q.ext_t[a - 3]);
+    double xv[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) xv[c] = c < 3 ? q.U[c] : q.W[c - 3];
+    if (!q.fixed) {
+        double Arow[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) Arow[c] = c == a ? add_x(zrow[c], Ma) : zrow[c];
+        const double ba = fma_x(Ma, a < 3 ? q.U[a] : q.W[a - 3], F0a);
+        // right-looking Cholesky A = L L^T: at step j lane j holds the pivot
+        double rs[6];
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            const double piv = __shfl_sync(full, Arow[j], j);
+            ok = ok && (piv > 0.0);
+            rs[j] = rsqrt(fmax(piv, 1e-300));
+            const double laj = mul_x(Arow[j], rs[j]);   // L[a][j] for a >= j
+            if (lane < 6) Ls[a * 6 + j] = laj;
+#pragma unroll
+            for (int c = j + 1; c < 6; ++c) Arow[c] = fma_x(-laj, __shfl_sync(full, laj, c), Arow[c]);
+        }
+        __syncwarp();
+        // L y = b, then L^T x = y (uniform in the warp; L from shared memory)
+        double yv[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            double t = __shfl_sync(full, ba, j);
+#pragma unroll
+            for (int k = 0; k < j; ++k) t = fma_x(-Ls[j * 6 + k], yv[k], t);
+            yv[j] = mul_x(t, rs[j]);
+        }
+#pragma unroll
+        for (int j = 5; j >= 0; --j) {
+            double t = yv[j];
+#pragma unroll
+            for (int k = j + 1; k < 6; ++k) t = fma_x(-Ls[k * 6 + j], xv[k], t);
+            xv[j] = mul_x(t, rs[j]);
+        }
+        if (!ok && lane == 0) atomicOr(err, kErrSolve);
+    }
+    DevPart& dp = parts[p];
+    if (lane < 6) {
+        double zv = 0.0;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) zv = fma_x(zrow[c], xv[c], zv);
+        if (a < 3)
+            dp.force[a] = add_x(F0a, -zv);
+        else
+            dp.torque[a - 3] = add_x(F0a, -zv);
+    }
+    if (lane < 3) {
+        const int L = a == 0 ? L3.x : (a == 1 ? L3.y : L3.z);
+        const int per = a == 0 ? per3.x : (a == 1 ? per3.y : per3.z);
+        const double v = a == 0 ? xv[0] : (a == 1 ? xv[1] : xv[2]);
+        const double w = a == 0 ? xv[3] : (a == 1 ? xv[4] : xv[5]);
+        dp.U[a] = v;
+        dp.W[a] = w;
+        dp.Uf[a] = (float)v;
+        dp.Wf[a] = (float)w;
+        dp.imp_f[a] = 0.0;
+        dp.imp_t[a] = 0.0;
+        double X = add_x(q.X[a], v);
+        if (per) {
+            if (X >= L)
+                X -= L;
+            else if (X < 0.0)
+                X += L;
+        } else if (X - q.R < 1.0 || X + q.R > L - 2.0) {
+            atomicOr(err, kErrWall);
+        }
+        dp.Xn[a] = X;
+        const double f = floor(X);
+        const double fr = X - f;
+        dp.gn.Xi[a] = (int)f;
+        dp.gn.frd[a] = fr;
+        dp.gn.fr[a] = (float)fr;
+        dp.gn.fl[a] = (fr > 0.0 ? kFrPos : 0) | (fr < 0.5 ? kFrBelowHalf : 0) | (fr > 0.5 ? kFrAboveHalf : 0);
+    }
+    if (lane == 0) {
+        const double w3[3] = {xv[3], xv[4], xv[5]};
+        double mn[3] = {q.m[0], q.m[1], q.m[2]};
+        if (w3[0] != 0.0 || w3[1] != 0.0 || w3[2] != 0.0) rotate_unit(q.m, w3, mn);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dp.mn[c] = mn[c];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // S5 + S6a: link sums and the implicit velocity update.  Grid (nb1, np): the
 // blocks of a particle split its link box; the last block of the particle (a
@@ -449,7 +651,9 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
     const F* psi = (const F*)D.psi_src;
     const F* phi = (const F*)D.phi_src;
     const R dph = corr_r<R>(D, 1);
-    const int o[3] = {(int)floor(q.X[0] - q.R) - 2, (int)floor(q.X[1] - q.R) - 2, (int)floor(q.X[2] - q.R) - 2};
+    // floor(X) - ceil(R) <= floor(X - R): the box holds every fluid node within
+    // R + 2 of the centre
+    const int o[3] = {q.g.Xi[0] - q.Rc - 2, q.g.Xi[1] - q.Rc - 2, q.g.Xi[2] - q.Rc - 2};
     const int tot = P.side1[0] * P.side1[1] * P.side1[2];
     double acc[K];
 #pragma unroll
@@ -542,125 +746,10 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
 #pragma unroll
         for (int k = 0; k < K; ++k) sum[k] = __ldcg(pb + k);
     }
-    block_sum_t<K>(sum, smem);
-    if (threadIdx.x != 0) return;
-    D.link_ticket[p] = 0u;
-
-    DevPart& dp = D.parts[p];
-    double zeta[6][6];
-    {
-        int k = 6;
-#pragma unroll
-        for (int a = 0; a < 6; ++a)
-#pragma unroll
-            for (int b = a; b < 6; ++b) {
-                zeta[a][b] = sum[k];
-                zeta[b][a] = sum[k];
-                ++k;
-            }
-    }
-    double F0[6];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        F0[a] = add_x(add_x(sum[a], q.imp_f[a]), q.ext_f[a]);
-        F0[3 + a] = add_x(add_x(sum[3 + a], q.imp_t[a]), q.ext_t[a]);
-    }
-    double V[6] = {q.U[0], q.U[1], q.U[2], q.W[0], q.W[1], q.W[2]};
-    if (!q.fixed) {
-        const double Mm[6] = {q.M, q.M, q.M, q.I, q.I, q.I};
-        double A[6][6], b[6], dinv[6];
-#pragma unroll
-        for (int a = 0; a < 6; ++a) {
-#pragma unroll
-            for (int c = 0; c < 6; ++c) A[a][c] = zeta[a][c];
-            A[a][a] = add_x(A[a][a], Mm[a]);
-            b[a] = fma_x(Mm[a], V[a], F0[a]);
-        }
-        // Cholesky A = L L^T (in place, lower triangle), then two triangular
-        // solves with the reciprocal diagonal
-        bool ok = true;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            double s = A[j][j];
-#pragma unroll
-            for (int k = 0; k < j; ++k) s = fma_x(-A[j][k], A[j][k], s);
-            ok = ok && (s > 0.0);
-            const double d = sqrt(fmax(s, 1e-300));
-            dinv[j] = 1.0 / d;
-#pragma unroll
-            for (int i = j + 1; i < 6; ++i) {
-                double t = A[i][j];
-#pragma unroll
-                for (int k = 0; k < j; ++k) t = fma_x(-A[i][k], A[j][k], t);
-                A[i][j] = mul_x(t, dinv[j]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            double t = b[i];
-#pragma unroll
-            for (int k = 0; k < i; ++k) t = fma_x(-A[i][k], b[k], t);
-            b[i] = mul_x(t, dinv[i]);
-        }
-#pragma unroll
-        for (int i = 5; i >= 0; --i) {
-            double t = b[i];
-#pragma unroll
-            for (int k = i + 1; k < 6; ++k) t = fma_x(-A[k][i], b[k], t);
-            b[i] = mul_x(t, dinv[i]);
-        }
-        if (!ok) atomicOr(D.err, kErrSolve);
-#pragma unroll
-        for (int a = 0; a < 6; ++a) V[a] = b[a];
-    }
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
-        double zv = 0.0;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) zv = fma_x(zeta[a][c], V[c], zv);
-        if (a < 3)
-            dp.force[a] = add_x(F0[a], -zv);
-        else
-            dp.torque[a - 3] = add_x(F0[a], -zv);
-    }
-    const int L[3] = {P.nx, P.ny, P.nz};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        dp.U[a] = V[a];
-        dp.W[a] = V[3 + a];
-        dp.Uf[a] = (float)V[a];
-        dp.Wf[a] = (float)V[3 + a];
-        dp.imp_f[a] = 0.0;
-        dp.imp_t[a] = 0.0;
-        double X = add_x(q.X[a], V[a]);
-        if (P.per[a]) {
-            if (X >= L[a])
-                X -= L[a];
-            else if (X < 0.0)
-                X += L[a];
-        } else if (X - q.R < 1.0 || X + q.R > L[a] - 2.0) {
-            atomicOr(D.err, kErrWall);
-        }
-        dp.Xn[a] = X;
-        dp.mn[a] = q.m[a];
-    }
-    // rotate m by the angle |Omega| about Omega (Rodrigues), renormalise
-    const double w = sqrt(dot_x(V[3], V[4], V[5], V[3], V[4], V[5]));
-    if (w > 0.0) {
-        const double k3[3] = {V[3] / w, V[4] / w, V[5] / w};
-        const double c = cos(w), sn = sin(w);
-        const double* m = q.m;
-        const double kxm[3] = {cross_x(k3[1], m[2], k3[2], m[1]), cross_x(k3[2], m[0], k3[0], m[2]),
-                               cross_x(k3[0], m[1], k3[1], m[0])};
-        const double km = dot_x(k3[0], k3[1], k3[2], m[0], m[1], m[2]);
-        double mn[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            mn[a] = fma_x(mul_x(k3[a], km), add_x(1.0, -c), fma_x(kxm[a], sn, mul_x(m[a], c)));
-        const double nn = sqrt(dot_x(mn[0], mn[1], mn[2], mn[0], mn[1], mn[2]));
-#pragma unroll
-        for (int a = 0; a < 3; ++a) dp.mn[a] = mn[a] / nn;
-    }
+    block_sum_t<K>(sum, smem);   // the totals stay in smem[0..K-1]
+    if (threadIdx.x >= 32) return;
+    particle_update(make_int3(P.nx, P.ny, P.nz), make_int3(P.per[0], P.per[1], P.per[2]), D.parts, D.link_ticket,
+                    D.err, p, q, smem, smem + 32);
 }
 
 // ---------------------------------------------------------------------------
@@ -827,9 +916,9 @@ __device__ __forceinline__ void scalars_node(const DevParams& P, const DevPtrs& 
             const int k = __ffsll((long long)adj) - 1;
             adj &= adj - 1;
             const DevPart& q = D.parts[k];
-            double r[3];
-            node_offset(P, q, x, y, z, r);
-            if (dot3_rn(q.m, r) <= 0.0) hn_src += PartR<R>::alpha(q);
+            int Di[3];
+            int_offset(P, q.g, x, y, z, Di);
+            if (cap_minus(q, q.g, Di, 0)) hn_src += PartR<R>::alpha(q);
         }
     }
     const R pn = ps + (R)6 * sps;
@@ -851,11 +940,14 @@ __device__ __forceinline__ void cover_origin(const DevParams& P, const DevPart& 
 {
     for (int a = 0; a < 3; ++a) {
         const int L = a == 0 ? P.nx : (a == 1 ? P.ny : P.nz);
-        double lo = fmin(q.X[a], q.Xn[a]);
+        const int i0 = q.g.Xi[a], i1 = q.gn.Xi[a];
+        int lo = min(i0, i1);
         // on a periodic axis the two centres may sit on opposite sides of the
         // wrap; take the lower end of the shorter arc
-        if (P.per[a] && fabs(q.X[a] - q.Xn[a]) > 0.5 * L) lo = fmax(q.X[a], q.Xn[a]);
-        o[a] = (int)floor(lo - q.R) - 3;
+        if (P.per[a] && abs(i0 - i1) > L / 2) lo = max(i0, i1);
+        // floor(lo) - ceil(R) <= floor(lo - R): the box starts at or below the
+        // lowest node that can change or neighbour a change
+        o[a] = lo - q.Rc - 3;
     }
 }
 
@@ -870,11 +962,15 @@ __device__ __forceinline__ void cover_mark_block(const DevParams& P, const DevPt
         int x, y, z;
         if (!box_node(P, o, P.side2, t, x, y, z)) continue;
         uint8_t own = 0;
-        for (int k = 0; k < P.np; ++k)
-            if (inside_at(P, D.parts[k].Xn, D.parts[k].R2, x, y, z)) {
+        for (int k = 0; k < P.np; ++k) {
+            const DevPart& qk = D.parts[k];
+            int Dk[3];
+            int_offset(P, qk.gn, x, y, z, Dk);
+            if (solid_test(qk.gn, Dk, qk.R2f, qk.rmarg, qk.R2)) {
                 own = (uint8_t)(k + 1);
                 break;
             }
+        }
         D.mask_next[x + P.nx * (y + P.ny * z)] = own;
     }
 }
@@ -950,16 +1046,19 @@ __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevP
         if (ob == 0 && nw == p + 1) {
             // covered: the particle takes the momentum the node's populations
             // carry; psi, phi are removed
-            double j[3] = {0.0, 0.0, 0.0};
+            R jr[3] = {0, 0, 0};
 #pragma unroll
             for (int i = 0; i < 19; ++i) {
-                const double fi = (double)PopStore<S>::load(f, (size_t)i * N + n, i, rho0);
-                j[0] += cx(i) * fi;
-                j[1] += cy(i) * fi;
-                j[2] += cz(i) * fi;
+                const R fi = (R)PopStore<S>::load(f, (size_t)i * N + n, i, rho0);
+                if (cx(i) != 0) jr[0] = cx(i) > 0 ? add_x(jr[0], fi) : add_x(jr[0], -fi);
+                if (cy(i) != 0) jr[1] = cy(i) > 0 ? add_x(jr[1], fi) : add_x(jr[1], -fi);
+                if (cz(i) != 0) jr[2] = cz(i) > 0 ? add_x(jr[2], fi) : add_x(jr[2], -fi);
             }
-            double r[3];
-            offset_from(P, q.Xn, x, y, z, r);
+            const double j[3] = {(double)jr[0], (double)jr[1], (double)jr[2]};
+            int Dn[3];
+            int_offset(P, q.gn, x, y, z, Dn);
+            const double r[3] = {__dsub_rn((double)Dn[0], q.gn.frd[0]), __dsub_rn((double)Dn[1], q.gn.frd[1]),
+                                 __dsub_rn((double)Dn[2], q.gn.frd[2])};
             acc[0] += j[0];
             acc[1] += j[1];
             acc[2] += j[2];
@@ -972,50 +1071,54 @@ __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevP
         } else if (ob == p + 1 && nw == 0) {
             // uncovered: equilibrium at the boundary velocity with the mean
             // density of neighbours fluid before and after; psi, phi = means
-            double rb = 0.0, pb = 0.0, hb = 0.0;
+            R rb = 0, pb = 0, hb = 0;
             int cnt = 0;
             for (int i = 1; i < 19; ++i) {
                 const int m = nb[i];
                 if (m < 0 || D.mask[m] || D.mask_next[m]) continue;
                 R rm = 0;
 #pragma unroll
-                for (int k = 0; k < 19; ++k) rm += (R)PopStore<S>::load(f, (size_t)k * N + m, k, rho0);
-                rb += (double)rm;
-                pb += (double)psi[m];
-                hb += (double)phi[m];
+                for (int k = 0; k < 19; ++k) rm = add_x(rm, (R)PopStore<S>::load(f, (size_t)k * N + m, k, rho0));
+                rb = add_x(rb, rm);
+                pb = add_x(pb, (R)psi[m]);
+                hb = add_x(hb, (R)phi[m]);
                 ++cnt;
             }
             if (cnt == 0) {
                 atomicOr(D.err, kErrOverlap);
-                rb = P.rho0;
-                pb = hb = 0.0;
+                rb = rho0;
+                pb = hb = 0;
             } else {
-                rb /= cnt;
-                pb /= cnt;
-                hb /= cnt;
+                rb = rb / (R)cnt;
+                pb = pb / (R)cnt;
+                hb = hb / (R)cnt;
             }
-            double r[3];
-            offset_from(P, q.Xn, x, y, z, r);
-            const double ub[3] = {add_x(q.U[0], cross_x(q.W[1], r[2], q.W[2], r[1])),
-                                  add_x(q.U[1], cross_x(q.W[2], r[0], q.W[0], r[2])),
-                                  add_x(q.U[2], cross_x(q.W[0], r[1], q.W[1], r[0]))};
+            int Dn[3];
+            int_offset(P, q.gn, x, y, z, Dn);
+            R r[3];
+            link_offset_r<R>(q.gn, Dn, 0, r);
+            const R U0 = PartR<R>::U(q, 0), U1 = PartR<R>::U(q, 1), U2 = PartR<R>::U(q, 2);
+            const R W0 = PartR<R>::W(q, 0), W1 = PartR<R>::W(q, 1), W2 = PartR<R>::W(q, 2);
+            const R ub[3] = {add_x(U0, cross_x(W1, r[2], W2, r[1])), add_x(U1, cross_x(W2, r[0], W0, r[2])),
+                             add_x(U2, cross_x(W0, r[1], W1, r[0]))};
 #pragma unroll
             for (int i = 0; i < 19; ++i)
-                PopStore<S>::store(f, (size_t)i * N + n, i, rho0, (R)feq_i<double>(i, rb, ub[0], ub[1], ub[2]));
+                PopStore<S>::store(f, (size_t)i * N + n, i, rho0, feq_i<R>(i, rb, ub[0], ub[1], ub[2]));
             u[n] = (F)ub[0];
             u[N + n] = (F)ub[1];
             u[2 * N + n] = (F)ub[2];
             psi[n] = (F)pb;
             phi[n] = (F)hb;
-            const double j[3] = {mul_x(rb, ub[0]), mul_x(rb, ub[1]), mul_x(rb, ub[2])};
+            const double j[3] = {(double)mul_x(rb, ub[0]), (double)mul_x(rb, ub[1]), (double)mul_x(rb, ub[2])};
+            const double rd[3] = {(double)r[0], (double)r[1], (double)r[2]};
             acc[0] -= j[0];
             acc[1] -= j[1];
             acc[2] -= j[2];
-            acc[3] -= cross_x(r[1], j[2], r[2], j[1]);
-            acc[4] -= cross_x(r[2], j[0], r[0], j[2]);
-            acc[5] -= cross_x(r[0], j[1], r[1], j[0]);
-            acc[6] -= pb;
-            acc[7] -= hb;
+            acc[3] -= cross_x(rd[1], j[2], rd[2], j[1]);
+            acc[4] -= cross_x(rd[2], j[0], rd[0], j[2]);
+            acc[5] -= cross_x(rd[0], j[1], rd[1], j[0]);
+            acc[6] -= (double)psi[n];
+            acc[7] -= (double)phi[n];
             acc[8] += 1.0;
         } else if (ob == p + 1) {
             atomicOr(D.err, kErrOverlap);   // passed straight into another sphere
@@ -1052,7 +1155,9 @@ __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevP
                 dk.imp_t[a] = s[3 + a];
                 dk.X[a] = dk.Xn[a];
                 dk.m[a] = dk.mn[a];
+                dk.mf[a] = (float)dk.mn[a];
             }
+            dk.g = dk.gn;
             dsum_psi += s[6] + s[9];
             dsum_phi += s[7] + s[10];
             dcnt += s[8];

@@ -136,12 +136,45 @@ inline void fill_prm(PrmR<R>& q, const DevParams& P)
     q.inv_kappa = P.kappa > 0.0 ? (R)(1.0 / P.kappa) : (R)0;
 }
 
+// A sphere centre X split for the geometric decisions: X = Xi + fr with
+// Xi = floor(X) and fr in [0, 1) exact in FP64 (frd) and rounded to FP32
+// (fr).  Offsets x - X of lattice nodes are then D - fr with an integer D, and
+// the periodic minimum image of the oracle (a shift by L when |x - X| > L/2)
+// is an integer decision once fr is compared with 0 and 1/2 (fl).
+enum : int { kFrPos = 1, kFrBelowHalf = 2, kFrAboveHalf = 4 };
+struct Geo {
+    int Xi[3];
+    int fl[3];
+    double frd[3];
+    float fr[3];
+    float pad;
+};
+
+__host__ __device__ inline void fill_geo(const double X[3], Geo& g)
+{
+    for (int a = 0; a < 3; ++a) {
+        const double f = floor(X[a]);
+        const double fr = X[a] - f;   // exact
+        g.Xi[a] = (int)f;
+        g.frd[a] = fr;
+        g.fr[a] = (float)fr;
+        g.fl[a] = (fr > 0.0 ? kFrPos : 0) | (fr < 0.5 ? kFrBelowHalf : 0) | (fr > 0.5 ? kFrAboveHalf : 0);
+    }
+    g.pad = 0.f;
+}
+
 struct DevPart {
     double X[3], U[3], W[3], m[3];   // position, velocity, spin, unit vector
     double Xn[3], mn[3];             // position and unit vector after this step
+    Geo g, gn;                       // X and Xn split for the geometric decisions
     float Uf[3], Wf[3];              // U, W in FP32 for the FP32 link arithmetic
+    float mf[3];                     // m in FP32
+    float R2f, rmarg, smarg;         // R^2 in FP32; FP32 error margins of the
+                                     // solid test and of the cap-side test
     float alpha_f, mu_pf, mu_mf, Hk_f;
     double R, R2, M, I, alpha, mu_p, mu_m, H;
+    int Rc;                          // ceil(R)
+    int pad0;
     double Hk;                       // H / kappa of the wetting ghost
     double ext_f[3], ext_t[3];
     double imp_f[3], imp_t[3];       // covering impulses, applied in the next step
@@ -305,6 +338,32 @@ __device__ __forceinline__ void neighbours(const DevParams& P, int x, int y, int
         int a = xs[1 + cx(i)], b = ys[1 + cy(i)], c = zs[1 + cz(i)];
         nb[i] = (a < 0 || b < 0 || c < 0) ? -1 : a + P.nx * (b + P.ny * c);
     }
+}
+
+// Integer part of the offset x - X on one axis after the oracle's periodic
+// minimum image (d > L/2: d - L; d < -L/2: d + L, with d = x - X exact):
+// the offset is exactly D - fr.  With h = L/2 and fr in [0, 1):
+//   L even: d > h iff D >= h + 1;        d < -h iff D < -h, or D = -h and fr > 0
+//   L odd (h = k + 1/2): d > h iff D >= k + 2, or D = k + 1 and fr < 1/2;
+//                        d < -h iff D <= -k - 1, or D = -k and fr > 1/2
+__host__ __device__ __forceinline__ int min_image_int(int x, int Xi, int fl, int L, int periodic)
+{
+    int D = x - Xi;
+    if (!periodic) return D;
+    if ((L & 1) == 0) {
+        const int h = L >> 1;
+        if (D >= h + 1)
+            D -= L;
+        else if (D < -h || (D == -h && (fl & kFrPos)))
+            D += L;
+    } else {
+        const int k = L >> 1;
+        if (D >= k + 2 || (D == k + 1 && (fl & kFrBelowHalf)))
+            D -= L;
+        else if (D <= -k - 1 || (D == -k && (fl & kFrAboveHalf)))
+            D += L;
+    }
+    return D;
 }
 
 // Wrap a box coordinate onto the lattice; -1 when it falls beyond a wall.
