@@ -171,6 +171,14 @@ void update_sides(lb_handle* h)
 void free_all(lb_handle* h)
 {
     if (h->device >= 0) cudaSetDevice(h->device);
+    if (h->side.s) {
+        cudaStreamSynchronize(h->side.s);
+        cudaStreamDestroy(h->side.s);
+        cudaEventDestroy(h->side.fork);
+        cudaEventDestroy(h->side.links_done);
+        cudaEventDestroy(h->side.mark_done);
+        h->side.s = nullptr;
+    }
     if (h->batch)
         batch_release(h);
     else if (h->region)
@@ -363,7 +371,7 @@ int lb_step(lb_handle* h, int nsteps)
     cudaSetDevice(h->device);
     const RowGrid g = row_grid(h->dp);
     for (int t = 0; t < nsteps; ++t) {
-        LB_TRY(h->ops->step(h->dp, ptrs(h, h->cur), g, h->stream));
+        LB_TRY(h->ops->step(h->dp, ptrs(h, h->cur), g, h->stream, h->side.s ? &h->side : nullptr));
         h->cur ^= 1;
     }
     return LB_OK;
@@ -608,6 +616,16 @@ int lb_create_in(const lb_params* p, lbb_batch* batch, void* region, lb_handle**
         e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
         h->own_stream = true;
     }
+    // the particle kernels' stream, at the highest priority so that its few
+    // blocks are placed as soon as the fluid kernels leave room
+    if (e == cudaSuccess) {
+        int lo = 0, hi = 0;
+        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side.s, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.links_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.mark_done, cudaEventDisableTiming);
+    }
     h->region_bytes = layout(p, h->ops, h->red_blocks, nullptr, nullptr);
     if (e == cudaSuccess) {
         if (region) {
@@ -619,7 +637,7 @@ int lb_create_in(const lb_params* p, lbb_batch* batch, void* region, lb_handle**
     }
     if (e != cudaSuccess) {
         h->region = nullptr;
-        if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+        free_all(h);
         delete h;
         cudaGetLastError();
         return cuda_status(e);

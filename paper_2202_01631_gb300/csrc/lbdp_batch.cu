@@ -179,6 +179,7 @@ struct lbb_batch {
     int grid[4] = {0, 0, 0, 0};
     int part_grid = 0;
     cudaGraphExec_t exec = nullptr;
+    SideStream side{};   // particle kernels, overlapping the fluid kernels
 };
 
 namespace {
@@ -314,7 +315,7 @@ int capture_graph(lbb_batch* b)
     LB_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int t = 0; t < b->graph_steps && e == cudaSuccess; ++t)
-        e = b->bops->step(b->cfg, b->grid, b->part_grid, b->d_hdr, b->stream);
+        e = b->bops->step(b->cfg, b->grid, b->part_grid, b->d_hdr, b->stream, &b->side);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
@@ -362,6 +363,14 @@ int lbb_create(const lbb_params* p, lbb_batch** out)
             e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
             b->own_stream = e == cudaSuccess;
         }
+    }
+    if (e == cudaSuccess) {
+        int lo = 0, hi = 0;
+        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->side.s, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.links_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.mark_done, cudaEventDisableTiming);
     }
     size_t cap = p->arena_bytes;
     if (e == cudaSuccess && cap == 0) {
@@ -412,6 +421,13 @@ void lbb_destroy(lbb_batch* b)
     if (b->d_left) cudaFree(b->d_left);
     if (b->base) cudaFree(b->base);
     if (b->arena) lb_arena_destroy(b->arena);
+    if (b->side.s) {
+        cudaStreamSynchronize(b->side.s);
+        cudaStreamDestroy(b->side.s);
+    }
+    if (b->side.fork) cudaEventDestroy(b->side.fork);
+    if (b->side.links_done) cudaEventDestroy(b->side.links_done);
+    if (b->side.mark_done) cudaEventDestroy(b->side.mark_done);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -509,7 +525,8 @@ int lbb_run(lbb_batch* b, int nsteps, long long* launches)
         if (st != LB_OK) return st;
         for (int k = 0; k < full; ++k) LB_TRY(cudaGraphLaunch(b->exec, b->stream));
     }
-    for (int k = 0; k < rest; ++k) LB_TRY(b->bops->step(b->cfg, b->grid, b->part_grid, b->d_hdr, b->stream));
+    for (int k = 0; k < rest; ++k)
+        LB_TRY(b->bops->step(b->cfg, b->grid, b->part_grid, b->d_hdr, b->stream, &b->side));
     for (Member& m : b->mem) {
         const long long ran = std::min<long long>(m.left, n);
         m.left -= ran;

@@ -21,11 +21,21 @@ struct RowGrid {
 // Kernel classes of one step, in launch order.
 enum KernelClass { kKMu = 0, kKLinks, kKCollide, kKScalars, kKCover, kNumKernelClasses };
 
+// A second stream for the particle kernels of a step: k_links (which needs
+// only mu/P and the populations) and k_cover_mark run there while the force,
+// collide-stream and transport kernels run on the main stream; collide-stream
+// waits for links_done (it bounces back with the new particle velocities),
+// k_cover_apply waits for mark_done.
+struct SideStream {
+    cudaStream_t s;
+    cudaEvent_t fork, links_done, mark_done;
+};
+
 struct PrecOps {
     int pop_bytes;   // bytes per stored population value
     int fld_bytes;   // bytes per stored field value
     // one full time step (fluid kernels, then particle kernels when np > 0)
-    cudaError_t (*step)(const DevParams&, const DevPtrs&, const RowGrid&, cudaStream_t);
+    cudaError_t (*step)(const DevParams&, const DevPtrs&, const RowGrid&, cudaStream_t, const SideStream*);
     // the same step with an event recorded before the first kernel and after
     // each kernel class: ev[0..5] around mu, links, collide, scalars, cover
     cudaError_t (*step_events)(const DevParams&, const DevPtrs&, const RowGrid&, cudaStream_t, cudaEvent_t* ev);
@@ -59,7 +69,8 @@ struct BatchOps {
     cudaError_t (*node_grid)(int nc, int cfg, int* blocks_per_sm);
     cudaError_t (*node)(int nc, int cfg, int grid, const BatchDev* B, cudaStream_t s);
     // the whole step: node kernels in cfg[4], particle kernels on part_grid blocks
-    cudaError_t (*step)(const int cfg[4], const int grid[4], int part_grid, const BatchDev* B, cudaStream_t s);
+    cudaError_t (*step)(const int cfg[4], const int grid[4], int part_grid, const BatchDev* B, cudaStream_t s,
+                        const SideStream* side);
 };
 
 extern const PrecOps kOpsF64;
@@ -96,6 +107,7 @@ struct lb_handle {
     int device;
     int cur;   // which buffer of each pair holds the current state
     lbb_batch* batch;   // owning batch, or NULL for a standalone box
+    lbdp::SideStream side;   // particle kernels' stream (side.s NULL until created)
     void* region;       // the single device allocation holding every array below
     size_t region_bytes;
     void* f[2];

@@ -33,11 +33,28 @@ struct Ops {
     }
 
     static cudaError_t launch_step(const DevParams& P, const DevPtrs& D, const RowGrid& g, cudaStream_t s,
-                                   cudaEvent_t* ev)
+                                   cudaEvent_t* ev, const SideStream* side)
     {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
         const dim3 pg1(P.nb1, P.np), pg2(P.nb2, P.np);
+        if (P.np > 0 && side && !ev) {
+            // particle kernels on the side stream, overlapping the fluid kernels
+            k_mup<C><<<g.grid, g.block, 0, s>>>(P, D);
+            cudaEventRecord(side->fork, s);
+            cudaStreamWaitEvent(side->s, side->fork, 0);
+            k_links<C><<<pg1, kPartThreads, kLinkSmem, side->s>>>(P, D);
+            cudaEventRecord(side->links_done, side->s);
+            k_cover_mark<C><<<pg2, kPartThreads, 0, side->s>>>(P, D);
+            cudaEventRecord(side->mark_done, side->s);
+            k_fdiv<C><<<g.grid, g.block, 0, s>>>(P, D);
+            cudaStreamWaitEvent(s, side->links_done, 0);
+            k_collide<C><<<g.grid, g.block, 0, s>>>(P, D);
+            k_scalars<C><<<g.grid, g.block, 0, s>>>(P, D);
+            cudaStreamWaitEvent(s, side->mark_done, 0);
+            k_cover_apply<C><<<pg2, kPartThreads, 0, s>>>(P, D);
+            return cudaGetLastError();
+        }
         if (ev) cudaEventRecord(ev[0], s);
         k_mup<C><<<g.grid, g.block, 0, s>>>(P, D);
         k_fdiv<C><<<g.grid, g.block, 0, s>>>(P, D);
@@ -56,15 +73,18 @@ struct Ops {
         return cudaGetLastError();
     }
 
-    static cudaError_t step(const DevParams& P, const DevPtrs& D, const RowGrid& g, cudaStream_t s)
+    static cudaError_t step(const DevParams& P, const DevPtrs& D, const RowGrid& g, cudaStream_t s,
+                            const SideStream* side)
     {
-        return launch_step(P, D, g, s, nullptr);
+        return launch_step(P, D, g, s, nullptr, side);
     }
 
+    // sequential order with events around the kernel classes (the per-kernel
+    // split; no overlap, so each class is timed alone)
     static cudaError_t step_events(const DevParams& P, const DevPtrs& D, const RowGrid& g, cudaStream_t s,
                                    cudaEvent_t* ev)
     {
-        return launch_step(P, D, g, s, ev);
+        return launch_step(P, D, g, s, ev, nullptr);
     }
 
     static int grid1d(const DevParams& P)
@@ -170,16 +190,32 @@ struct BOps {
         return cudaLaunchKernel((const void*)fn(nc, cfg), dim3(grid), dim3(kBatchCfgs[cfg].threads), args, 0, s);
     }
 
-    static cudaError_t step(const int cfg[4], const int grid[4], int part_grid, const BatchDev* B, cudaStream_t s)
+    static cudaError_t step(const int cfg[4], const int grid[4], int part_grid, const BatchDev* B, cudaStream_t s,
+                            const SideStream* side)
     {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
+        const size_t lsm = block_sum_t_bytes<kLinkK>(kPartThreads);
         if ((e = node(kNcMup, cfg[0], grid[0], B, s)) != cudaSuccess) return e;
-        if ((e = node(kNcFdiv, cfg[1], grid[1], B, s)) != cudaSuccess) return e;
-        kb_links<C><<<part_grid, kPartThreads, block_sum_t_bytes<kLinkK>(kPartThreads), s>>>(B);
-        if ((e = node(kNcCollide, cfg[2], grid[2], B, s)) != cudaSuccess) return e;
-        if ((e = node(kNcScalars, cfg[3], grid[3], B, s)) != cudaSuccess) return e;
-        kb_cover_mark<C><<<part_grid, kPartThreads, 0, s>>>(B);
+        if (side) {
+            cudaEventRecord(side->fork, s);
+            cudaStreamWaitEvent(side->s, side->fork, 0);
+            kb_links<C><<<part_grid, kPartThreads, lsm, side->s>>>(B);
+            cudaEventRecord(side->links_done, side->s);
+            kb_cover_mark<C><<<part_grid, kPartThreads, 0, side->s>>>(B);
+            cudaEventRecord(side->mark_done, side->s);
+            if ((e = node(kNcFdiv, cfg[1], grid[1], B, s)) != cudaSuccess) return e;
+            cudaStreamWaitEvent(s, side->links_done, 0);
+            if ((e = node(kNcCollide, cfg[2], grid[2], B, s)) != cudaSuccess) return e;
+            if ((e = node(kNcScalars, cfg[3], grid[3], B, s)) != cudaSuccess) return e;
+            cudaStreamWaitEvent(s, side->mark_done, 0);
+        } else {
+            if ((e = node(kNcFdiv, cfg[1], grid[1], B, s)) != cudaSuccess) return e;
+            kb_links<C><<<part_grid, kPartThreads, lsm, s>>>(B);
+            if ((e = node(kNcCollide, cfg[2], grid[2], B, s)) != cudaSuccess) return e;
+            if ((e = node(kNcScalars, cfg[3], grid[3], B, s)) != cudaSuccess) return e;
+            kb_cover_mark<C><<<part_grid, kPartThreads, 0, s>>>(B);
+        }
         kb_cover_apply<C><<<part_grid, kPartThreads, 0, s>>>(B);
         kb_advance<<<(kBatchMaxBoxes + 255) / 256, 256, 0, s>>>(B);
         return cudaGetLastError();
