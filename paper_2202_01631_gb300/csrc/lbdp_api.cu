@@ -144,6 +144,7 @@ RowGrid row_grid(const DevParams& P)
     int bx = P.nx >= 128 ? 128 : ((P.nx + 31) / 32) * 32;
     g.block = dim3(bx, 1, 1);
     g.grid = dim3((P.nx + bx - 1) / bx, P.ny, P.nz);
+    g.tiles = dim3((P.nx + 31) / 32, (P.ny + 3) / 4, (P.nz + 3) / 4);
     return g;
 }
 

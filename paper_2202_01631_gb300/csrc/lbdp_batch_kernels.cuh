@@ -101,16 +101,14 @@ __device__ __forceinline__ void node_body(const DevParams& P, const DevPtrs& D, 
 }
 
 // Minimum resident blocks per SM asked of the compiler, which sets the
-// register budget.  Budget 0 ("tight") is the single-box kernels' (80 per
-// thread for collide-stream, 64 for the others) and spills a little here:
-// box parameters staged in shared memory occupy registers where the
-// single-box kernels read them as constant-bank operands.  Budget 1
-// ("loose", 128 / 80) does not spill but halves collide-stream occupancy.
-// The autotuner picks.
+// register budget: 64 per thread ("tight", the single-box budget) or 80
+// ("loose").  Box parameters staged in shared memory occupy registers where
+// the single-box kernels read them as constant-bank operands, so the tight
+// budget spills a few words; the autotuner picks.
 template <int NC, int T, int RB>
 struct NodeBounds {
     static constexpr int min_blocks =
-        RB == 0 ? (NC == kNcCollide ? 768 / T : 1024 / T) : (NC == kNcCollide ? 512 / T : 768 / T);
+        RB == 0 ? 1024 / T : 768 / T;   // 64 or 80 registers
 };
 
 template <class C, int NC, int T, int CPT, int TSI, int RB>

@@ -16,6 +16,7 @@ namespace lbdp {
 // Launch geometry of the row kernels: one thread per node, blocks along x.
 struct RowGrid {
     dim3 grid, block;
+    dim3 tiles;   // grid of the 32 x 4 x 4 tiled kernels
 };
 
 // Kernel classes of one step, in launch order.

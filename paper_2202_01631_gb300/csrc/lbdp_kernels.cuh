@@ -386,6 +386,77 @@ __device__ __forceinline__ bool box_node(const DevParams& P, const int o[3], con
 }
 
 // ---------------------------------------------------------------------------
+// neighbour access of the stencil bodies.  A body sees node x through an
+// accessor: mask(i) is the mask of neighbour x + c_i (kWallSlot beyond a
+// wall) and get<k>(i) the value of field k there (own(k) = get<k>(0)).  Where
+// mask(i) is not 0 the bodies do not use get<k>(i) except multiplied by 0.
+// GAcc reads global memory through the D3Q19 neighbour indices; TAcc reads a
+// tile staged in shared memory.  Both hand the same values to the same
+// arithmetic.
+// ---------------------------------------------------------------------------
+template <class F, int NF>
+struct GAcc {
+    int nb[19];
+    int n;
+    const uint8_t* mk;
+    const F* f[NF];
+    __device__ __forceinline__ int at(int i) const { return nb[i] >= 0 ? nb[i] : n; }
+    __device__ __forceinline__ uint8_t mask(int i) const { return nb[i] >= 0 ? mk[at(i)] : kWallSlot; }
+    template <int K>
+    __device__ __forceinline__ F get(int i) const
+    {
+        return f[K][at(i)];
+    }
+};
+
+// Tile of TX x TY x TZ nodes with a one-node halo, fields [NF][slots] and
+// the mask [slots] in shared memory; slot of tile node (tx, ty, tz) is
+// (tx + 1) + HX ((ty + 1) + HY (tz + 1)).
+template <int TX, int TY, int TZ>
+struct TileShape {
+    static constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
+    static constexpr int slots = HX * HY * HZ;
+    static __host__ __device__ constexpr int off(int i) { return cx(i) + HX * (cy(i) + HY * cz(i)); }
+};
+
+template <class F, int NF, class T>
+struct TAcc {
+    const F* sf;          // [NF][T::slots]
+    const uint8_t* sm;    // [T::slots]
+    int slot;
+    __device__ __forceinline__ uint8_t mask(int i) const { return sm[slot + T::off(i)]; }
+    template <int K>
+    __device__ __forceinline__ F get(int i) const
+    {
+        return sf[K * T::slots + slot + T::off(i)];
+    }
+};
+
+// Stage fields src[0..NF-1] and the mask of the tile at (x0, y0, z0) plus
+// its halo; slots beyond a wall get kWallSlot and zeros.
+template <class F, int NF, class T>
+__device__ __forceinline__ void stage_tile(const DevParams& P, const uint8_t* mask, const F* const (&src)[NF],
+                                           int x0, int y0, int z0, F* sf, uint8_t* sm)
+{
+    for (int s = threadIdx.x; s < T::slots; s += blockDim.x) {
+        const int lx = s % T::HX, ly = (s / T::HX) % T::HY, lz = s / (T::HX * T::HY);
+        const int gx = wrap_coord(x0 + lx - 1, P.nx, P.per[0]);
+        const int gy = wrap_coord(y0 + ly - 1, P.ny, P.per[1]);
+        const int gz = wrap_coord(z0 + lz - 1, P.nz, P.per[2]);
+        if (gx >= 0 && gy >= 0 && gz >= 0) {
+            const int g = gx + P.nx * (gy + P.ny * gz);
+            sm[s] = mask[g];
+#pragma unroll
+            for (int k = 0; k < NF; ++k) sf[k * T::slots + s] = src[k][g];
+        } else {
+            sm[s] = kWallSlot;
+#pragma unroll
+            for (int k = 0; k < NF; ++k) sf[k * T::slots + s] = (F)0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // S1: chemical potentials and pressure tensor, one thread per node.  Every
 // neighbour load is issued before any decision (walls clamp to the node
 // itself), so the loads overlap instead of waiting behind mask branches.
@@ -436,32 +507,26 @@ __device__ __forceinline__ void mup_node(const DevParams& P, const DevPtrs& D, i
 //   -6 sum_i w_i [(P(x) + P~_i)/2] . c_i = -3 sum_i w_i P~_i . c_i
 // (sum_i w_i c_i = 0), with P~_i = P(x) at solid and wall neighbours.
 // ---------------------------------------------------------------------------
-template <class C>
-__device__ __forceinline__ void fdiv_node(const DevParams& P, const DevPtrs& D, int x, int y, int z)
+template <class C, class A>
+__device__ __forceinline__ void fdiv_compute(const DevParams& P, const DevPtrs& D, int n, const A& a)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
-    const int n = x + P.nx * (y + P.ny * z);
-    if (D.mask[n]) return;
     const PrmR<R>& Q = prm<R>(P);
     const size_t N = (size_t)P.N;
     R Fx = Q.g[0], Fy = Q.g[1], Fz = Q.g[2];
     if (P.thermo) {
-        const F* pt = (const F*)D.pt;
-        int nb[19];
-        neighbours(P, x, y, z, nb);
-        const R o0 = (R)pt[n], o1 = (R)pt[N + n], o2 = (R)pt[2 * N + n];
-        const R o3 = (R)pt[3 * N + n], o4 = (R)pt[4 * N + n], o5 = (R)pt[5 * N + n];
+        const R o0 = (R)a.template get<0>(0), o1 = (R)a.template get<1>(0), o2 = (R)a.template get<2>(0);
+        const R o3 = (R)a.template get<3>(0), o4 = (R)a.template get<4>(0), o5 = (R)a.template get<5>(0);
         R d0 = 0, d1 = 0, d2 = 0;
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
-            const int m = nb[i] >= 0 ? nb[i] : n;
-            const bool own = nb[i] < 0 || D.mask[m];
+            const bool own = a.mask(i) != 0;
             // components multiplied by a zero velocity component are never
             // loaded (the unrolled cdot drops them)
-            const R xx = own ? o0 : (R)pt[m], yy = own ? o1 : (R)pt[N + m], zz = own ? o2 : (R)pt[2 * N + m];
-            const R xy = own ? o3 : (R)pt[3 * N + m], xz = own ? o4 : (R)pt[4 * N + m];
-            const R yz = own ? o5 : (R)pt[5 * N + m];
+            const R xx = own ? o0 : (R)a.template get<0>(i), yy = own ? o1 : (R)a.template get<1>(i);
+            const R zz = own ? o2 : (R)a.template get<2>(i), xy = own ? o3 : (R)a.template get<3>(i);
+            const R xz = own ? o4 : (R)a.template get<4>(i), yz = own ? o5 : (R)a.template get<5>(i);
             const R w = wgt_r<R>(i);
             d0 += w * cdot<R>(i, xx, xy, xz);
             d1 += w * cdot<R>(i, xy, yy, yz);
@@ -475,6 +540,23 @@ __device__ __forceinline__ void fdiv_node(const DevParams& P, const DevPtrs& D, 
     force[n] = (F)Fx;
     force[N + n] = (F)Fy;
     force[2 * N + n] = (F)Fz;
+}
+
+template <class C>
+__device__ __forceinline__ void fdiv_node(const DevParams& P, const DevPtrs& D, int x, int y, int z)
+{
+    using F = typename C::fld_t;
+    const int n = x + P.nx * (y + P.ny * z);
+    if (D.mask[n]) return;
+    const size_t N = (size_t)P.N;
+    const F* pt = (const F*)D.pt;
+    GAcc<F, 6> a;
+    neighbours(P, x, y, z, a.nb);
+    a.n = n;
+    a.mk = D.mask;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a.f[k] = pt + k * N;
+    fdiv_compute<C>(P, D, n, a);
 }
 
 // Rotate the unit vector m by the angle |w| about w (Rodrigues):
@@ -761,62 +843,18 @@ __device__ __forceinline__ bool near_wall(const DevParams& P, int x, int y, int 
            (!P.per[2] && (z == 0 || z == P.nz - 1));
 }
 
+// BGK collision with Guo forcing of node n from its streamed populations fl
+// (f_i after pull and bounce-back) and the force F; writes f_dst and u.
 template <class C>
-__device__ __forceinline__ void collide_node(const DevParams& P, const DevPtrs& D, int x, int y, int z)
+__device__ __forceinline__ void collide_store(const PrmR<typename C::real>& Q, const DevPtrs& D, size_t N, int n,
+                                              const typename C::real (&fl)[19], typename C::real Fx,
+                                              typename C::real Fy, typename C::real Fz)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
     using S = typename C::pop_t;
-    const int n = x + P.nx * (y + P.ny * z);
-    if (D.mask[n]) return;
-    const PrmR<R>& Q = prm<R>(P);
-    const size_t N = (size_t)P.N;
-    const S* fs = (const S*)D.f_src;
     S* fd = (S*)D.f_dst;
-    const F* force = (const F*)D.force;
     const R rho0 = Q.rho0;
-    int nb[19];
-    neighbours(P, x, y, z, nb);
-    const R Fx = (R)force[n], Fy = (R)force[N + n], Fz = (R)force[2 * N + n];
-
-    R fl[19];
-    if (!D.bflag[n] && !near_wall(P, x, y, z)) {
-        // every source x - c_j is a fluid node: plain pull
-#pragma unroll
-        for (int j = 0; j < 19; ++j) fl[j] = (R)PopStore<S>::load(fs, (size_t)j * N + nb[opp(j)], j, rho0);
-    } else {
-        const F* phi = (const F*)D.phi_src;
-        const R dph = corr_r<R>(D, 1);
-        bool have_g = false;
-        R gphi[3] = {0, 0, 0};
-#pragma unroll
-        for (int j = 0; j < 19; ++j) {
-            if (j == 0) {
-                fl[0] = (R)PopStore<S>::load(fs, n, 0, rho0);
-                continue;
-            }
-            const int i = opp(j);
-            const int m = nb[i];   // source x - c_j = x + c_i
-            if (m < 0) {
-                fl[j] = (R)PopStore<S>::load(fs, (size_t)i * N + n, i, rho0);
-            } else {
-                const uint8_t q = D.mask[m];
-                if (q) {
-                    if (!have_g) {
-                        grad_phi_at<R, F>(nb, phi, D.mask, (R)phi[n] + dph, dph, gphi);
-                        have_g = true;
-                    }
-                    R r[3], ub[3], vs[3];
-                    link_velocity<R>(P, D.parts[q - 1], x, y, z, i, gphi, r, ub, vs);
-                    const R cub = (R)cx(i) * ub[0] + (R)cy(i) * ub[1] + (R)cz(i) * ub[2];
-                    const R fi = (R)PopStore<S>::load(fs, (size_t)i * N + n, i, rho0);
-                    fl[j] = fi - (R)6 * wgt_r<R>(i) * rho0 * cub;
-                } else {
-                    fl[j] = (R)PopStore<S>::load(fs, (size_t)j * N + m, j, rho0);
-                }
-            }
-        }
-    }
     R rho = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int j = 0; j < 19; ++j) {
@@ -848,84 +886,201 @@ __device__ __forceinline__ void collide_node(const DevParams& P, const DevPtrs& 
     u[2 * N + n] = (F)uz;
 }
 
-// ---------------------------------------------------------------------------
-// S4: psi and phi transport, production and sink, one thread per node
-// ---------------------------------------------------------------------------
+// Collide-stream of a fluid node next to a wall or a particle: halfway
+// bounce-back on wall links, moving bounce-back with u_b = U + Omega x r + v_s
+// on particle links.  Out of line: these nodes are few, and keeping their
+// code out of the common path keeps its register budget small.
 template <class C>
-__device__ __forceinline__ void scalars_node(const DevParams& P, const DevPtrs& D, int x, int y, int z)
+static __device__ __noinline__ void collide_boundary(const DevParams& P, const DevPtrs& D, int x, int y, int z)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
+    using S = typename C::pop_t;
     const int n = x + P.nx * (y + P.ny * z);
-    if (D.mask[n]) return;
     const PrmR<R>& Q = prm<R>(P);
     const size_t N = (size_t)P.N;
-    const F* psi = (const F*)D.psi_src;
-    const F* phi = (const F*)D.phi_src;
-    const F* mps = (const F*)D.mupsi;
-    const F* mph = (const F*)D.muphi;
-    const F* u = (const F*)D.u;
-    const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
-    const R ps = (R)psi[n] + dps, ph = (R)phi[n] + dph;
-    const R a0 = (R)mps[n], b0 = (R)mph[n];
-    const R ux = (R)u[n], uy = (R)u[N + n], uz = (R)u[2 * N + n];
+    const S* fs = (const S*)D.f_src;
+    const F* force = (const F*)D.force;
+    const R rho0 = Q.rho0;
     int nb[19];
     neighbours(P, x, y, z, nb);
+    const R Fx = (R)force[n], Fy = (R)force[N + n], Fz = (R)force[2 * N + n];
+    const F* phi = (const F*)D.phi_src;
+    const R dph = corr_r<R>(D, 1);
+    bool have_g = false;
+    R gphi[3] = {0, 0, 0};
+    R fl[19];
+#pragma unroll
+    for (int j = 0; j < 19; ++j) {
+        if (j == 0) {
+            fl[0] = (R)PopStore<S>::load(fs, n, 0, rho0);
+            continue;
+        }
+        const int i = opp(j);
+        const int m = nb[i];   // source x - c_j = x + c_i
+        if (m < 0) {
+            fl[j] = (R)PopStore<S>::load(fs, (size_t)i * N + n, i, rho0);
+        } else {
+            const uint8_t q = D.mask[m];
+            if (q) {
+                if (!have_g) {
+                    grad_phi_at<R, F>(nb, phi, D.mask, (R)phi[n] + dph, dph, gphi);
+                    have_g = true;
+                }
+                R r[3], ub[3], vs[3];
+                link_velocity<R>(P, D.parts[q - 1], x, y, z, i, gphi, r, ub, vs);
+                const R cub = cdot<R>(i, ub[0], ub[1], ub[2]);
+                const R fi = (R)PopStore<S>::load(fs, (size_t)i * N + n, i, rho0);
+                fl[j] = fma_x(-((R)6 * wgt_r<R>(i) * rho0), cub, fi);
+            } else {
+                fl[j] = (R)PopStore<S>::load(fs, (size_t)j * N + m, j, rho0);
+            }
+        }
+    }
+    collide_store<C>(Q, D, N, n, fl, Fx, Fy, Fz);
+}
+
+template <class C>
+__device__ __forceinline__ void collide_node(const DevParams& P, const DevPtrs& D, int x, int y, int z)
+{
+    using R = typename C::real;
+    using F = typename C::fld_t;
+    using S = typename C::pop_t;
+    const int n = x + P.nx * (y + P.ny * z);
+    if (D.mask[n]) return;
+    if (D.bflag[n] || near_wall(P, x, y, z)) {
+        collide_boundary<C>(P, D, x, y, z);
+        return;
+    }
+    // every source x - c_j is a fluid node: plain pull
+    const PrmR<R>& Q = prm<R>(P);
+    const size_t N = (size_t)P.N;
+    const S* fs = (const S*)D.f_src;
+    const F* force = (const F*)D.force;
+    int nb[19];
+    neighbours(P, x, y, z, nb);
+    const R Fx = (R)force[n], Fy = (R)force[N + n], Fz = (R)force[2 * N + n];
+    R fl[19];
+#pragma unroll
+    for (int j = 0; j < 19; ++j) fl[j] = (R)PopStore<S>::load(fs, (size_t)j * N + nb[opp(j)], j, Q.rho0);
+    collide_store<C>(Q, D, N, n, fl, Fx, Fy, Fz);
+}
+
+// ---------------------------------------------------------------------------
+// S4: psi and phi transport, production and sink, one thread per node
+// ---------------------------------------------------------------------------
+// Links of fluid node x into particles (k_scalars): no diffusive flux; the
+// scalars leave with the boundary velocity of the bounce-back rule,
+// c.u_b g(x); Janus production on the m.(x - X) <= 0 side of each adjacent
+// particle.  Out of line (few nodes); adds to the running sums in order.
+template <class R>
+struct LinkSums {
+    R sps, sph, src;
+};
+
+template <class C>
+static __device__ __noinline__ LinkSums<typename C::real> scalars_particle_links(
+    const DevParams& P, const DevPtrs& D, int x, int y, int z, typename C::real ps, typename C::real ph,
+    typename C::real sps, typename C::real sph)
+{
+    using R = typename C::real;
+    using F = typename C::fld_t;
+    const F* phi = (const F*)D.phi_src;
+    const R dph = corr_r<R>(D, 1);
+    int nb[19];
+    neighbours(P, x, y, z, nb);
+    unsigned long long adj = 0ull;
+    R gphi[3];
+    grad_phi_at<R, F>(nb, phi, D.mask, ph, dph, gphi);
+    for (int i = 1; i < 19; ++i) {
+        const int m = nb[i];
+        if (m < 0) continue;
+        const uint8_t mk = D.mask[m];
+        if (!mk) continue;
+        adj |= 1ull << (mk - 1);
+        R r[3], ubv[3], vs[3];
+        link_velocity<R>(P, D.parts[mk - 1], x, y, z, i, gphi, r, ubv, vs);
+        const R cub = cdot<R>(i, ubv[0], ubv[1], ubv[2]);
+        const R w = wgt_r<R>(i);
+        sps = fma_x(w, -mul_x(cub, ps), sps);
+        sph = fma_x(w, -mul_x(cub, ph), sph);
+    }
+    R src = 0;
+    while (adj) {
+        const int k = __ffsll((long long)adj) - 1;
+        adj &= adj - 1;
+        const DevPart& q = D.parts[k];
+        int Di[3];
+        int_offset(P, q.g, x, y, z, Di);
+        if (cap_minus(q, q.g, Di, 0)) src += PartR<R>::alpha(q);
+    }
+    return {sps, sph, src};
+}
+
+// Fields of the transport body: 0 psi, 1 phi, 2 mu_psi, 3 mu_phi, 4..6 u.
+template <class C, class A>
+__device__ __forceinline__ void scalars_compute(const DevParams& P, const DevPtrs& D, int x, int y, int z, int n,
+                                                const A& a)
+{
+    using R = typename C::real;
+    using F = typename C::fld_t;
+    const PrmR<R>& Q = prm<R>(P);
+    const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
+    const R ps = (R)a.template get<0>(0) + dps, ph = (R)a.template get<1>(0) + dph;
+    const R a0 = (R)a.template get<2>(0), b0 = (R)a.template get<3>(0);
+    const R ux = (R)a.template get<4>(0), uy = (R)a.template get<5>(0), uz = (R)a.template get<6>(0);
     R sps = 0, sph = 0;
     bool solid_nb = false;
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-        const int m = nb[i] >= 0 ? nb[i] : n;
-        const uint8_t mk = nb[i] >= 0 ? D.mask[m] : kWallSlot;
+        const uint8_t mk = a.mask(i);
         const R cu0 = cdot<R>(i, ux, uy, uz);
-        const R cu1 = cdot<R>(i, (R)u[m], (R)u[N + m], (R)u[2 * N + m]);
+        const R cu1 = cdot<R>(i, (R)a.template get<4>(i), (R)a.template get<5>(i), (R)a.template get<6>(i));
         const R ub = (R)0.5 * (cu0 + cu1);
-        const R psm = (R)psi[m] + dps, phm = (R)phi[m] + dph;
+        const R psm = (R)a.template get<0>(i) + dps, phm = (R)a.template get<1>(i) + dph;
         const R aps = ub > (R)0 ? ub * ps : ub * psm;
         const R aph = ub > (R)0 ? ub * ph : ub * phm;
         const R w = wgt_r<R>(i);
         // links to walls and particles carry no flux here (particle links are
         // handled below)
         const R on = mk ? (R)0 : (R)1;
-        sps += on * (w * (Q.Mpsi * ((R)mps[m] - a0) - aps));
-        sph += on * (w * (Q.Mphi * ((R)mph[m] - b0) - aph));
+        sps += on * (w * (Q.Mpsi * ((R)a.template get<2>(i) - a0) - aps));
+        sph += on * (w * (Q.Mphi * ((R)a.template get<3>(i) - b0) - aph));
         solid_nb = solid_nb || (mk != 0 && mk != kWallSlot);
     }
     R hn_src = 0;
     if (solid_nb) {
-        // links into particles: no diffusive flux; the scalar leaves with the
-        // boundary velocity of the bounce-back rule, c.u_b g(x); Janus
-        // production on the m.(x - X) <= 0 side of each adjacent particle
-        unsigned long long adj = 0ull;
-        R gphi[3];
-        grad_phi_at<R, F>(nb, phi, D.mask, ph, dph, gphi);
-        for (int i = 1; i < 19; ++i) {
-            const int m = nb[i];
-            if (m < 0) continue;
-            const uint8_t mk = D.mask[m];
-            if (!mk) continue;
-            adj |= 1ull << (mk - 1);
-            R r[3], ubv[3], vs[3];
-            link_velocity<R>(P, D.parts[mk - 1], x, y, z, i, gphi, r, ubv, vs);
-            const R cub = (R)cx(i) * ubv[0] + (R)cy(i) * ubv[1] + (R)cz(i) * ubv[2];
-            const R w = wgt_r<R>(i);
-            sps += w * ((R)0 - cub * ps);
-            sph += w * ((R)0 - cub * ph);
-        }
-        while (adj) {
-            const int k = __ffsll((long long)adj) - 1;
-            adj &= adj - 1;
-            const DevPart& q = D.parts[k];
-            int Di[3];
-            int_offset(P, q.g, x, y, z, Di);
-            if (cap_minus(q, q.g, Di, 0)) hn_src += PartR<R>::alpha(q);
-        }
+        const LinkSums<R> l = scalars_particle_links<C>(P, D, x, y, z, ps, ph, sps, sph);
+        sps = l.sps;
+        sph = l.sph;
+        hn_src = l.src;
     }
     const R pn = ps + (R)6 * sps;
     R hn = ph + (R)6 * sph - Q.kd * (ph - (Q.phib + Q.E * tanh_r(ps)));
     hn += hn_src;
     ((F*)D.psi_dst)[n] = (F)pn;
     ((F*)D.phi_dst)[n] = (F)hn;
+}
+
+template <class C>
+__device__ __forceinline__ void scalars_node(const DevParams& P, const DevPtrs& D, int x, int y, int z)
+{
+    using F = typename C::fld_t;
+    const int n = x + P.nx * (y + P.ny * z);
+    if (D.mask[n]) return;
+    const size_t N = (size_t)P.N;
+    GAcc<F, 7> a;
+    neighbours(P, x, y, z, a.nb);
+    a.n = n;
+    a.mk = D.mask;
+    a.f[0] = (const F*)D.psi_src;
+    a.f[1] = (const F*)D.phi_src;
+    a.f[2] = (const F*)D.mupsi;
+    a.f[3] = (const F*)D.muphi;
+    a.f[4] = (const F*)D.u;
+    a.f[5] = (const F*)D.u + N;
+    a.f[6] = (const F*)D.u + 2 * N;
+    scalars_compute<C>(P, D, x, y, z, n, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -1184,6 +1339,69 @@ __global__ void __launch_bounds__(kRowThreads) k_mup(DevParams P, DevPtrs D)
     if (x < P.nx) mup_node<C>(P, D, x, blockIdx.y, blockIdx.z);
 }
 
+// Tiled force and transport kernels: a 256-thread block stages the inputs
+// of a 32 x 4 x 4 tile and its halo in shared memory once, then each thread
+// computes two nodes, reading all neighbours at fixed shared-memory offsets.
+using Tile = TileShape<32, 4, 4>;
+constexpr int kTileThreads = 256;
+
+template <class F, int NF>
+__host__ __device__ constexpr size_t tile_smem() { return (size_t)NF * Tile::slots * sizeof(F) + Tile::slots; }
+
+// The two nodes of this thread: (tx, ty, tz0) and (tx, ty, tz0 + 2).
+template <class Body>
+__device__ __forceinline__ void tile_nodes(const DevParams& P, const uint8_t* sm, Body body)
+{
+    const int tx = threadIdx.x & 31, ty = (threadIdx.x >> 5) & 3, tz0 = threadIdx.x >> 7;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int tz = tz0 + 2 * h;
+        const int x = blockIdx.x * 32 + tx, y = blockIdx.y * 4 + ty, z = blockIdx.z * 4 + tz;
+        if (x >= P.nx || y >= P.ny || z >= P.nz) continue;
+        const int slot = (tx + 1) + Tile::HX * ((ty + 1) + Tile::HY * (tz + 1));
+        if (sm[slot]) continue;   // node inside a particle
+        body(x, y, z, x + P.nx * (y + P.ny * z), slot);
+    }
+}
+
+template <class C>
+__global__ void __launch_bounds__(kTileThreads) kt_fdiv(DevParams P, DevPtrs D)
+{
+    using F = typename C::fld_t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];   // tile_smem<F, 6>()
+    F* sf = (F*)smem_raw;
+    uint8_t* sm = (uint8_t*)(sf + 6 * Tile::slots);
+    const size_t N = (size_t)P.N;
+    const F* pt = (const F*)D.pt;
+    const F* const src[6] = {pt, pt + N, pt + 2 * N, pt + 3 * N, pt + 4 * N, pt + 5 * N};
+    stage_tile<F, 6, Tile>(P, D.mask, src, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, sf, sm);
+    __syncthreads();
+    tile_nodes(P, sm, [&](int, int, int, int n, int slot) {
+        const TAcc<F, 6, Tile> a{sf, sm, slot};
+        fdiv_compute<C>(P, D, n, a);
+    });
+}
+
+template <class C>
+__global__ void __launch_bounds__(kTileThreads) kt_scalars(const __grid_constant__ DevParams P,
+                                                            const __grid_constant__ DevPtrs D)
+{
+    using F = typename C::fld_t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];   // tile_smem<F, 7>()
+    F* sf = (F*)smem_raw;
+    uint8_t* sm = (uint8_t*)(sf + 7 * Tile::slots);
+    const size_t N = (size_t)P.N;
+    const F* u = (const F*)D.u;
+    const F* const src[7] = {(const F*)D.psi_src, (const F*)D.phi_src, (const F*)D.mupsi, (const F*)D.muphi,
+                             u, u + N, u + 2 * N};
+    stage_tile<F, 7, Tile>(P, D.mask, src, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, sf, sm);
+    __syncthreads();
+    tile_nodes(P, sm, [&](int x, int y, int z, int n, int slot) {
+        const TAcc<F, 7, Tile> a{sf, sm, slot};
+        scalars_compute<C>(P, D, x, y, z, n, a);
+    });
+}
+
 template <class C>
 __global__ void __launch_bounds__(kRowThreads) k_fdiv(DevParams P, DevPtrs D)
 {
@@ -1192,14 +1410,16 @@ __global__ void __launch_bounds__(kRowThreads) k_fdiv(DevParams P, DevPtrs D)
 }
 
 template <class C>
-__global__ void __launch_bounds__(kRowThreads, 6) k_collide(DevParams P, DevPtrs D)
+__global__ void __launch_bounds__(kRowThreads, 8) k_collide(const __grid_constant__ DevParams P,
+                                                             const __grid_constant__ DevPtrs D)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x < P.nx) collide_node<C>(P, D, x, blockIdx.y, blockIdx.z);
 }
 
 template <class C>
-__global__ void __launch_bounds__(kRowThreads) k_scalars(DevParams P, DevPtrs D)
+__global__ void __launch_bounds__(kRowThreads) k_scalars(const __grid_constant__ DevParams P,
+                                                          const __grid_constant__ DevPtrs D)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x < P.nx) scalars_node<C>(P, D, x, blockIdx.y, blockIdx.z);

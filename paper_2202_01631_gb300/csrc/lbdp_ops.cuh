@@ -17,6 +17,8 @@ struct Ops {
     using R = typename C::real;
 
     static constexpr size_t kLinkSmem = block_sum_t_bytes<kLinkK>(kPartThreads);
+    static constexpr size_t kFdivSmem = tile_smem<typename C::fld_t, 6>();
+    static constexpr size_t kScalSmem = tile_smem<typename C::fld_t, 7>();
 
     // Opt the kernels that use more than 48 KiB of shared memory in, once per
     // device.
@@ -28,6 +30,10 @@ struct Ops {
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
         e = cudaFuncSetAttribute(k_links<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinkSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kt_fdiv<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFdivSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kt_scalars<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScalSmem);
         if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
         return e;
     }
@@ -47,23 +53,23 @@ struct Ops {
             cudaEventRecord(side->links_done, side->s);
             k_cover_mark<C><<<pg2, kPartThreads, 0, side->s>>>(P, D);
             cudaEventRecord(side->mark_done, side->s);
-            k_fdiv<C><<<g.grid, g.block, 0, s>>>(P, D);
+            kt_fdiv<C><<<g.tiles, kTileThreads, kFdivSmem, s>>>(P, D);
             cudaStreamWaitEvent(s, side->links_done, 0);
             k_collide<C><<<g.grid, g.block, 0, s>>>(P, D);
-            k_scalars<C><<<g.grid, g.block, 0, s>>>(P, D);
+            kt_scalars<C><<<g.tiles, kTileThreads, kScalSmem, s>>>(P, D);
             cudaStreamWaitEvent(s, side->mark_done, 0);
             k_cover_apply<C><<<pg2, kPartThreads, 0, s>>>(P, D);
             return cudaGetLastError();
         }
         if (ev) cudaEventRecord(ev[0], s);
         k_mup<C><<<g.grid, g.block, 0, s>>>(P, D);
-        k_fdiv<C><<<g.grid, g.block, 0, s>>>(P, D);
+        kt_fdiv<C><<<g.tiles, kTileThreads, kFdivSmem, s>>>(P, D);
         if (ev) cudaEventRecord(ev[1], s);
         if (P.np > 0) k_links<C><<<pg1, kPartThreads, kLinkSmem, s>>>(P, D);
         if (ev) cudaEventRecord(ev[2], s);
         k_collide<C><<<g.grid, g.block, 0, s>>>(P, D);
         if (ev) cudaEventRecord(ev[3], s);
-        k_scalars<C><<<g.grid, g.block, 0, s>>>(P, D);
+        kt_scalars<C><<<g.tiles, kTileThreads, kScalSmem, s>>>(P, D);
         if (ev) cudaEventRecord(ev[4], s);
         if (P.np > 0) {
             k_cover_mark<C><<<pg2, kPartThreads, 0, s>>>(P, D);
