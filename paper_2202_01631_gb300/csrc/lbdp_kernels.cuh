@@ -228,15 +228,16 @@ __device__ __forceinline__ R psi_ghost(const DevParams& P, const DevPart& q, int
     return fma_x(PartR<R>::Hk(q), cn, ps);
 }
 
-// Equilibrium population i of (rho, u) (refill of uncovered nodes and the
-// host-set state), rounding written out.
+// Equilibrium population i of (rho, u) as its deviation from the rest
+// equilibrium, f_eq - w_i rho0 =
+// w_i [(rho - rho0) + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)], rounding written out.
 template <class Real>
-__device__ __forceinline__ Real feq_i(int i, Real rho, Real ux, Real uy, Real uz)
+__device__ __forceinline__ Real geq_i(int i, Real rho, Real rho0, Real ux, Real uy, Real uz)
 {
     const Real cu = cdot<Real>(i, ux, uy, uz);
     const Real uu = dot_x(ux, uy, uz, ux, uy, uz);
-    const Real t = fma_x((Real)-1.5, uu, fma_x(mul_x((Real)4.5, cu), cu, fma_x((Real)3, cu, (Real)1)));
-    return mul_x(mul_x(wgt_r<Real>(i), rho), t);
+    const Real t = fma_x((Real)-1.5, uu, fma_x(mul_x((Real)4.5, cu), cu, mul_x((Real)3, cu)));
+    return mul_x(wgt_r<Real>(i), fma_x(rho, t, add_x(rho, -rho0)));
 }
 
 __device__ __forceinline__ float tanh_r(float v) { return tanhf(v); }
@@ -461,28 +462,23 @@ __device__ __forceinline__ void stage_tile(const DevParams& P, const uint8_t* ma
 // neighbour load is issued before any decision (walls clamp to the node
 // itself), so the loads overlap instead of waiting behind mask branches.
 // ---------------------------------------------------------------------------
-template <class C>
-__device__ __forceinline__ void mup_node(const DevParams& P, const DevPtrs& D, int x, int y, int z)
+// Fields of the chemical-potential body: 0 psi, 1 phi.
+template <class C, class A>
+__device__ __forceinline__ void mup_compute(const DevParams& P, const DevPtrs& D, int x, int y, int z, int n,
+                                            const A& a)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
-    const int n = x + P.nx * (y + P.ny * z);
-    if (D.mask[n]) return;
     const PrmR<R>& Q = prm<R>(P);
     const size_t N = (size_t)P.N;
-    const F* psi = (const F*)D.psi_src;
-    const F* phi = (const F*)D.phi_src;
     const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
-    int nb[19];
-    neighbours(P, x, y, z, nb);
     R v[19];
     uint8_t mk[19];
-    v[0] = (R)psi[n] + dps;
+    v[0] = (R)a.template get<0>(0) + dps;
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-        const int m = nb[i] >= 0 ? nb[i] : n;
-        mk[i] = nb[i] >= 0 ? D.mask[m] : kWallSlot;
-        v[i] = (R)psi[m] + dps;
+        mk[i] = a.mask(i);
+        v[i] = (R)a.template get<0>(i) + dps;
     }
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
@@ -492,7 +488,7 @@ __device__ __forceinline__ void mup_node(const DevParams& P, const DevPtrs& D, i
             v[i] = psi_ghost<R>(P, D.parts[mk[i] - 1], x, y, z, i, v[0]);
     }
     R mps, mph, pt[6];
-    mu_pressure<R>(Q, v, (R)phi[n] + dph, P.thermo != 0, mps, mph, pt);
+    mu_pressure<R>(Q, v, (R)a.template get<1>(0) + dph, P.thermo != 0, mps, mph, pt);
     ((F*)D.mupsi)[n] = (F)mps;
     ((F*)D.muphi)[n] = (F)mph;
     if (P.thermo) {
@@ -500,6 +496,21 @@ __device__ __forceinline__ void mup_node(const DevParams& P, const DevPtrs& D, i
 #pragma unroll
         for (int k = 0; k < 6; ++k) ptg[k * N + n] = (F)pt[k];
     }
+}
+
+template <class C>
+__device__ __forceinline__ void mup_node(const DevParams& P, const DevPtrs& D, int x, int y, int z)
+{
+    using F = typename C::fld_t;
+    const int n = x + P.nx * (y + P.ny * z);
+    if (D.mask[n]) return;
+    GAcc<F, 2> a;
+    neighbours(P, x, y, z, a.nb);
+    a.n = n;
+    a.mk = D.mask;
+    a.f[0] = (const F*)D.psi_src;
+    a.f[1] = (const F*)D.phi_src;
+    mup_compute<C>(P, D, x, y, z, n, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -843,11 +854,16 @@ __device__ __forceinline__ bool near_wall(const DevParams& P, int x, int y, int 
            (!P.per[2] && (z == 0 || z == P.nz - 1));
 }
 
-// BGK collision with Guo forcing of node n from its streamed populations fl
-// (f_i after pull and bounce-back) and the force F; writes f_dst and u.
+// BGK collision with Guo forcing of node n from its streamed populations,
+// given as deviations g_i = f_i - w_i rho0 (FP32 cancellation in the moments
+// would otherwise cost the small velocity its low digits):
+//   rho = rho0 + sum g,  j = sum c g  (sum_i w_i c_i = 0),
+//   g_eq = w [(rho - rho0) + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)],
+//   g* = g - (g - g_eq)/tau + (1 - 1/(2 tau)) S_i.
+// Writes f_dst (as deviations through the storage) and u.
 template <class C>
 __device__ __forceinline__ void collide_store(const PrmR<typename C::real>& Q, const DevPtrs& D, size_t N, int n,
-                                              const typename C::real (&fl)[19], typename C::real Fx,
+                                              const typename C::real (&gl)[19], typename C::real Fx,
                                               typename C::real Fy, typename C::real Fz)
 {
     using R = typename C::real;
@@ -855,14 +871,15 @@ __device__ __forceinline__ void collide_store(const PrmR<typename C::real>& Q, c
     using S = typename C::pop_t;
     S* fd = (S*)D.f_dst;
     const R rho0 = Q.rho0;
-    R rho = 0, jx = 0, jy = 0, jz = 0;
+    R dr = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int j = 0; j < 19; ++j) {
-        rho += fl[j];
-        if (cx(j) != 0) jx += cx(j) > 0 ? fl[j] : -fl[j];
-        if (cy(j) != 0) jy += cy(j) > 0 ? fl[j] : -fl[j];
-        if (cz(j) != 0) jz += cz(j) > 0 ? fl[j] : -fl[j];
+        dr += gl[j];
+        if (cx(j) != 0) jx += cx(j) > 0 ? gl[j] : -gl[j];
+        if (cy(j) != 0) jy += cy(j) > 0 ? gl[j] : -gl[j];
+        if (cz(j) != 0) jz += cz(j) > 0 ? gl[j] : -gl[j];
     }
+    const R rho = rho0 + dr;
     const R ux = (jx + (R)0.5 * Fx) / rho;
     const R uy = (jy + (R)0.5 * Fy) / rho;
     const R uz = (jz + (R)0.5 * Fz) / rho;
@@ -876,9 +893,9 @@ __device__ __forceinline__ void collide_store(const PrmR<typename C::real>& Q, c
         const R w = wgt_r<R>(j);
         // Guo source w [3 (c - u) + 9 (c.u) c] . F = w [3 (c.F - u.F) + 9 (c.u)(c.F)]
         const R Sg = w * ((R)3 * (cF - uF) + (R)9 * cu * cF);
-        const R fe = w * rho * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu);
-        const R out = fl[j] - (fl[j] - fe) * itau + omf * Sg;
-        PopStore<S>::store(fd, (size_t)j * N + n, j, rho0, out);
+        const R ge = w * (dr + rho * ((R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu));
+        const R out = gl[j] - (gl[j] - ge) * itau + omf * Sg;
+        PopStore<S>::store_dev(fd, (size_t)j * N + n, j, rho0, out);
     }
     F* u = (F*)D.u;
     u[n] = (F)ux;
@@ -913,13 +930,13 @@ static __device__ __noinline__ void collide_boundary(const DevParams& P, const D
 #pragma unroll
     for (int j = 0; j < 19; ++j) {
         if (j == 0) {
-            fl[0] = (R)PopStore<S>::load(fs, n, 0, rho0);
+            fl[0] = (R)PopStore<S>::load_dev(fs, n, 0, rho0);
             continue;
         }
         const int i = opp(j);
         const int m = nb[i];   // source x - c_j = x + c_i
         if (m < 0) {
-            fl[j] = (R)PopStore<S>::load(fs, (size_t)i * N + n, i, rho0);
+            fl[j] = (R)PopStore<S>::load_dev(fs, (size_t)i * N + n, i, rho0);
         } else {
             const uint8_t q = D.mask[m];
             if (q) {
@@ -930,10 +947,10 @@ static __device__ __noinline__ void collide_boundary(const DevParams& P, const D
                 R r[3], ub[3], vs[3];
                 link_velocity<R>(P, D.parts[q - 1], x, y, z, i, gphi, r, ub, vs);
                 const R cub = cdot<R>(i, ub[0], ub[1], ub[2]);
-                const R fi = (R)PopStore<S>::load(fs, (size_t)i * N + n, i, rho0);
+                const R fi = (R)PopStore<S>::load_dev(fs, (size_t)i * N + n, i, rho0);
                 fl[j] = fma_x(-((R)6 * wgt_r<R>(i) * rho0), cub, fi);
             } else {
-                fl[j] = (R)PopStore<S>::load(fs, (size_t)j * N + m, j, rho0);
+                fl[j] = (R)PopStore<S>::load_dev(fs, (size_t)j * N + m, j, rho0);
             }
         }
     }
@@ -962,7 +979,7 @@ __device__ __forceinline__ void collide_node(const DevParams& P, const DevPtrs& 
     const R Fx = (R)force[n], Fy = (R)force[N + n], Fz = (R)force[2 * N + n];
     R fl[19];
 #pragma unroll
-    for (int j = 0; j < 19; ++j) fl[j] = (R)PopStore<S>::load(fs, (size_t)j * N + nb[opp(j)], j, Q.rho0);
+    for (int j = 0; j < 19; ++j) fl[j] = (R)PopStore<S>::load_dev(fs, (size_t)j * N + nb[opp(j)], j, Q.rho0);
     collide_store<C>(Q, D, N, n, fl, Fx, Fy, Fz);
 }
 
@@ -1204,7 +1221,7 @@ __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevP
             R jr[3] = {0, 0, 0};
 #pragma unroll
             for (int i = 0; i < 19; ++i) {
-                const R fi = (R)PopStore<S>::load(f, (size_t)i * N + n, i, rho0);
+                const R fi = (R)PopStore<S>::load_dev(f, (size_t)i * N + n, i, rho0);   // sum c f = sum c g
                 if (cx(i) != 0) jr[0] = cx(i) > 0 ? add_x(jr[0], fi) : add_x(jr[0], -fi);
                 if (cy(i) != 0) jr[1] = cy(i) > 0 ? add_x(jr[1], fi) : add_x(jr[1], -fi);
                 if (cz(i) != 0) jr[2] = cz(i) > 0 ? add_x(jr[2], fi) : add_x(jr[2], -fi);
@@ -1231,10 +1248,10 @@ __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevP
             for (int i = 1; i < 19; ++i) {
                 const int m = nb[i];
                 if (m < 0 || D.mask[m] || D.mask_next[m]) continue;
-                R rm = 0;
+                R rm = 0;   // rho - rho0 = sum g
 #pragma unroll
-                for (int k = 0; k < 19; ++k) rm = add_x(rm, (R)PopStore<S>::load(f, (size_t)k * N + m, k, rho0));
-                rb = add_x(rb, rm);
+                for (int k = 0; k < 19; ++k) rm = add_x(rm, (R)PopStore<S>::load_dev(f, (size_t)k * N + m, k, rho0));
+                rb = add_x(rb, add_x(rho0, rm));
                 pb = add_x(pb, (R)psi[m]);
                 hb = add_x(hb, (R)phi[m]);
                 ++cnt;
@@ -1258,7 +1275,7 @@ __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevP
                              add_x(U2, cross_x(W0, r[1], W1, r[0]))};
 #pragma unroll
             for (int i = 0; i < 19; ++i)
-                PopStore<S>::store(f, (size_t)i * N + n, i, rho0, feq_i<R>(i, rb, ub[0], ub[1], ub[2]));
+                PopStore<S>::store_dev(f, (size_t)i * N + n, i, rho0, geq_i<R>(i, rb, rho0, ub[0], ub[1], ub[2]));
             u[n] = (F)ub[0];
             u[N + n] = (F)ub[1];
             u[2 * N + n] = (F)ub[2];
@@ -1481,15 +1498,15 @@ __global__ void k_set_fields(DevParams P, DevPtrs D, const double* rho_in, const
         if (rho_in) {
             rho = rho_in[n];
         } else {
-            R s = 0;
+            R s = 0;   // rho - rho0
 #pragma unroll
-            for (int i = 0; i < 19; ++i) s += (R)PopStore<S>::load(f, (size_t)i * N + n, i, rho0);
-            rho = (double)s;
+            for (int i = 0; i < 19; ++i) s += (R)PopStore<S>::load_dev(f, (size_t)i * N + n, i, rho0);
+            rho = P.rho0 + (double)s;
         }
         const double ux = (double)u[n], uy = (double)u[N + n], uz = (double)u[2 * N + n];
 #pragma unroll
         for (int i = 0; i < 19; ++i)
-            PopStore<S>::store(f, (size_t)i * N + n, i, rho0, (R)feq_i<double>(i, rho, ux, uy, uz));
+            PopStore<S>::store_dev(f, (size_t)i * N + n, i, rho0, (R)geq_i<double>(i, rho, P.rho0, ux, uy, uz));
     }
 }
 
@@ -1536,11 +1553,11 @@ __global__ void k_get_fields(DevParams P, DevPtrs D, int which, double* out_rho,
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
         const bool solid = D.mask[n] != 0;
         if (which & 1) {
-            R s = 0;
+            R s = 0;   // rho - rho0
             if (!solid)
 #pragma unroll
-                for (int i = 0; i < 19; ++i) s += (R)PopStore<S>::load(f, (size_t)i * N + n, i, rho0);
-            out_rho[n] = solid ? 0.0 : (double)s;
+                for (int i = 0; i < 19; ++i) s += (R)PopStore<S>::load_dev(f, (size_t)i * N + n, i, rho0);
+            out_rho[n] = solid ? 0.0 : P.rho0 + (double)s;
         }
         if (which & 2)
             for (int a = 0; a < 3; ++a) out_u[a * N + n] = solid ? 0.0 : (double)u[a * N + n];

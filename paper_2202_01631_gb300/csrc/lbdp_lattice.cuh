@@ -228,10 +228,20 @@ struct DevPtrs {
 template <class S>
 struct PopStore;
 
+// load/store move f_i; load_dev/store_dev move the deviation from the rest
+// equilibrium, g_i = f_i - w_i rho0, in which collide-stream works.
 template <>
 struct PopStore<double> {
     static __device__ __forceinline__ double load(const double* p, size_t k, int, double) { return p[k]; }
     static __device__ __forceinline__ void store(double* p, size_t k, int, double, double f) { p[k] = f; }
+    static __device__ __forceinline__ double load_dev(const double* p, size_t k, int i, double rho0)
+    {
+        return fma_x(-wgt_r<double>(i), rho0, p[k]);
+    }
+    static __device__ __forceinline__ void store_dev(double* p, size_t k, int i, double rho0, double g)
+    {
+        p[k] = fma_x(wgt_r<double>(i), rho0, g);
+    }
 };
 
 // FP32: f_i - w_i rho0 keeps the O(1e-2) deviations at full FP32 precision.
@@ -245,6 +255,8 @@ struct PopStore<float> {
     {
         p[k] = fma_x(-wgt_r<float>(i), rho0, f);
     }
+    static __device__ __forceinline__ float load_dev(const float* p, size_t k, int, float) { return p[k]; }
+    static __device__ __forceinline__ void store_dev(float* p, size_t k, int, float, float g) { p[k] = g; }
 };
 
 // FP16/BF16: (f_i - w_i rho0)/w_i, a deviation of the same scale in every
@@ -259,6 +271,14 @@ struct PopStore<__half> {
     {
         p[k] = __float2half_rn(fma_x(f, inv_wgt_r<float>(i), -rho0));
     }
+    static __device__ __forceinline__ float load_dev(const __half* p, size_t k, int i, float)
+    {
+        return __half2float(p[k]) * wgt_r<float>(i);
+    }
+    static __device__ __forceinline__ void store_dev(__half* p, size_t k, int i, float, float g)
+    {
+        p[k] = __float2half_rn(g * inv_wgt_r<float>(i));
+    }
 };
 
 template <>
@@ -270,6 +290,14 @@ struct PopStore<__nv_bfloat16> {
     static __device__ __forceinline__ void store(__nv_bfloat16* p, size_t k, int i, float rho0, float f)
     {
         p[k] = __float2bfloat16_rn(fma_x(f, inv_wgt_r<float>(i), -rho0));
+    }
+    static __device__ __forceinline__ float load_dev(const __nv_bfloat16* p, size_t k, int i, float)
+    {
+        return __bfloat162float(p[k]) * wgt_r<float>(i);
+    }
+    static __device__ __forceinline__ void store_dev(__nv_bfloat16* p, size_t k, int i, float, float g)
+    {
+        p[k] = __float2bfloat16_rn(g * inv_wgt_r<float>(i));
     }
 };
 
