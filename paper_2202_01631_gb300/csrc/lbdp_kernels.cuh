@@ -331,9 +331,10 @@ __device__ void block_sum(double (&v)[K], double* smem /* [32*K] */)
 }
 
 // FP64 block reduction through shared memory: each warp transposes its K x 32
-// values so that lane k adds column k (warps holding only zeros skip it), then
-// K threads add the warp results in warp order.  The order is fixed, so the
-// result is deterministic; it is valid in thread 0.  sm holds
+// values so that lane k adds column k (column k + 32 in a second pass when
+// K > 32; warps holding only zeros skip it), then threads add the warp results
+// in warp order.  The order is fixed, so the result is deterministic; it is
+// valid in thread 0 and stays in sm[0..K-1].  sm holds
 // (32 + 1) * K * (blockDim.x / 32) doubles.
 template <int K>
 __device__ void block_sum_t(double (&v)[K], double* sm)
@@ -350,17 +351,21 @@ __device__ void block_sum_t(double (&v)[K], double* sm)
         for (int k = 0; k < K; ++k) wbuf[lane * K + k] = v[k];
     }
     __syncwarp();
-    if (lane < K) {
-        double s = 0.0;
-        if (any)
-            for (int l = 0; l < 32; ++l) s += wbuf[l * K + lane];
-        wres[warp * K + lane] = s;
+#pragma unroll
+    for (int c0 = 0; c0 < K; c0 += 32) {
+        const int c = c0 + lane;
+        if (c < K) {
+            double s = 0.0;
+            if (any)
+                for (int l = 0; l < 32; ++l) s += wbuf[l * K + c];
+            wres[warp * K + c] = s;
+        }
     }
     __syncthreads();
-    if (threadIdx.x < K) {
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
         double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += wres[w * K + threadIdx.x];
-        sm[threadIdx.x] = s;
+        for (int w = 0; w < nw; ++w) s += wres[w * K + k];
+        sm[k] = s;
     }
     __syncthreads();
     if (threadIdx.x == 0)
@@ -668,6 +673,17 @@ static __device__ __noinline__ void particle_update(int3 L3, int3 per3, DevPart*
         if (!ok && lane == 0) atomicOr(err, kErrSolve);
     }
     DevPart& dp = parts[p];
+    if (lane == 0) {
+        // psi, phi carried into the surface: sum 6 w g c.u_b with u_b at V(t+1)
+        double wps = tot[kLinkGpsi + 6], wph = tot[kLinkGphi + 6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            wps = fma_x(tot[kLinkGpsi + c], xv[c], wps);
+            wph = fma_x(tot[kLinkGphi + c], xv[c], wph);
+        }
+        dp.wall_psi = wps;
+        dp.wall_phi = wph;
+    }
     if (lane < 6) {
         double zv = 0.0;
 #pragma unroll
@@ -743,7 +759,7 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
     const S* fs = (const S*)D.f_src;
     const F* psi = (const F*)D.psi_src;
     const F* phi = (const F*)D.phi_src;
-    const R dph = corr_r<R>(D, 1);
+    const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
     // floor(X) - ceil(R) <= floor(X - R): the box holds every fluid node within
     // R + 2 of the centre
     const int o[3] = {q.g.Xi[0] - q.Rc - 2, q.g.Xi[1] - q.Rc - 2, q.g.Xi[2] - q.Rc - 2};
@@ -772,8 +788,9 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
         R fv[19];
 #pragma unroll
         for (int i = 1; i < 19; ++i) fv[i] = (R)PopStore<S>::load(fs, (size_t)i * N + n, i, Q.rho0);
+        const R ps = (R)psi[n] + dps, ph = (R)phi[n] + dph;
         R gphi[3];
-        grad_phi_at<R, F>(nb, phi, D.mask, (R)phi[n] + dph, dph, gphi);
+        grad_phi_at<R, F>(nb, phi, D.mask, ph, dph, gphi);
         R pt[6] = {0, 0, 0, 0, 0, 0};
         if (P.thermo) {
             // the pressure tensor the fluid's force used this step
@@ -815,6 +832,16 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
             for (int a = 0; a < 6; ++a)
 #pragma unroll
                 for (int b = a; b < 6; ++b, ++k) nacc[k] = fma_x(mul_x(zc, g6[a]), g6[b], nacc[k]);
+            // scalar flux into the surface, 6 w g(x) c.u_b with
+            // c.u_b = (c, r x c) . V(t+1) + c.v_s
+            const R wps = mul_x(w6, ps), wph = mul_x(w6, ph);
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+                nacc[kLinkGpsi + a] = fma_x(wps, g6[a], nacc[kLinkGpsi + a]);
+                nacc[kLinkGphi + a] = fma_x(wph, g6[a], nacc[kLinkGphi + a]);
+            }
+            nacc[kLinkGpsi + 6] = fma_x(wps, cvs, nacc[kLinkGpsi + 6]);
+            nacc[kLinkGphi + 6] = fma_x(wph, cvs, nacc[kLinkGphi + 6]);
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] += (double)nacc[k];
@@ -842,7 +869,7 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
     block_sum_t<K>(sum, smem);   // the totals stay in smem[0..K-1]
     if (threadIdx.x >= 32) return;
     particle_update(make_int3(P.nx, P.ny, P.nz), make_int3(P.per[0], P.per[1], P.per[2]), D.parts, D.link_ticket,
-                    D.err, p, q, smem, smem + 32);
+                    D.err, p, q, smem, smem + 64);   // totals in smem[0..K-1], K <= 64
 }
 
 // ---------------------------------------------------------------------------
@@ -1168,11 +1195,8 @@ __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevP
     S* f = (S*)D.f_dst;
     F* psi = (F*)D.psi_dst;
     F* phi = (F*)D.phi_dst;
-    const F* psi0 = (const F*)D.psi_src;
-    const F* phi0 = (const F*)D.phi_src;
     F* u = (F*)D.u;
     const R rho0 = prm<R>(P).rho0;
-    const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
@@ -1183,37 +1207,15 @@ __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevP
         const uint8_t ob = D.mask[n], nw = D.mask_next[n];
         int nb[19];
         neighbours(P, x, y, z, nb);
-        // boundary flag for the next step (fluid node with a solid neighbour)
-        // and the links of this node into particle p; all mask loads first
-        bool adj = false, lk[19], any = false;
+        // boundary flag for the next step (fluid node with a solid neighbour);
+        // all mask loads first
+        bool adj = false;
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
             const int m = nb[i] >= 0 ? nb[i] : n;
             adj = adj || (nb[i] >= 0 && D.mask_next[m]);
-            lk[i] = ob == 0 && nb[i] >= 0 && D.mask[m] == p + 1;
-            any = any || lk[i];
         }
         D.bflag[n] = (!nw && adj) ? 1 : 0;
-        if (any) {
-            // psi, phi carried into the surface this step through the links of
-            // this node into particle p: 6 w_i c_i.u_b g(x), as in k_scalars
-            const R ps = (R)psi0[n] + dps, ph = (R)phi0[n] + dph;
-            R gphi[3];
-            grad_phi_at<R, F>(nb, phi0, D.mask, ph, dph, gphi);
-            R a9 = 0, a10 = 0;
-#pragma unroll
-            for (int i = 1; i < 19; ++i) {
-                if (!lk[i]) continue;
-                R r[3], ub[3], vs[3];
-                link_velocity<R>(P, q, x, y, z, i, gphi, r, ub, vs);
-                const R cub = cdot<R>(i, ub[0], ub[1], ub[2]);
-                const R w6 = (R)6 * wgt_r<R>(i);
-                a9 = fma_x(w6, mul_x(cub, ps), a9);
-                a10 = fma_x(w6, mul_x(cub, ph), a10);
-            }
-            acc[9] += (double)a9;
-            acc[10] += (double)a10;
-        }
         if (ob == nw) continue;
         if (ob == 0 && nw == p + 1) {
             // covered: the particle takes the momentum the node's populations
@@ -1330,8 +1332,8 @@ __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevP
                 dk.mf[a] = (float)dk.mn[a];
             }
             dk.g = dk.gn;
-            dsum_psi += s[6] + s[9];
-            dsum_phi += s[7] + s[10];
+            dsum_psi += s[6] + dk.wall_psi;
+            dsum_phi += s[7] + dk.wall_phi;
             dcnt += s[8];
         }
     }

@@ -179,6 +179,7 @@ struct DevPart {
     double ext_f[3], ext_t[3];
     double imp_f[3], imp_t[3];       // covering impulses, applied in the next step
     double force[3], torque[3];
+    double wall_psi, wall_phi;       // psi, phi carried into the surface this step
     int fixed;
     int pad;
 };
@@ -190,9 +191,14 @@ enum : int {
     kErrSolve = 4,     // singular particle velocity system
 };
 
-constexpr int kLinkK = 27;    // per-block link partials: F0[3], T0[3], zeta upper triangle [21]
-constexpr int kCoverK = 11;   // per-block cover partials: impulse F[3], T[3], dpsi, dphi,
-                              // dcount, wall psi, wall phi
+// per-block link partials: F0[3], T0[3], zeta upper triangle [21], then the
+// coefficients of the scalar flux into the surface, linear in V(t+1):
+// sum 6 w psi (c, r x c) [6], sum 6 w psi c.v_s, and the same for phi
+constexpr int kLinkK = 41;
+constexpr int kLinkGpsi = 27, kLinkGphi = 34;
+static_assert(kLinkK <= 64, "the particle update keeps its scratch at smem + 64");
+constexpr int kCoverK = 9;    // per-block cover partials: impulse F[3], T[3], dpsi, dphi,
+                              // dcount
 constexpr int kMaxPartBlocks = 128;
 
 // Raw device pointers of one step (type-erased storage).
