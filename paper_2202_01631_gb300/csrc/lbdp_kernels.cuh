@@ -108,7 +108,8 @@ __device__ __forceinline__ void grad_phi_at(const int nb[19], const Fld* phi, co
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
         int m = nb[i];
-        R v = (m < 0 || mask[m]) ? own : (R)phi[m] + dphi;
+        // differences from the node's own value (sum_i w_i c_i = 0)
+        const R v = (m < 0 || mask[m]) ? (R)0 : add_x((R)phi[m] + dphi, -own);
         const R w = wgt_r<R>(i);
         if (cx(i) != 0) g[0] = fma_x(cx(i) > 0 ? w : -w, v, g[0]);
         if (cy(i) != 0) g[1] = fma_x(cy(i) > 0 ? w : -w, v, g[1]);
@@ -250,6 +251,13 @@ __device__ __forceinline__ double tanh_r(double v) { return tanh(v); }
 //   P = [psi mu_psi + phi mu_phi - f - kappa |grad psi|^2/2] I + kappa grad psi grad psi,
 //   f = A psi^4/4 - A psi^2/2 + C (phi - phi0)^2/2.               (Eq. free_energy)
 // 1/cosh^2 is taken as 1 - tanh^2.  P is returned as xx yy zz xy xz yz.
+// Written for FP32: A psi (psi^2 - 1) and f + A/4 = A (psi^2 - 1)^2 / 4 + ...
+// do not cancel in the bulk phases, the stencils act on differences from the
+// node's own value (sum_i w_i c_i = 0), and P is returned less the bulk
+// pressure A/4 on its diagonal.  A constant part of P exerts no force: the
+// link-form divergence sums w_i c_i over all 18 directions of a node, and the
+// particle stress sums w_i c_i and w_i r_b x c_i over the boundary links of a
+// sphere, which vanish for the same reason.
 template <class R>
 __device__ __forceinline__ void mu_pressure(const PrmR<R>& Q, const R v[19], R ph, bool want_p, R& mps, R& mph,
                                             R pt[6])
@@ -259,8 +267,8 @@ __device__ __forceinline__ void mu_pressure(const PrmR<R>& Q, const R v[19], R p
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
         const R w = wgt_r<R>(i);
-        const R wv = w * v[i];
-        lap += w * (v[i] - ps);
+        const R wv = w * (v[i] - ps);
+        lap += wv;
         if (cx(i) != 0) g0 += cx(i) > 0 ? wv : -wv;
         if (cy(i) != 0) g1 += cy(i) > 0 ? wv : -wv;
         if (cz(i) != 0) g2 += cz(i) > 0 ? wv : -wv;
@@ -272,11 +280,12 @@ __device__ __forceinline__ void mu_pressure(const PrmR<R>& Q, const R v[19], R p
     const R th = tanh_r(ps);
     const R dphi = ph - (Q.phib + Q.E * th);
     mph = Q.C * dphi;
-    mps = Q.A * (ps * ps * ps - ps) - Q.kappa * lap - Q.C * Q.E * dphi * ((R)1 - th * th);
+    const R t = fma_x(ps, ps, (R)-1);   // psi^2 - 1
+    mps = Q.A * ps * t - Q.kappa * lap - Q.C * Q.E * dphi * ((R)1 - th * th);
     if (!want_p) return;
-    const R f = (R)0.25 * Q.A * ps * ps * ps * ps - (R)0.5 * Q.A * ps * ps + (R)0.5 * Q.C * dphi * dphi;
+    const R fs = (R)0.25 * Q.A * t * t + (R)0.5 * Q.C * dphi * dphi;   // f + A/4
     const R gg = g0 * g0 + g1 * g1 + g2 * g2;
-    const R piso = ps * mps + ph * mph - f - (R)0.5 * Q.kappa * gg;
+    const R piso = ps * mps + ph * mph - fs - (R)0.5 * Q.kappa * gg;   // less A/4
     pt[0] = piso + Q.kappa * g0 * g0;
     pt[1] = piso + Q.kappa * g1 * g1;
     pt[2] = piso + Q.kappa * g2 * g2;
