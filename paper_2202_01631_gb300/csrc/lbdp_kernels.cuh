@@ -434,16 +434,30 @@ struct TileShape {
     static __host__ __device__ constexpr int off(int i) { return cx(i) + HX * (cy(i) + HY * cz(i)); }
 };
 
+// Shared-memory place of field k of slot s: fields 2j and 2j+1 interleave
+// ([j][slot][2]), so a body that reads both gets them in one 64-bit load; an
+// odd last field stands alone.
+template <class T>
+__host__ __device__ constexpr int tile_index(int k, int s)
+{
+    return (k & ~1) * T::slots + 2 * s + (k & 1);
+}
+template <int NF, class T>
+__host__ __device__ constexpr int tile_index_last(int k, int s)
+{
+    return ((NF & 1) && k == NF - 1) ? (NF - 1) * T::slots + s : tile_index<T>(k, s);
+}
+
 template <class F, int NF, class T>
 struct TAcc {
-    const F* sf;          // [NF][T::slots]
+    const F* sf;          // NF fields x T::slots, paired (tile_index_last)
     const uint8_t* sm;    // [T::slots]
     int slot;
     __device__ __forceinline__ uint8_t mask(int i) const { return sm[slot + T::off(i)]; }
     template <int K>
     __device__ __forceinline__ F get(int i) const
     {
-        return sf[K * T::slots + slot + T::off(i)];
+        return sf[tile_index_last<NF, T>(K, slot + T::off(i))];
     }
 };
 
@@ -462,11 +476,11 @@ __device__ __forceinline__ void stage_tile(const DevParams& P, const uint8_t* ma
             const int g = gx + P.nx * (gy + P.ny * gz);
             sm[s] = mask[g];
 #pragma unroll
-            for (int k = 0; k < NF; ++k) sf[k * T::slots + s] = src[k][g];
+            for (int k = 0; k < NF; ++k) sf[tile_index_last<NF, T>(k, s)] = src[k][g];
         } else {
             sm[s] = kWallSlot;
 #pragma unroll
-            for (int k = 0; k < NF; ++k) sf[k * T::slots + s] = (F)0;
+            for (int k = 0; k < NF; ++k) sf[tile_index_last<NF, T>(k, s)] = (F)0;
         }
     }
 }
@@ -1000,22 +1014,28 @@ __device__ __forceinline__ void collide_node(const DevParams& P, const DevPtrs& 
     using F = typename C::fld_t;
     using S = typename C::pop_t;
     const int n = x + P.nx * (y + P.ny * z);
-    if (D.mask[n]) return;
-    if (D.bflag[n] || near_wall(P, x, y, z)) {
-        collide_boundary<C>(P, D, x, y, z);
-        return;
-    }
-    // every source x - c_j is a fluid node: plain pull
     const PrmR<R>& Q = prm<R>(P);
     const size_t N = (size_t)P.N;
     const S* fs = (const S*)D.f_src;
     const F* force = (const F*)D.force;
     int nb[19];
     neighbours(P, x, y, z, nb);
+    // issue every load of the common case at once (one memory round trip);
+    // solid and boundary nodes drop them (a few percent of the nodes)
+    const uint8_t mk = D.mask[n], bf = D.bflag[n];
     const R Fx = (R)force[n], Fy = (R)force[N + n], Fz = (R)force[2 * N + n];
     R fl[19];
 #pragma unroll
-    for (int j = 0; j < 19; ++j) fl[j] = (R)PopStore<S>::load_dev(fs, (size_t)j * N + nb[opp(j)], j, Q.rho0);
+    for (int j = 0; j < 19; ++j) {
+        const int m = nb[opp(j)] >= 0 ? nb[opp(j)] : n;
+        fl[j] = (R)PopStore<S>::load_dev(fs, (size_t)j * N + m, j, Q.rho0);
+    }
+    if (mk) return;
+    if (bf || near_wall(P, x, y, z)) {
+        collide_boundary<C>(P, D, x, y, z);
+        return;
+    }
+    // every source x - c_j is a fluid node: plain pull
     collide_store<C>(Q, D, N, n, fl, Fx, Fy, Fz);
 }
 
@@ -1082,6 +1102,7 @@ __device__ __forceinline__ void scalars_compute(const DevParams& P, const DevPtr
     const R ps = (R)a.template get<0>(0) + dps, ph = (R)a.template get<1>(0) + dph;
     const R a0 = (R)a.template get<2>(0), b0 = (R)a.template get<3>(0);
     const R ux = (R)a.template get<4>(0), uy = (R)a.template get<5>(0), uz = (R)a.template get<6>(0);
+    const R ma0 = Q.Mpsi * a0, mb0 = Q.Mphi * b0;
     R sps = 0, sph = 0;
     bool solid_nb = false;
 #pragma unroll
@@ -1091,14 +1112,15 @@ __device__ __forceinline__ void scalars_compute(const DevParams& P, const DevPtr
         const R cu1 = cdot<R>(i, (R)a.template get<4>(i), (R)a.template get<5>(i), (R)a.template get<6>(i));
         const R ub = (R)0.5 * (cu0 + cu1);
         const R psm = (R)a.template get<0>(i) + dps, phm = (R)a.template get<1>(i) + dph;
-        const R aps = ub > (R)0 ? ub * ps : ub * psm;
-        const R aph = ub > (R)0 ? ub * ph : ub * phm;
-        const R w = wgt_r<R>(i);
+        // donor-cell upwind advection, diffusion M (mu(x + c) - mu(x))
+        const bool up = ub > (R)0;
+        const R tps = fma_x(Q.Mpsi, (R)a.template get<2>(i), -ma0) - ub * (up ? ps : psm);
+        const R tph = fma_x(Q.Mphi, (R)a.template get<3>(i), -mb0) - ub * (up ? ph : phm);
         // links to walls and particles carry no flux here (particle links are
         // handled below)
-        const R on = mk ? (R)0 : (R)1;
-        sps += on * (w * (Q.Mpsi * ((R)a.template get<2>(i) - a0) - aps));
-        sph += on * (w * (Q.Mphi * ((R)a.template get<3>(i) - b0) - aph));
+        const R w = wgt_r<R>(i);
+        sps = fma_x(w, mk ? (R)0 : tps, sps);
+        sph = fma_x(w, mk ? (R)0 : tph, sph);
         solid_nb = solid_nb || (mk != 0 && mk != kWallSlot);
     }
     R hn_src = 0;
