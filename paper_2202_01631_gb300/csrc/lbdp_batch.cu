@@ -146,13 +146,8 @@ struct Member {
     lb_handle* h;
     size_t off;        // arena offset of the box's region
     long long left;    // steps still to run (host mirror of the device count)
-    int np_seen;       // particles when the tables were last built
-};
-
-template <class T>
-struct DevArray {
-    T* p = nullptr;
-    size_t cap = 0;
+    int cur0;          // buffer the launch plans take as current at parity 0
+    int np_seen;       // particles when the plans were built
 };
 
 }  // namespace
@@ -166,25 +161,21 @@ struct lbb_batch {
     int sms = 0;
     char* base = nullptr;
     lb_arena* arena = nullptr;
-    int graph_steps = 16;
+    int graph_steps = 16;   // even
     std::vector<Member> mem;
     bool dirty = true;
-    BatchDev* d_hdr = nullptr;
-    BoxDev* d_boxes = nullptr;
-    int* d_cur = nullptr;
     long long* d_left = nullptr;
-    DevArray<NodeTile> d_node[kNodeTileSizes];
-    DevArray<PartTile> d_link, d_cover;
+    std::vector<LaunchPlan> plans;
+    int par = 0;            // parity of the steps run since the plans were built
     int cfg[4] = {0, 0, 0, 0};
-    int grid[4] = {0, 0, 0, 0};
-    int part_grid = 0;
-    cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};   // graphs starting at parity 0 / 1
     SideStream side{};   // particle kernels, overlapping the fluid kernels
 };
 
 namespace {
 
-constexpr int kStepLaunches = 8;   // 4 node kernels, 3 particle kernels, the buffer flip
+constexpr int kStepLaunches = 7;   // per launch plan: 4 node kernels, 3 particle kernels
+constexpr int kTilesPerBlock = 8;  // node tiles a block of a box takes
 
 int find_member(const lbb_batch* b, const lb_handle* h)
 {
@@ -195,136 +186,103 @@ int find_member(const lbb_batch* b, const lb_handle* h)
 
 void drop_graph(lbb_batch* b)
 {
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    b->exec = nullptr;
-}
-
-int set_grids(lbb_batch* b)
-{
-    for (int k = 0; k < 4; ++k) {
-        int bps = 0;
-        LB_TRY(b->bops->node_grid(k, b->cfg[k], &bps));
-        b->grid[k] = b->sms * std::max(bps, 1);
+    for (auto& g : b->exec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
     }
-    b->part_grid = 2 * b->sms;
-    drop_graph(b);
-    return LB_OK;
 }
 
-template <class T>
-cudaError_t ensure(lbb_batch* b, DevArray<T>& a, size_t n)
-{
-    if (n <= a.cap) return cudaSuccess;
-    size_t cap = std::max<size_t>(n, 2 * a.cap);
-    cudaError_t e = cudaStreamSynchronize(b->stream);   // kernels may still read the old array
-    if (e != cudaSuccess) return e;
-    if (a.p) cudaFree(a.p);
-    a.p = nullptr;
-    a.cap = 0;
-    e = cudaMalloc((void**)&a.p, cap * sizeof(T));
-    if (e == cudaSuccess) a.cap = cap;
-    return e;
-}
-
-// Rebuild the device tables from the member list (boxes, tiles, header).
-int rebuild(lbb_batch* b)
+// Build the launch plans from the member list: up to kLaunchBoxes boxes per
+// launch, each box's pointer sets taken from its current buffer.
+void rebuild(lbb_batch* b)
 {
     const int nb = (int)b->mem.size();
-    std::vector<BoxDev> boxes(nb);
-    std::vector<NodeTile> nt[kNodeTileSizes];
-    std::vector<PartTile> lt, ct;
-    for (int i = 0; i < nb; ++i) {
-        lb_handle* h = b->mem[i].h;
-        BoxDev& bd = boxes[i];
-        bd.P = h->dp;
-        bd.D[0] = handle_ptrs(h, 0);
-        bd.D[1] = handle_ptrs(h, 1);
-        bd.mx = div_magic((unsigned)h->dp.nx);
-        bd.my = div_magic((unsigned)h->dp.ny);
-        const int N = (int)h->dp.N;
-        for (int k = 0; k < kNodeTileSizes; ++k)
-            for (int s = 0; s < N; s += 128 << k) nt[k].push_back({i, s});
-        for (int p = 0; p < h->dp.np; ++p) {
-            for (int j = 0; j < h->dp.nb1; ++j) lt.push_back({i, p, j, h->dp.nb1});
-            for (int j = 0; j < h->dp.nb2; ++j) ct.push_back({i, p, j, h->dp.nb2});
+    b->plans.assign((nb + kLaunchBoxes - 1) / kLaunchBoxes, LaunchPlan());
+    for (size_t l = 0; l < b->plans.size(); ++l) {
+        LaunchPlan& pl = b->plans[l];
+        memset(&pl.L, 0, sizeof(pl.L));
+        pl.L.left = b->d_left;
+        pl.L.base = (int)l * kLaunchBoxes;
+        pl.L.nbox = std::min(kLaunchBoxes, nb - pl.L.base);
+        int gmax[kNodeTileSizes] = {1, 1};
+        int lmax = 1, cmax = 1;
+        for (int j = 0; j < pl.L.nbox; ++j) {
+            Member& m = b->mem[pl.L.base + j];
+            lb_handle* h = m.h;
+            BoxDev& bd = pl.L.box[j];
+            m.cur0 = h->cur;
+            m.np_seen = h->dp.np;
+            bd.P = h->dp;
+            bd.D[0] = handle_ptrs(h, m.cur0);
+            bd.D[1] = handle_ptrs(h, m.cur0 ^ 1);
+            bd.mx = div_magic((unsigned)h->dp.nx);
+            bd.my = div_magic((unsigned)h->dp.ny);
+            for (int k = 0; k < kNodeTileSizes; ++k) {
+                const long long tiles = (h->dp.N + (128 << k) - 1) / (128 << k);
+                const int g = (int)std::max<long long>(1, (tiles + kTilesPerBlock - 1) / kTilesPerBlock);
+                pl.L.gx[k][j] = g;
+                gmax[k] = std::max(gmax[k], g);
+            }
+            lmax = std::max(lmax, h->dp.np * h->dp.nb1);
+            cmax = std::max(cmax, h->dp.np * h->dp.nb2);
         }
-        b->mem[i].np_seen = h->dp.np;
+        for (int k = 0; k < kNodeTileSizes; ++k) pl.node[k] = dim3(gmax[k], pl.L.nbox);
+        pl.link = dim3(lmax, pl.L.nbox);
+        pl.cover = dim3(cmax, pl.L.nbox);
     }
-    BatchDev hdr;
-    memset(&hdr, 0, sizeof(hdr));
-    for (int k = 0; k < kNodeTileSizes; ++k) {
-        LB_TRY(ensure(b, b->d_node[k], std::max<size_t>(nt[k].size(), 1)));
-        hdr.node[k] = b->d_node[k].p;
-        hdr.n_node[k] = (int)nt[k].size();
-    }
-    LB_TRY(ensure(b, b->d_link, std::max<size_t>(lt.size(), 1)));
-    LB_TRY(ensure(b, b->d_cover, std::max<size_t>(ct.size(), 1)));
-    hdr.boxes = b->d_boxes;
-    hdr.cur = b->d_cur;
-    hdr.left = b->d_left;
-    hdr.nbox = nb;
-    hdr.link = b->d_link.p;
-    hdr.n_link = (int)lt.size();
-    hdr.cover = b->d_cover.p;
-    hdr.n_cover = (int)ct.size();
-    cudaStream_t s = b->stream;
-    // pageable sources: each copy has read its source when the call returns
-    if (nb) LB_TRY(cudaMemcpyAsync(b->d_boxes, boxes.data(), nb * sizeof(BoxDev), cudaMemcpyHostToDevice, s));
-    for (int k = 0; k < kNodeTileSizes; ++k)
-        if (!nt[k].empty())
-            LB_TRY(cudaMemcpyAsync(b->d_node[k].p, nt[k].data(), nt[k].size() * sizeof(NodeTile),
-                                   cudaMemcpyHostToDevice, s));
-    if (!lt.empty())
-        LB_TRY(cudaMemcpyAsync(b->d_link.p, lt.data(), lt.size() * sizeof(PartTile), cudaMemcpyHostToDevice, s));
-    if (!ct.empty())
-        LB_TRY(cudaMemcpyAsync(b->d_cover.p, ct.data(), ct.size() * sizeof(PartTile), cudaMemcpyHostToDevice, s));
-    LB_TRY(cudaMemcpyAsync(b->d_hdr, &hdr, sizeof(hdr), cudaMemcpyHostToDevice, s));
+    b->par = 0;
     b->dirty = false;
-    return LB_OK;
+    drop_graph(b);
 }
 
-bool tables_stale(const lbb_batch* b)
+// The plans still describe the batch: same boxes and particles, and every box
+// with steps left has run the same steps since they were built.
+bool plans_stale(const lbb_batch* b)
 {
     if (b->dirty) return true;
-    for (const Member& m : b->mem)
+    for (const Member& m : b->mem) {
         if (m.np_seen != m.h->dp.np) return true;
+        if (m.left > 0 && m.h->cur != (m.cur0 ^ b->par)) return true;
+    }
     return false;
 }
 
-// Upload each box's current buffer and steps to run (all_one: 1 for every
-// box, used while tuning).
+// Upload the steps each box still has to run (all_one: 1 for every box, used
+// while tuning).
 int upload_counts(lbb_batch* b, bool all_one)
 {
     const int nb = (int)b->mem.size();
     if (nb == 0) return LB_OK;
-    std::vector<int> cur(nb);
     std::vector<long long> left(nb);
-    for (int i = 0; i < nb; ++i) {
-        cur[i] = b->mem[i].h->cur;
-        left[i] = all_one ? 1 : b->mem[i].left;
-    }
-    LB_TRY(cudaMemcpyAsync(b->d_cur, cur.data(), nb * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    for (int i = 0; i < nb; ++i) left[i] = all_one ? 1 : b->mem[i].left;
     LB_TRY(cudaMemcpyAsync(b->d_left, left.data(), nb * sizeof(long long), cudaMemcpyHostToDevice, b->stream));
     return LB_OK;
 }
 
-int capture_graph(lbb_batch* b)
+int step(lbb_batch* b, int par)
 {
-    if (b->exec) return LB_OK;
+    return cuda_status(b->bops->step(b->cfg, b->plans.data(), (int)b->plans.size(), par, b->d_left,
+                                     (int)b->mem.size(), b->stream, &b->side));
+}
+
+// graph_steps steps starting at parity p0 (graph_steps is even, so a launch
+// of it leaves the parity unchanged)
+int capture_graph(lbb_batch* b, int p0)
+{
+    if (b->exec[p0]) return LB_OK;
     cudaGraph_t g = nullptr;
     LB_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    for (int t = 0; t < b->graph_steps && e == cudaSuccess; ++t)
-        e = b->bops->step(b->cfg, b->grid, b->part_grid, b->d_hdr, b->stream, &b->side);
+    int st = LB_OK;
+    for (int t = 0; t < b->graph_steps && st == LB_OK; ++t) st = step(b, (p0 + t) & 1);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (st == LB_OK) st = cuda_status(e2);
+    if (st == LB_OK) st = cuda_status(cudaGraphInstantiate(&b->exec[p0], g, 0));
     if (g) cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-        b->exec = nullptr;
+    if (st != LB_OK) {
+        b->exec[p0] = nullptr;
         cudaGetLastError();
     }
-    return cuda_status(e);
+    return st;
 }
 
 }  // namespace
@@ -354,6 +312,7 @@ int lbb_create(const lbb_params* p, lbb_batch** out)
     b->precision = p->precision;
     b->bops = batch_ops_for(p->precision);
     b->graph_steps = p->graph_steps > 0 ? p->graph_steps : 16;
+    b->graph_steps += b->graph_steps & 1;   // even: parity returns after a graph
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) {
@@ -381,18 +340,10 @@ int lbb_create(const lbb_params* p, lbb_batch** out)
     cap = cap / kGranule * kGranule;
     if (e == cudaSuccess && lb_arena_create(cap, &b->arena) != LB_OK) e = cudaErrorInvalidValue;
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->base, cap);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_hdr, sizeof(BatchDev));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_boxes, kBatchMaxBoxes * sizeof(BoxDev));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_cur, kBatchMaxBoxes * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_left, kBatchMaxBoxes * sizeof(long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_left, 0, kBatchMaxBoxes * sizeof(long long), b->stream);
     if (e == cudaSuccess) e = b->bops->prepare();
     int st = cuda_status(e);
-    if (st == LB_OK) {
-        // default launch shape: 128 threads, one node per thread
-        st = set_grids(b);
-    }
-    if (st == LB_OK) st = rebuild(b);
     if (st == LB_OK) st = cuda_status(cudaStreamSynchronize(b->stream));
     if (st != LB_OK) {
         cudaGetLastError();
@@ -411,13 +362,6 @@ void lbb_destroy(lbb_batch* b)
     std::vector<Member> ms = b->mem;
     for (const Member& m : ms) lb_destroy(m.h);
     drop_graph(b);
-    for (auto& a : b->d_node)
-        if (a.p) cudaFree(a.p);
-    if (b->d_link.p) cudaFree(b->d_link.p);
-    if (b->d_cover.p) cudaFree(b->d_cover.p);
-    if (b->d_hdr) cudaFree(b->d_hdr);
-    if (b->d_boxes) cudaFree(b->d_boxes);
-    if (b->d_cur) cudaFree(b->d_cur);
     if (b->d_left) cudaFree(b->d_left);
     if (b->base) cudaFree(b->base);
     if (b->arena) lb_arena_destroy(b->arena);
@@ -478,7 +422,7 @@ int lbb_add_box(lbb_batch* b, const lb_params* p, lb_handle** out)
         lb_arena_free(b->arena, off);
         return st;
     }
-    b->mem.push_back({h, off, 0, 0});
+    b->mem.push_back({h, off, 0, 0, 0});
     b->dirty = true;
     *out = h;
     return LB_OK;
@@ -513,26 +457,24 @@ int lbb_run(lbb_batch* b, int nsteps, long long* launches)
     for (const Member& m : b->mem) most = std::max(most, m.left);
     const int n = (int)std::min<long long>(nsteps, most);
     if (n == 0) return LB_OK;
-    if (tables_stale(b)) {
-        const int st = rebuild(b);
-        if (st != LB_OK) return st;
-    }
+    if (plans_stale(b)) rebuild(b);
     int st = upload_counts(b, false);
     if (st != LB_OK) return st;
     const int full = n / b->graph_steps, rest = n % b->graph_steps;
     if (full > 0) {
-        st = capture_graph(b);
+        st = capture_graph(b, b->par);
         if (st != LB_OK) return st;
-        for (int k = 0; k < full; ++k) LB_TRY(cudaGraphLaunch(b->exec, b->stream));
+        for (int k = 0; k < full; ++k) LB_TRY(cudaGraphLaunch(b->exec[b->par], b->stream));
     }
-    for (int k = 0; k < rest; ++k)
-        LB_TRY(b->bops->step(b->cfg, b->grid, b->part_grid, b->d_hdr, b->stream, &b->side));
+    for (int k = 0; k < rest && st == LB_OK; ++k) st = step(b, (b->par + k) & 1);
+    if (st != LB_OK) return st;
+    b->par = (b->par + n) & 1;
     for (Member& m : b->mem) {
         const long long ran = std::min<long long>(m.left, n);
         m.left -= ran;
         m.h->cur ^= (int)(ran & 1);
     }
-    if (launches) *launches = (long long)n * kStepLaunches;
+    if (launches) *launches = (long long)n * ((long long)b->plans.size() * kStepLaunches + 1);
     return LB_OK;
 }
 
@@ -554,7 +496,8 @@ int lbb_set_config(lbb_batch* b, const int cfg[4])
         if (cfg[k] < 0 || cfg[k] >= kNumBatchCfgs) return LB_ERR_PARAM;
     cudaSetDevice(b->device);
     for (int k = 0; k < 4; ++k) b->cfg[k] = cfg[k];
-    return set_grids(b);
+    drop_graph(b);
+    return LB_OK;
 }
 
 int lbb_tune(lbb_batch* b, int reps, int cfg_out[4], double ms_out[4])
@@ -563,10 +506,7 @@ int lbb_tune(lbb_batch* b, int reps, int cfg_out[4], double ms_out[4])
     if (b->mem.empty()) return LB_ERR_STATE;
     cudaSetDevice(b->device);
     cudaStream_t s = b->stream;
-    if (tables_stale(b)) {
-        const int st = rebuild(b);
-        if (st != LB_OK) return st;
-    }
+    if (plans_stale(b)) rebuild(b);
     // collide-stream rewrites the stored velocity: keep a copy in staging
     for (const Member& m : b->mem) {
         const size_t ub = 3 * (size_t)m.h->dp.N * m.h->ops->fld_bytes;
@@ -581,12 +521,17 @@ int lbb_tune(lbb_batch* b, int reps, int cfg_out[4], double ms_out[4])
     for (int nc = 0; nc < 4 && st == LB_OK; ++nc) {
         best_ms[nc] = 1e300;
         for (int k = 0; k < kNumBatchCfgs && st == LB_OK; ++k) {
-            int bps = 0;
-            st = cuda_status(b->bops->node_grid(nc, k, &bps));
-            const int grid = b->sms * std::max(bps, 1);
-            for (int w = 0; w < 2 && st == LB_OK; ++w) st = cuda_status(b->bops->node(nc, k, grid, b->d_hdr, s));
+            auto all = [&]() {
+                for (LaunchPlan& pl : b->plans) {
+                    pl.L.par = b->par;
+                    const int e = cuda_status(b->bops->node(nc, k, &pl, s));
+                    if (e != LB_OK) return e;
+                }
+                return (int)LB_OK;
+            };
+            for (int w = 0; w < 2 && st == LB_OK; ++w) st = all();
             if (st == LB_OK) st = cuda_status(cudaEventRecord(e0, s));
-            for (int r = 0; r < reps && st == LB_OK; ++r) st = cuda_status(b->bops->node(nc, k, grid, b->d_hdr, s));
+            for (int r = 0; r < reps && st == LB_OK; ++r) st = all();
             if (st == LB_OK) st = cuda_status(cudaEventRecord(e1, s));
             if (st == LB_OK) st = cuda_status(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -612,7 +557,8 @@ int lbb_tune(lbb_batch* b, int reps, int cfg_out[4], double ms_out[4])
         if (cfg_out) cfg_out[k] = best[k];
         if (ms_out) ms_out[k] = best_ms[k];
     }
-    return set_grids(b);
+    drop_graph(b);
+    return LB_OK;
 }
 
 int lbb_sync(lbb_batch* b)

@@ -54,8 +54,8 @@ struct PrecOps {
 
 // One batched step over the boxes of a batch (see lbdp_batch_kernels.cuh):
 // node kernels in launch configuration cfg[class], particle kernels with the
-// single-box split, then the buffer flip of every box that ran.
-struct BatchDev;
+// single-box split, then the step count of every box that ran.
+struct BoxLaunch;
 constexpr int kNumBatchCfgs = 4;   // node kernel configurations
 struct BatchCfg {
     int threads, cells, tile_index;   // tile = threads * cells = 128 << tile_index nodes
@@ -63,15 +63,18 @@ struct BatchCfg {
 };
 extern const BatchCfg kBatchCfgs[kNumBatchCfgs];
 
+// A launch of up to kLaunchBoxes boxes: its parameter block and its grids.
+struct LaunchPlan;
+
 struct BatchOps {
     // per-device kernel attributes (call once before the first launch or capture)
     cudaError_t (*prepare)();
-    // grid: resident blocks per SM * SMs for a node kernel of class nc in cfg
-    cudaError_t (*node_grid)(int nc, int cfg, int* blocks_per_sm);
-    cudaError_t (*node)(int nc, int cfg, int grid, const BatchDev* B, cudaStream_t s);
-    // the whole step: node kernels in cfg[4], particle kernels on part_grid blocks
-    cudaError_t (*step)(const int cfg[4], const int grid[4], int part_grid, const BatchDev* B, cudaStream_t s,
-                        const SideStream* side);
+    // node kernel of class nc in configuration cfg over one launch's boxes
+    cudaError_t (*node)(int nc, int cfg, const LaunchPlan* L, cudaStream_t s);
+    // the whole step at parity par over launches L[0..nl-1], then the count-down
+    // of left[0..nbox-1]
+    cudaError_t (*step)(const int cfg[4], LaunchPlan* L, int nl, int par, long long* left, int nbox,
+                        cudaStream_t s, const SideStream* side);
 };
 
 extern const PrecOps kOpsF64;

@@ -146,7 +146,7 @@ struct Ops {
 // Launchers of the batched kernels of one precision configuration.
 template <class C>
 struct BOps {
-    using KFn = void (*)(const BatchDev*);
+    using KFn = void (*)(BoxLaunch);
 
     template <int NC>
     static KFn node_fn(int cfg)
@@ -183,47 +183,46 @@ struct BOps {
         return e;
     }
 
-    static cudaError_t node_grid(int nc, int cfg, int* blocks_per_sm)
+    static cudaError_t node(int nc, int cfg, const LaunchPlan* L, cudaStream_t s)
     {
         if (nc < 0 || nc >= kNumNodeClasses || cfg < 0 || cfg >= kNumBatchCfgs) return cudaErrorInvalidValue;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn(nc, cfg), kBatchCfgs[cfg].threads, 0);
+        void* args[] = {(void*)&L->L};
+        return cudaLaunchKernel((const void*)fn(nc, cfg), L->node[kBatchCfgs[cfg].tile_index],
+                                dim3(kBatchCfgs[cfg].threads), args, 0, s);
     }
 
-    static cudaError_t node(int nc, int cfg, int grid, const BatchDev* B, cudaStream_t s)
-    {
-        if (nc < 0 || nc >= kNumNodeClasses || cfg < 0 || cfg >= kNumBatchCfgs) return cudaErrorInvalidValue;
-        void* args[] = {(void*)&B};
-        return cudaLaunchKernel((const void*)fn(nc, cfg), dim3(grid), dim3(kBatchCfgs[cfg].threads), args, 0, s);
-    }
-
-    static cudaError_t step(const int cfg[4], const int grid[4], int part_grid, const BatchDev* B, cudaStream_t s,
-                            const SideStream* side)
+    static cudaError_t step(const int cfg[4], LaunchPlan* Ls, int nl, int par, long long* left, int nbox,
+                            cudaStream_t s, const SideStream* side)
     {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
         const size_t lsm = block_sum_t_bytes<kLinkK>(kPartThreads);
-        if ((e = node(kNcMup, cfg[0], grid[0], B, s)) != cudaSuccess) return e;
-        if (side) {
-            cudaEventRecord(side->fork, s);
-            cudaStreamWaitEvent(side->s, side->fork, 0);
-            kb_links<C><<<part_grid, kPartThreads, lsm, side->s>>>(B);
-            cudaEventRecord(side->links_done, side->s);
-            kb_cover_mark<C><<<part_grid, kPartThreads, 0, side->s>>>(B);
-            cudaEventRecord(side->mark_done, side->s);
-            if ((e = node(kNcFdiv, cfg[1], grid[1], B, s)) != cudaSuccess) return e;
-            cudaStreamWaitEvent(s, side->links_done, 0);
-            if ((e = node(kNcCollide, cfg[2], grid[2], B, s)) != cudaSuccess) return e;
-            if ((e = node(kNcScalars, cfg[3], grid[3], B, s)) != cudaSuccess) return e;
-            cudaStreamWaitEvent(s, side->mark_done, 0);
-        } else {
-            if ((e = node(kNcFdiv, cfg[1], grid[1], B, s)) != cudaSuccess) return e;
-            kb_links<C><<<part_grid, kPartThreads, lsm, s>>>(B);
-            if ((e = node(kNcCollide, cfg[2], grid[2], B, s)) != cudaSuccess) return e;
-            if ((e = node(kNcScalars, cfg[3], grid[3], B, s)) != cudaSuccess) return e;
-            kb_cover_mark<C><<<part_grid, kPartThreads, 0, s>>>(B);
+        for (int l = 0; l < nl; ++l) {
+            LaunchPlan* L = Ls + l;
+            L->L.par = par;   // copied into each launch's parameters at the call
+            if ((e = node(kNcMup, cfg[0], L, s)) != cudaSuccess) return e;
+            if (side) {
+                cudaEventRecord(side->fork, s);
+                cudaStreamWaitEvent(side->s, side->fork, 0);
+                kb_links<C><<<L->link, kPartThreads, lsm, side->s>>>(L->L);
+                cudaEventRecord(side->links_done, side->s);
+                kb_cover_mark<C><<<L->cover, kPartThreads, 0, side->s>>>(L->L);
+                cudaEventRecord(side->mark_done, side->s);
+                if ((e = node(kNcFdiv, cfg[1], L, s)) != cudaSuccess) return e;
+                cudaStreamWaitEvent(s, side->links_done, 0);
+                if ((e = node(kNcCollide, cfg[2], L, s)) != cudaSuccess) return e;
+                if ((e = node(kNcScalars, cfg[3], L, s)) != cudaSuccess) return e;
+                cudaStreamWaitEvent(s, side->mark_done, 0);
+            } else {
+                if ((e = node(kNcFdiv, cfg[1], L, s)) != cudaSuccess) return e;
+                kb_links<C><<<L->link, kPartThreads, lsm, s>>>(L->L);
+                if ((e = node(kNcCollide, cfg[2], L, s)) != cudaSuccess) return e;
+                if ((e = node(kNcScalars, cfg[3], L, s)) != cudaSuccess) return e;
+                kb_cover_mark<C><<<L->cover, kPartThreads, 0, s>>>(L->L);
+            }
+            kb_cover_apply<C><<<L->cover, kPartThreads, 0, s>>>(L->L);
         }
-        kb_cover_apply<C><<<part_grid, kPartThreads, 0, s>>>(B);
-        kb_advance<<<(kBatchMaxBoxes + 255) / 256, 256, 0, s>>>(B);
+        kb_advance<<<(nbox + 255) / 256, 256, 0, s>>>(left, nbox);
         return cudaGetLastError();
     }
 
@@ -231,7 +230,6 @@ struct BOps {
     {
         BatchOps t;
         t.prepare = &prepare;
-        t.node_grid = &node_grid;
         t.node = &node;
         t.step = &step;
         return t;
