@@ -98,12 +98,15 @@ int lbb_run(lbb_batch* b, int nsteps, long long* launches);
  * candidate per kernel; ms_out[4] (optional): its time per launch.  Results do
  * not depend on the configuration. */
 int lbb_tune(lbb_batch* b, int reps, int cfg_out[4], double ms_out[4]);
-/* Set the candidates directly (cfg[k] in [0, lbb_num_configs())). */
+/* Set the candidates directly (cfg[k] in [0, lbb_num_configs()); candidate
+ * 4 -- 32 x 4 x 4 tiles staged in shared memory -- exists for the force and
+ * transport kernels (k = 1, 3) only). */
 int lbb_set_config(lbb_batch* b, const int cfg[4]);
 int lbb_num_configs(void);
 /* Candidate k: threads per block, cells (nodes) per thread, and the register
  * budget (0: the single-box kernels' budget; 1: a larger one that avoids
- * spills at lower occupancy). */
+ * spills at lower occupancy).  Candidate 4 is the shared-memory tile (two
+ * nodes per thread). */
 int lbb_config_shape(int k, int* threads, int* cells, int* regs);
 
 /* Wait for the batch stream; report a device error of any member box. */

@@ -22,7 +22,8 @@
 using namespace lbdp;
 
 namespace lbdp {
-const BatchCfg kBatchCfgs[kNumBatchCfgs] = {{128, 1, 0, 0}, {128, 1, 0, 1}, {256, 1, 1, 1}, {128, 2, 1, 1}};
+const BatchCfg kBatchCfgs[kNumBatchCfgs] = {
+    {128, 1, 0, 0}, {128, 1, 0, 1}, {256, 1, 1, 1}, {128, 2, 1, 1}, {256, 2, -1, 1}};
 }  // namespace lbdp
 
 // ---------------------------------------------------------------------------
@@ -177,6 +178,12 @@ namespace {
 constexpr int kStepLaunches = 7;   // per launch plan: 4 node kernels, 3 particle kernels
 constexpr int kTilesPerBlock = 8;  // node tiles a block of a box takes
 
+// Candidate 4 (shared-memory tiles) exists for the force and transport kernels.
+bool cfg_valid(int nc, int cfg)
+{
+    return cfg >= 0 && cfg < kNumBatchCfgs && (cfg < 4 || nc == 1 || nc == 3);
+}
+
 int find_member(const lbb_batch* b, const lb_handle* h)
 {
     for (size_t i = 0; i < b->mem.size(); ++i)
@@ -205,7 +212,7 @@ void rebuild(lbb_batch* b)
         pl.L.base = (int)l * kLaunchBoxes;
         pl.L.nbox = std::min(kLaunchBoxes, nb - pl.L.base);
         int gmax[kNodeTileSizes] = {1, 1};
-        int lmax = 1, cmax = 1;
+        int tmax = 1, lmax = 1, cmax = 1;
         for (int j = 0; j < pl.L.nbox; ++j) {
             Member& m = b->mem[pl.L.base + j];
             lb_handle* h = m.h;
@@ -223,10 +230,14 @@ void rebuild(lbb_batch* b)
                 pl.L.gx[k][j] = g;
                 gmax[k] = std::max(gmax[k], g);
             }
+            const long long t3 = (long long)((h->dp.nx + 31) / 32) * ((h->dp.ny + 3) / 4) * ((h->dp.nz + 3) / 4);
+            pl.L.gt[j] = (int)std::max<long long>(1, (t3 + 1) / 2);   // two tiles per block
+            tmax = std::max(tmax, pl.L.gt[j]);
             lmax = std::max(lmax, h->dp.np * h->dp.nb1);
             cmax = std::max(cmax, h->dp.np * h->dp.nb2);
         }
         for (int k = 0; k < kNodeTileSizes; ++k) pl.node[k] = dim3(gmax[k], pl.L.nbox);
+        pl.tiles = dim3(tmax, pl.L.nbox);
         pl.link = dim3(lmax, pl.L.nbox);
         pl.cover = dim3(cmax, pl.L.nbox);
     }
@@ -493,7 +504,7 @@ int lbb_set_config(lbb_batch* b, const int cfg[4])
 {
     if (!b || !cfg) return LB_ERR_PARAM;
     for (int k = 0; k < 4; ++k)
-        if (cfg[k] < 0 || cfg[k] >= kNumBatchCfgs) return LB_ERR_PARAM;
+        if (!cfg_valid(k, cfg[k])) return LB_ERR_PARAM;
     cudaSetDevice(b->device);
     for (int k = 0; k < 4; ++k) b->cfg[k] = cfg[k];
     drop_graph(b);
@@ -521,6 +532,7 @@ int lbb_tune(lbb_batch* b, int reps, int cfg_out[4], double ms_out[4])
     for (int nc = 0; nc < 4 && st == LB_OK; ++nc) {
         best_ms[nc] = 1e300;
         for (int k = 0; k < kNumBatchCfgs && st == LB_OK; ++k) {
+            if (!cfg_valid(nc, k)) continue;
             auto all = [&]() {
                 for (LaunchPlan& pl : b->plans) {
                     pl.L.par = b->par;

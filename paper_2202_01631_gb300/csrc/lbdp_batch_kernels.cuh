@@ -44,6 +44,7 @@ struct BoxLaunch {
     int base, nbox;
     int par;                               // step parity: D[par] is current
     int gx[kNodeTileSizes][kLaunchBoxes];  // node blocks of each box per tile size
+    int gt[kLaunchBoxes];                  // blocks of each box for the 32x4x4 tiles
     BoxDev box[kLaunchBoxes];
 };
 static_assert(sizeof(BoxLaunch) <= 32000, "kernel parameter block");
@@ -53,6 +54,7 @@ static_assert(sizeof(BoxLaunch) <= 32000, "kernel parameter block");
 struct LaunchPlan {
     BoxLaunch L;
     dim3 node[kNodeTileSizes];
+    dim3 tiles;
     dim3 link, cover;
 };
 
@@ -99,6 +101,53 @@ __global__ void __launch_bounds__(T, (NodeBounds<NC, T, RB>::min_blocks))
                 node_body<C, NC>(P, D, x, y, z);
             }
         }
+    }
+}
+
+// Force and transport with the single-box shared-memory tiles: the blocks of
+// box b loop over its 32 x 4 x 4 tiles.
+template <class C, int NC>
+__global__ void __launch_bounds__(kTileThreads) kb_tiled(const __grid_constant__ BoxLaunch L)
+{
+    using F = typename C::fld_t;
+    constexpr int NF = NC == kNcFdiv ? 6 : 7;
+    extern __shared__ __align__(16) unsigned char smem_raw[];   // tile_smem<F, NF>()
+    F* sf = (F*)smem_raw;
+    uint8_t* sm = (uint8_t*)(sf + NF * Tile::slots);
+    const int b = blockIdx.y;
+    if (b >= L.nbox) return;
+    const int g = L.gt[b];
+    if ((int)blockIdx.x >= g || L.left[L.base + b] <= 0) return;
+    const DevParams& P = L.box[b].P;
+    const DevPtrs& D = L.box[b].D[L.par];
+    const size_t N = (size_t)P.N;
+    const int ntx = (P.nx + 31) >> 5, nty = (P.ny + 3) >> 2, ntz = (P.nz + 3) >> 2;
+    const F* pt = (const F*)D.pt;
+    const F* u = (const F*)D.u;
+    const F* src[NF];
+    if (NC == kNcFdiv) {
+#pragma unroll
+        for (int k = 0; k < NF; ++k) src[k] = pt + k * N;
+    } else {
+        src[0] = (const F*)D.psi_src;
+        src[1] = (const F*)D.phi_src;
+        src[2] = (const F*)D.mupsi;
+        src[3] = (const F*)D.muphi;
+#pragma unroll
+        for (int k = 4; k < NF; ++k) src[k] = u + (k - 4) * N;
+    }
+    for (int t = blockIdx.x; t < ntx * nty * ntz; t += g) {
+        const int x0 = (t % ntx) * 32, y0 = ((t / ntx) % nty) * 4, z0 = (t / (ntx * nty)) * 4;
+        __syncthreads();   // every node of the previous tile is done with sf, sm
+        stage_tile<F, NF, Tile>(P, D.mask, src, x0, y0, z0, sf, sm);
+        __syncthreads();
+        tile_nodes(P, sm, x0, y0, z0, [&](int x, int y, int z, int n, int slot) {
+            const TAcc<F, NF, Tile> a{sf, sm, slot};
+            if (NC == kNcFdiv)
+                fdiv_compute<C>(P, D, n, a);
+            else
+                scalars_compute<C>(P, D, x, y, z, n, a);
+        });
     }
 }
 

@@ -56,9 +56,10 @@ struct PrecOps {
 // node kernels in launch configuration cfg[class], particle kernels with the
 // single-box split, then the step count of every box that ran.
 struct BoxLaunch;
-constexpr int kNumBatchCfgs = 4;   // node kernel configurations
+constexpr int kNumBatchCfgs = 5;   // node kernel configurations (4: shared-memory tiles,
+                                   // force and transport only)
 struct BatchCfg {
-    int threads, cells, tile_index;   // tile = threads * cells = 128 << tile_index nodes
+    int threads, cells, tile_index;   // tile = threads * cells = 128 << tile_index nodes (-1: 32x4x4)
     int regs;                         // register budget: 0 tight, 1 loose
 };
 extern const BatchCfg kBatchCfgs[kNumBatchCfgs];

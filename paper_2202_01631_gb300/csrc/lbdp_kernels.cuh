@@ -1398,15 +1398,16 @@ constexpr int kTileThreads = 256;
 template <class F, int NF>
 __host__ __device__ constexpr size_t tile_smem() { return (size_t)NF * Tile::slots * sizeof(F) + Tile::slots; }
 
-// The two nodes of this thread: (tx, ty, tz0) and (tx, ty, tz0 + 2).
+// The two nodes of this thread in the tile at (x0, y0, z0): (tx, ty, tz0)
+// and (tx, ty, tz0 + 2).
 template <class Body>
-__device__ __forceinline__ void tile_nodes(const DevParams& P, const uint8_t* sm, Body body)
+__device__ __forceinline__ void tile_nodes(const DevParams& P, const uint8_t* sm, int x0, int y0, int z0, Body body)
 {
     const int tx = threadIdx.x & 31, ty = (threadIdx.x >> 5) & 3, tz0 = threadIdx.x >> 7;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int tz = tz0 + 2 * h;
-        const int x = blockIdx.x * 32 + tx, y = blockIdx.y * 4 + ty, z = blockIdx.z * 4 + tz;
+        const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
         if (x >= P.nx || y >= P.ny || z >= P.nz) continue;
         const int slot = (tx + 1) + Tile::HX * ((ty + 1) + Tile::HY * (tz + 1));
         if (sm[slot]) continue;   // node inside a particle
@@ -1426,7 +1427,7 @@ __global__ void __launch_bounds__(kTileThreads) kt_fdiv(DevParams P, DevPtrs D)
     const F* const src[6] = {pt, pt + N, pt + 2 * N, pt + 3 * N, pt + 4 * N, pt + 5 * N};
     stage_tile<F, 6, Tile>(P, D.mask, src, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, sf, sm);
     __syncthreads();
-    tile_nodes(P, sm, [&](int, int, int, int n, int slot) {
+    tile_nodes(P, sm, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, [&](int, int, int, int n, int slot) {
         const TAcc<F, 6, Tile> a{sf, sm, slot};
         fdiv_compute<C>(P, D, n, a);
     });
@@ -1446,7 +1447,7 @@ __global__ void __launch_bounds__(kTileThreads) kt_scalars(const __grid_constant
                              u, u + N, u + 2 * N};
     stage_tile<F, 7, Tile>(P, D.mask, src, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, sf, sm);
     __syncthreads();
-    tile_nodes(P, sm, [&](int x, int y, int z, int n, int slot) {
+    tile_nodes(P, sm, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, [&](int x, int y, int z, int n, int slot) {
         const TAcc<F, 7, Tile> a{sf, sm, slot};
         scalars_compute<C>(P, D, x, y, z, n, a);
     });

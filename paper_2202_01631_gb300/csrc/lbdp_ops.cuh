@@ -151,7 +151,7 @@ struct BOps {
     template <int NC>
     static KFn node_fn(int cfg)
     {
-        static_assert(kNumBatchCfgs == 4, "configuration table");
+        static_assert(kNumBatchCfgs == 5, "configuration table");
         switch (cfg) {
             case 0: return kb_node<C, NC, 128, 1, 0, 0>;
             case 1: return kb_node<C, NC, 128, 1, 0, 1>;
@@ -179,6 +179,12 @@ struct BOps {
         if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
         e = cudaFuncSetAttribute(kb_links<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)block_sum_t_bytes<kLinkK>(kPartThreads));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kb_tiled<C, kNcFdiv>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tile_smem<typename C::fld_t, 6>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kb_tiled<C, kNcScalars>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tile_smem<typename C::fld_t, 7>());
         if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
         return e;
     }
@@ -187,6 +193,15 @@ struct BOps {
     {
         if (nc < 0 || nc >= kNumNodeClasses || cfg < 0 || cfg >= kNumBatchCfgs) return cudaErrorInvalidValue;
         void* args[] = {(void*)&L->L};
+        if (cfg == 4) {
+            if (nc == kNcFdiv)
+                return cudaLaunchKernel((const void*)kb_tiled<C, kNcFdiv>, L->tiles, dim3(kTileThreads), args,
+                                        tile_smem<typename C::fld_t, 6>(), s);
+            if (nc == kNcScalars)
+                return cudaLaunchKernel((const void*)kb_tiled<C, kNcScalars>, L->tiles, dim3(kTileThreads), args,
+                                        tile_smem<typename C::fld_t, 7>(), s);
+            return cudaErrorInvalidValue;
+        }
         return cudaLaunchKernel((const void*)fn(nc, cfg), L->node[kBatchCfgs[cfg].tile_index],
                                 dim3(kBatchCfgs[cfg].threads), args, 0, s);
     }

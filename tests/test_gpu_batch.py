@@ -112,7 +112,7 @@ def test_batch_autotuned_launch_shapes(lbdp):
     tuning runs leave the state unchanged."""
     specs = _specs()
     ref = [_alone(lbdp, s, k, "fp32", 6) for k, s in enumerate(specs)]
-    for cfg in [[0, 0, 0, 0], [1, 2, 3, 1], [3, 3, 2, 2], None]:
+    for cfg in [[0, 0, 0, 0], [1, 2, 3, 1], [3, 4, 2, 4], None]:
         batch = lbdp.Batch(precision="fp32", arena_bytes=1 << 30, graph_steps=3)
         try:
             members = []
@@ -121,6 +121,8 @@ def test_batch_autotuned_launch_shapes(lbdp):
                 _setup(b, spec, k)
                 batch.set_steps(b, 6)
                 members.append(b)
+            with pytest.raises(lbdp.LbError):
+                batch.set_config([4, 0, 0, 0])   # the tile candidate exists for force and transport only
             if cfg is None:
                 got, ms = batch.tune(reps=3)
                 assert all(0 <= c < lbdp.lbb_num_configs() for c in got) and all(m > 0 for m in ms)
