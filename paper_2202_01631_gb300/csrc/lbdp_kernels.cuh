@@ -933,19 +933,32 @@ __device__ __forceinline__ void collide_store(const PrmR<typename C::real>& Q, c
     const R ux = (jx + (R)0.5 * Fx) / rho;
     const R uy = (jy + (R)0.5 * Fy) / rho;
     const R uz = (jz + (R)0.5 * Fz) / rho;
-    const R itau = Q.itau, omf = Q.omf;
+    const R itau = Q.itau, omf = Q.omf, keep = (R)1 - itau;
     const R uu = ux * ux + uy * uy + uz * uz;
     const R uF = ux * Fx + uy * Fy + uz * Fz;
+    // rest direction
+    {
+        const R w = wgt_r<R>(0);
+        const R ge = w * (dr - (R)1.5 * rho * uu);
+        const R Sg = w * ((R)-3 * uF);
+        PopStore<S>::store_dev(fd, n, 0, rho0, fma_x(gl[0], keep, fma_x(ge, itau, omf * Sg)));
+    }
+    // opposite pairs (j, j+1): c.u and c.F change sign, so the equilibrium
+    // and the Guo source split into a shared even part and an odd part
+    //   g_eq = A +- B,  A = w [(rho - rho0) + rho (4.5 (c.u)^2 - 1.5 u^2)],  B = 3 w rho c.u
+    //   S    = C +- E,  C = w [9 (c.u)(c.F) - 3 u.F],                      E = 3 w c.F
 #pragma unroll
-    for (int j = 0; j < 19; ++j) {
+    for (int j = 1; j < 19; j += 2) {
         const R cu = cdot<R>(j, ux, uy, uz);
         const R cF = cdot<R>(j, Fx, Fy, Fz);
         const R w = wgt_r<R>(j);
-        // Guo source w [3 (c - u) + 9 (c.u) c] . F = w [3 (c.F - u.F) + 9 (c.u)(c.F)]
-        const R Sg = w * ((R)3 * (cF - uF) + (R)9 * cu * cF);
-        const R ge = w * (dr + rho * ((R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu));
-        const R out = gl[j] - (gl[j] - ge) * itau + omf * Sg;
-        PopStore<S>::store_dev(fd, (size_t)j * N + n, j, rho0, out);
+        const R A = w * (dr + rho * ((R)4.5 * cu * cu - (R)1.5 * uu));
+        const R B = (R)3 * w * rho * cu;
+        const R Cs = w * ((R)9 * cu * cF - (R)3 * uF);
+        const R E = (R)3 * w * cF;
+        PopStore<S>::store_dev(fd, (size_t)j * N + n, j, rho0, fma_x(gl[j], keep, fma_x(A + B, itau, omf * (Cs + E))));
+        PopStore<S>::store_dev(fd, (size_t)(j + 1) * N + n, j + 1, rho0,
+                               fma_x(gl[j + 1], keep, fma_x(A - B, itau, omf * (Cs - E))));
     }
     F* u = (F*)D.u;
     u[n] = (F)ux;
