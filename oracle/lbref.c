@@ -16,7 +16,10 @@
  *       on particle links with phoretic slip          (Sec. Particles, Eq. for v_s)
  *       then BGK collision with Guo forcing
  *   S4  explicit conservative update of psi and phi   (Eq. diffusion_reaction)
- *       with Janus production (Eq. activity) and the sink k_d (phi - phi0)
+ *       with Janus production (Eq. activity) and the sink k_d (phi - phi0);
+ *       or, with scalar_scheme = 1, the same equations by lattice Boltzmann:
+ *       D3Q7 distributions collide to an equilibrium built on the chemical
+ *       potential and stream with bounce-back at walls and moving surfaces
  *   S6b particle translation and rotation
  *   S7  covering / uncovering of nodes swept by moving particles, and the
  *       uniform correction that keeps the psi and phi totals exact
@@ -70,7 +73,12 @@ struct ref_sim {
     long nfluid;
     int err;
     double wall_psi, wall_phi; /* psi, phi carried into the particles this step */
+    double* h;  /* [14][N] scheme 1: D3Q7 distributions of psi (0..6), phi (7..13) */
+    double* hs; /* [14][N] their post-collision values */
 };
+
+/* D3Q7 (directions 0..6 of the D3Q19 table), weights 1/4 and 1/8, c_s^2 = 1/4. */
+static const double W7[7] = {0.25, 0.125, 0.125, 0.125, 0.125, 0.125, 0.125};
 
 /* ------------------------------------------------------------------ */
 /* geometry                                                            */
@@ -579,6 +587,130 @@ static void step_scalars(ref_sim* s)
 }
 
 /* ------------------------------------------------------------------ */
+/* S4 by lattice Boltzmann (scalar_scheme = 1)                         */
+/* ------------------------------------------------------------------ */
+
+/* Equilibrium of a scalar g with chemical potential mu and mobility M at
+ * velocity u, relaxation time 1 (so Gamma = M / (1 - 1/2) = 2M):
+ *   h_i = w_i (Gamma mu + g c_i.u) / c_s^2   (i = 1..6),
+ *   h_0 = g - sum_{i>0} h_i = g - 3 Gamma mu.
+ * Its moments are g, g u and Gamma mu I, which gives
+ * dg/dt + div(g u) = M lap mu (Eq. diffusion_reaction). */
+static double heq7(int i, double g, double mu, double M, const double u[3])
+{
+    const double G = 2.0 * M;
+    if (i == 0) return g - 3.0 * G * mu;
+    const double cu = CX[i] * u[0] + CY[i] * u[1] + CZ[i] * u[2];
+    return W7[i] * (G * mu + g * cu) / 0.25;
+}
+
+static void step_scalars_lb(ref_sim* s)
+{
+    const ref_params* p = &s->p;
+    const long N = s->N;
+    s->wall_psi = 0.0;
+    s->wall_phi = 0.0;
+    /* collision (relaxation time 1: the post-collision populations are the
+     * equilibrium), with the sink and the Janus production added to the rest
+     * population of phi */
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long n = nidx(s, x, y, z);
+                if (s->mask[n]) {
+                    for (int k = 0; k < 14; ++k) s->hs[k * N + n] = 0.0;
+                    continue;
+                }
+                double u0[3] = {s->u[n], s->u[N + n], s->u[2 * N + n]};
+                double ps = s->psi[n], ph = s->phi[n];
+                for (int i = 0; i < 7; ++i) {
+                    s->hs[i * N + n] = heq7(i, ps, s->mupsi[n], p->M_psi, u0);
+                    s->hs[(7 + i) * N + n] = heq7(i, ph, s->muphi[n], p->M_phi, u0);
+                }
+                double src = -p->k_d * (ph - phi0_of(s, ps));
+                unsigned char adj[REF_MAXP];
+                memset(adj, 0, (size_t)s->np);
+                for (int i = 1; i < 19; ++i) {
+                    long m = nbr(s, x, y, z, CX[i], CY[i], CZ[i]);
+                    if (m >= 0 && s->mask[m]) adj[s->mask[m] - 1] = 1;
+                }
+                for (int k = 0; k < s->np; ++k) {
+                    if (!adj[k]) continue;
+                    const ref_part* P = &s->part[k];
+                    double r[3];
+                    node_offset(s, P, x, y, z, r);
+                    double side = P->m[0] * r[0] + P->m[1] * r[1] + P->m[2] * r[2];
+                    if (side <= 0.0) src += P->alpha;
+                }
+                s->hs[7 * N + n] += src;
+            }
+    /* pull streaming: from the fluid node x - c_i; halfway bounce-back from a
+     * wall; from a particle, moving-wall bounce-back that carries g c.u_b into
+     * the surface (c the direction from x into the particle) */
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long n = nidx(s, x, y, z);
+                if (s->mask[n]) {
+                    for (int k = 0; k < 14; ++k) s->h[k * N + n] = 0.0;
+                    s->psin[n] = s->phin[n] = 0.0;
+                    continue;
+                }
+                double sp = 0.0, sh = 0.0;
+                for (int i = 0; i < 7; ++i) {
+                    double a, b;
+                    if (i == 0) {
+                        a = s->hs[n];
+                        b = s->hs[7 * N + n];
+                    } else {
+                        const int j = opp(i);   /* direction from x to the source */
+                        long m = nbr(s, x, y, z, CX[j], CY[j], CZ[j]);
+                        if (m >= 0 && !s->mask[m]) {
+                            a = s->hs[i * N + m];
+                            b = s->hs[(7 + i) * N + m];
+                        } else if (m < 0) {
+                            a = s->hs[j * N + n];
+                            b = s->hs[(7 + j) * N + n];
+                        } else {
+                            const ref_part* P = &s->part[s->mask[m] - 1];
+                            double r[3], ub[3], vs[3];
+                            link_velocity(s, P, x, y, z, j, r, ub, vs);
+                            double cub = CX[j] * ub[0] + CY[j] * ub[1] + CZ[j] * ub[2];
+                            /* 2 w_j g c_j.u_b / c_s^2 = g c_j.u_b */
+                            a = s->hs[j * N + n] - s->psi[n] * cub;
+                            b = s->hs[(7 + j) * N + n] - s->phi[n] * cub;
+                            s->wall_psi += s->psi[n] * cub;
+                            s->wall_phi += s->phi[n] * cub;
+                        }
+                    }
+                    s->h[i * N + n] = a;
+                    s->h[(7 + i) * N + n] = b;
+                    sp += a;
+                    sh += b;
+                }
+                s->psin[n] = sp;
+                s->phin[n] = sh;
+            }
+    double* t = s->psi;
+    s->psi = s->psin;
+    s->psin = t;
+    t = s->phi;
+    s->phi = s->phin;
+    s->phin = t;
+}
+
+/* Distributions of scheme 1 at equilibrium with mu = 0 (fields set from
+ * outside, refilled nodes). */
+static void lb_fill_node(ref_sim* s, long n, const double u[3])
+{
+    const long N = s->N;
+    for (int i = 0; i < 7; ++i) {
+        s->h[i * N + n] = heq7(i, s->psi[n], 0.0, s->p.M_psi, u);
+        s->h[(7 + i) * N + n] = heq7(i, s->phi[n], 0.0, s->p.M_phi, u);
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* S6b: particle motion with the velocity of this step                 */
 /* ------------------------------------------------------------------ */
 
@@ -658,6 +790,8 @@ static void step_cover(ref_sim* s)
                     dpsi += s->psi[n];
                     dphi += s->phi[n];
                     s->psi[n] = s->phi[n] = 0.0;
+                    if (s->h)
+                        for (int k = 0; k < 14; ++k) s->h[k * N + n] = 0.0;
                     for (int i = 0; i < 19; ++i) s->f[i * N + n] = 0.0;
                     s->u[n] = s->u[N + n] = s->u[2 * N + n] = 0.0;
                     --dfl;
@@ -701,6 +835,7 @@ static void step_cover(ref_sim* s)
                     P->imp_t[2] -= r[0] * j[1] - r[1] * j[0];
                     s->psi[n] = pb;
                     s->phi[n] = hb;
+                    if (s->h) lb_fill_node(s, n, ub);
                     dpsi -= pb;
                     dphi -= hb;
                     ++dfl;
@@ -719,6 +854,10 @@ static void step_cover(ref_sim* s)
         if (s->mask[n]) continue;
         s->psi[n] += cps;
         s->phi[n] += cph;
+        if (s->h) {   /* the rest populations carry the correction */
+            s->h[n] += cps;
+            s->h[7 * N + n] += cph;
+        }
     }
 }
 
@@ -729,6 +868,7 @@ static void step_cover(ref_sim* s)
 ref_sim* ref_create(const ref_params* p)
 {
     if (p->nx <= 0 || p->ny <= 0 || p->nz <= 0 || p->tau <= 0.5 || p->rho0 <= 0.0) return NULL;
+    if (p->scalar_scheme != 0 && p->scalar_scheme != 1) return NULL;
     ref_sim* s = (ref_sim*)calloc(1, sizeof(ref_sim));
     if (!s) return NULL;
     s->p = *p;
@@ -751,10 +891,20 @@ ref_sim* ref_create(const ref_params* p)
         ref_destroy(s);
         return NULL;
     }
+    if (p->scalar_scheme == 1) {
+        s->h = (double*)calloc((size_t)(14 * N), sizeof(double));
+        s->hs = (double*)calloc((size_t)(14 * N), sizeof(double));
+        if (!s->h || !s->hs) {
+            ref_destroy(s);
+            return NULL;
+        }
+    }
     s->nfluid = N;
     double u0[3] = {0, 0, 0};
     for (int i = 0; i < 19; ++i)
         for (long n = 0; n < N; ++n) s->f[i * N + n] = feq(i, p->rho0, u0);
+    if (s->h)
+        for (long n = 0; n < N; ++n) lb_fill_node(s, n, u0);
     return s;
 }
 
@@ -773,6 +923,8 @@ void ref_destroy(ref_sim* s)
     free(s->u);
     free(s->mask);
     free(s->maskn);
+    free(s->h);
+    free(s->hs);
     free(s);
 }
 
@@ -791,6 +943,7 @@ int ref_set_fields(ref_sim* s, const double* rho, const double* u, const double*
         double rr = rho ? rho[n] : r;
         double uu[3] = {s->u[n], s->u[N + n], s->u[2 * N + n]};
         for (int i = 0; i < 19; ++i) s->f[i * N + n] = s->mask[n] ? 0.0 : feq(i, rr, uu);
+        if (s->h && !s->mask[n]) lb_fill_node(s, n, uu);
     }
     return 0;
 }
@@ -832,6 +985,8 @@ int ref_add_particle(ref_sim* s, const ref_particle_desc* d)
                     s->mask[n] = (unsigned char)s->np;
                     s->psi[n] = s->phi[n] = 0.0;
                     for (int i = 0; i < 19; ++i) s->f[i * N + n] = 0.0;
+                    if (s->h)
+                        for (int k = 0; k < 14; ++k) s->h[k * N + n] = 0.0;
                     s->u[n] = s->u[N + n] = s->u[2 * N + n] = 0.0;
                     s->nfluid--;
                 }
@@ -845,7 +1000,10 @@ int ref_step(ref_sim* s, int nsteps)
         step_mu(s);
         step_links(s);
         step_collide(s);
-        step_scalars(s);
+        if (s->h)
+            step_scalars_lb(s);
+        else
+            step_scalars(s);
         step_move(s);
         step_cover(s);
     }

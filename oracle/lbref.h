@@ -36,6 +36,8 @@ typedef struct {
     double C, M_phi, E, phi_b, k_d; /* solute stiffness, mobility, solubility,
                                        background, degradation rate      */
     int thermo_force;       /* 1: force -psi grad mu_psi - phi grad mu_phi */
+    int scalar_scheme;      /* psi, phi transport: 0 finite differences on D3Q19
+                               links; 1 lattice Boltzmann, D3Q7 distributions  */
 } ref_params;
 
 typedef struct {

@@ -36,6 +36,7 @@ class RefParams(C.Structure):
         ("C", C.c_double), ("M_phi", C.c_double), ("E", C.c_double),
         ("phi_b", C.c_double), ("k_d", C.c_double),
         ("thermo_force", C.c_int),
+        ("scalar_scheme", C.c_int),
     ]
 
 
@@ -127,7 +128,7 @@ class Oracle:
 
     DEFAULTS = dict(periodic=(1, 1, 1), tau=1.0, rho0=1.0, body_force=(0.0, 0.0, 0.0),
                     A=0.0625, kappa=0.04, M_psi=0.1, C=0.0625, M_phi=1.6, E=0.0,
-                    phi_b=0.0, k_d=0.0, thermo_force=1)
+                    phi_b=0.0, k_d=0.0, thermo_force=1, scalar_scheme=0)
 
     def __init__(self, params: dict):
         self.lib = _load()
@@ -146,6 +147,7 @@ class Oracle:
         for k in ("tau", "rho0", "A", "kappa", "M_psi", "C", "M_phi", "E", "phi_b", "k_d"):
             setattr(p, k, float(q[k]))
         p.thermo_force = int(q["thermo_force"])
+        p.scalar_scheme = int(q["scalar_scheme"])
         self.shape = (p.nz, p.ny, p.nx)
         self.N = p.nx * p.ny * p.nz
         h = self.lib.ref_create(C.byref(p))
