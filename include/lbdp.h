@@ -86,6 +86,17 @@ typedef struct {
     double E, phi_b;        /* solubility: phi0(psi) = phi_b + E tanh psi   */
     double k_d;             /* degradation rate of the sink                 */
     void* cuda_stream;      /* cudaStream_t to queue work on, or NULL       */
+    int scalar_scheme;      /* transport of psi and phi (Eq. diffusion_reaction):
+                               0 conservative finite differences on the D3Q19
+                               links (donor-cell advection);
+                               1 lattice Boltzmann: D3Q7 distributions with
+                               relaxation time 1 whose equilibrium carries the
+                               chemical potential (mobility M = Gamma/2) and
+                               moving-wall bounce-back at particles.  With
+                               relaxation time 1 the post-collision
+                               distributions are functions of the node's
+                               fields, so none are stored.  Other values:
+                               LB_ERR_PARAM                                */
 } lb_params;
 
 /* One sphere (Sec. "Particles").  pos must keep the sphere one node clear of

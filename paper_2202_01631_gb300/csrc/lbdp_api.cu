@@ -37,6 +37,7 @@ int validate(const lb_params* p)
     if (p->kappa < 0.0 || p->M_psi < 0.0 || p->M_phi < 0.0 || p->k_d < 0.0) return LB_ERR_PARAM;
     for (int a = 0; a < 3; ++a)
         if (p->periodic[a] != 0 && p->periodic[a] != 1) return LB_ERR_PARAM;
+    if (p->scalar_scheme != 0 && p->scalar_scheme != 1) return LB_ERR_PARAM;
     return LB_OK;
 }
 
@@ -591,6 +592,7 @@ int lb_create_in(const lb_params* p, lbb_batch* batch, void* region, lb_handle**
     P.N = (long long)p->nx * p->ny * p->nz;
     P.np = 0;
     P.thermo = p->thermo_force;
+    P.scheme = p->scalar_scheme;
     P.tau = p->tau;
     P.rho0 = p->rho0;
     P.A = p->A;

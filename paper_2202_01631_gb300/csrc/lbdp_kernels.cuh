@@ -855,9 +855,11 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
             for (int a = 0; a < 6; ++a)
 #pragma unroll
                 for (int b = a; b < 6; ++b, ++k) nacc[k] = fma_x(mul_x(zc, g6[a]), g6[b], nacc[k]);
-            // scalar flux into the surface, 6 w g(x) c.u_b with
-            // c.u_b = (c, r x c) . V(t+1) + c.v_s
-            const R wps = mul_x(w6, ps), wph = mul_x(w6, ph);
+            // scalar flux into the surface, 6 w g(x) c.u_b (finite
+            // differences) or g(x) c.u_b on the six D3Q7 links (lattice
+            // Boltzmann), with c.u_b = (c, r x c) . V(t+1) + c.v_s
+            const R ws = P.scheme ? (i < 7 ? (R)1 : (R)0) : w6;
+            const R wps = mul_x(ws, ps), wph = mul_x(ws, ph);
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
                 nacc[kLinkGpsi + a] = fma_x(wps, g6[a], nacc[kLinkGpsi + a]);
@@ -1057,8 +1059,11 @@ __device__ __forceinline__ void collide_node(const DevParams& P, const DevPtrs& 
 // ---------------------------------------------------------------------------
 // Links of fluid node x into particles (k_scalars): no diffusive flux; the
 // scalars leave with the boundary velocity of the bounce-back rule,
-// c.u_b g(x); Janus production on the m.(x - X) <= 0 side of each adjacent
-// particle.  Out of line (few nodes); adds to the running sums in order.
+// c.u_b g(x) -- weighted w_i on the D3Q19 links of the finite-difference
+// scheme, 1 on the six D3Q7 links of the lattice-Boltzmann one; Janus
+// production on the m.(x - X) <= 0 side of each adjacent particle (any of
+// the 18 neighbours).  Out of line (few nodes); adds to the running sums in
+// order.
 template <class R>
 struct LinkSums {
     R sps, sph, src;
@@ -1084,10 +1089,11 @@ static __device__ __noinline__ LinkSums<typename C::real> scalars_particle_links
         const uint8_t mk = D.mask[m];
         if (!mk) continue;
         adj |= 1ull << (mk - 1);
+        if (P.scheme && i >= 7) continue;
         R r[3], ubv[3], vs[3];
         link_velocity<R>(P, D.parts[mk - 1], x, y, z, i, gphi, r, ubv, vs);
         const R cub = cdot<R>(i, ubv[0], ubv[1], ubv[2]);
-        const R w = wgt_r<R>(i);
+        const R w = P.scheme ? (R)1 : wgt_r<R>(i);
         sps = fma_x(w, -mul_x(cub, ps), sps);
         sph = fma_x(w, -mul_x(cub, ph), sph);
     }
@@ -1103,6 +1109,65 @@ static __device__ __noinline__ LinkSums<typename C::real> scalars_particle_links
     return {sps, sph, src};
 }
 
+// Lattice-Boltzmann transport (scalar_scheme 1): D3Q7, weights 1/4 (rest)
+// and 1/8, c_s^2 = 1/4, relaxation time 1, Gamma = 2M.  The post-collision
+// distributions are then the equilibrium of the node's own fields,
+//   h_i* = M mu + g c_i.u / 2   (i = 1..6),   h_0* = g - 6 M mu (+ sources),
+// so the pull stream needs no stored distributions: the node's new total is
+//   g'(x) = h_0*(x) + sum_i  h_i*(x - c_i)          (fluid source)
+//                          | h_ibar*(x)              (wall: bounce-back)
+//                          | h_ibar*(x) - g(x) c_ibar.u_b   (moving surface)
+// with ibar the direction from x to the source.  Written per link from x
+// towards y = x + c_j (j = ibar), after taking M mu(x) from each of the six
+// terms of h_0*:
+//   fluid y: M (mu(y) - mu(x)) - g(y) c_j.u(y) / 2,   otherwise g(x) c_j.u(x) / 2
+// and -g(x) c_j.u_b more on a particle link (scalars_particle_links).
+template <class C, class A>
+__device__ __forceinline__ void scalars_compute_lb(const DevParams& P, const DevPtrs& D, int x, int y, int z,
+                                                   int n, const A& a)
+{
+    using R = typename C::real;
+    using F = typename C::fld_t;
+    const PrmR<R>& Q = prm<R>(P);
+    const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
+    const R ps = (R)a.template get<0>(0) + dps, ph = (R)a.template get<1>(0) + dph;
+    const R a0 = (R)a.template get<2>(0), b0 = (R)a.template get<3>(0);
+    const R ux = (R)a.template get<4>(0), uy = (R)a.template get<5>(0), uz = (R)a.template get<6>(0);
+    const R ma0 = Q.Mpsi * a0, mb0 = Q.Mphi * b0;
+    const R hps = (R)0.5 * ps, hph = (R)0.5 * ph;
+    R sps = 0, sph = 0;
+    bool solid_nb = false;
+#pragma unroll
+    for (int i = 1; i < 7; ++i) {
+        const uint8_t mk = a.mask(i);
+        const R cu0 = cdot<R>(i, ux, uy, uz);
+        const R cu1 = cdot<R>(i, (R)a.template get<4>(i), (R)a.template get<5>(i), (R)a.template get<6>(i));
+        const R psm = (R)a.template get<0>(i) + dps, phm = (R)a.template get<1>(i) + dph;
+        const R tps = mk ? mul_x(hps, cu0) : fma_x(Q.Mpsi, (R)a.template get<2>(i), -ma0) - (R)0.5 * mul_x(psm, cu1);
+        const R tph = mk ? mul_x(hph, cu0) : fma_x(Q.Mphi, (R)a.template get<3>(i), -mb0) - (R)0.5 * mul_x(phm, cu1);
+        sps += tps;
+        sph += tph;
+        solid_nb = solid_nb || (mk != 0 && mk != kWallSlot);
+    }
+#pragma unroll
+    for (int i = 7; i < 19; ++i) {
+        const uint8_t mk = a.mask(i);
+        solid_nb = solid_nb || (mk != 0 && mk != kWallSlot);
+    }
+    R hn_src = 0;
+    if (solid_nb) {
+        const LinkSums<R> l = scalars_particle_links<C>(P, D, x, y, z, ps, ph, sps, sph);
+        sps = l.sps;
+        sph = l.sph;
+        hn_src = l.src;
+    }
+    const R pn = ps + sps;
+    R hn = ph + sph - Q.kd * (ph - (Q.phib + Q.E * tanh_r(ps)));
+    hn += hn_src;
+    ((F*)D.psi_dst)[n] = (F)pn;
+    ((F*)D.phi_dst)[n] = (F)hn;
+}
+
 // Fields of the transport body: 0 psi, 1 phi, 2 mu_psi, 3 mu_phi, 4..6 u.
 template <class C, class A>
 __device__ __forceinline__ void scalars_compute(const DevParams& P, const DevPtrs& D, int x, int y, int z, int n,
@@ -1110,6 +1175,10 @@ __device__ __forceinline__ void scalars_compute(const DevParams& P, const DevPtr
 {
     using R = typename C::real;
     using F = typename C::fld_t;
+    if (P.scheme) {
+        scalars_compute_lb<C>(P, D, x, y, z, n, a);
+        return;
+    }
     const PrmR<R>& Q = prm<R>(P);
     const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
     const R ps = (R)a.template get<0>(0) + dps, ph = (R)a.template get<1>(0) + dph;

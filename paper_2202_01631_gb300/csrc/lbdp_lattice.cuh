@@ -101,6 +101,7 @@ struct DevParams {
     long long N;
     int np;
     int thermo;
+    int scheme;     // psi/phi transport: 0 finite differences, 1 D3Q7 lattice Boltzmann
     double tau, rho0;
     double g[3];
     double A, kappa, Mpsi, C, Mphi, E, phib, kd;

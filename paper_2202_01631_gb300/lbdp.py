@@ -39,6 +39,7 @@ class LbParams(C.Structure):
         ("E", C.c_double), ("phi_b", C.c_double),
         ("k_d", C.c_double),
         ("cuda_stream", C.c_void_p),
+        ("scalar_scheme", C.c_int),
     ]
 
 
@@ -187,6 +188,7 @@ def lb_params(**kw) -> LbParams:
                  ("E", 0.0), ("phi_b", 0.0), ("k_d", 0.0)):
         setattr(p, k, float(kw.get(k, d)))
     p.cuda_stream = kw.get("cuda_stream", None)
+    p.scalar_scheme = int(kw.get("scalar_scheme", 0))
     return p
 
 

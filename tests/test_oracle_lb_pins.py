@@ -131,3 +131,9 @@ def test_lb_flat_interface_profile():
     core = np.abs(psi) < 0.9
     xi_fit = 1.0 / np.polyfit(z[core], np.arctanh(psi[core]), 1)[0]
     assert abs(xi_fit - math.sqrt(2 * kappa / A)) < 0.08 * math.sqrt(2 * kappa / A)
+
+
+def test_unknown_scheme_rejected():
+    import pytest
+    with pytest.raises(ValueError):
+        Oracle(dict(nx=4, ny=4, nz=4, scalar_scheme=2))
