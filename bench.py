@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
     ap.add_argument("--edge", type=int, default=128)
+    ap.add_argument("--scalar-scheme", type=int, default=0, choices=[0, 1],
+                    help="psi/phi transport: 0 finite differences, 1 D3Q7 lattice Boltzmann")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="single", choices=["single", "batched", "served"])
     ap.add_argument("--boxes", type=int, default=64, help="batched form: number of boxes")
@@ -66,9 +68,12 @@ def parse():
     return ap.parse_args()
 
 
-def workload(edge):
+def workload(edge, scalar_scheme=0):
     from paper_2202_01631_gb300 import workloads as W
-    return W.interface(theta_c_deg=60.0, solubility_ratio=2.0, mobility=0.1, seed=0, edge=edge)
+    wl = W.interface(theta_c_deg=60.0, solubility_ratio=2.0, mobility=0.1, seed=0, edge=edge)
+    if scalar_scheme:
+        wl.params = dict(wl.params, scalar_scheme=scalar_scheme)
+    return wl
 
 
 def dist_setup(args):
@@ -280,7 +285,7 @@ def run_ours(args):
     build.build()
     from paper_2202_01631_gb300 import lbdp
 
-    wl = workload(args.edge)
+    wl = workload(args.edge, args.scalar_scheme)
     N = wl.nodes
     stream = torch.cuda.Stream()
     box = build_box(wl, args.precision, stream.cuda_stream)
@@ -351,7 +356,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
         "config": {"workload": wl.name, "nodes": N, "precision": args.precision,
                    "particles": len(wl.particles), "theta_c_deg": 60.0, "solubility_ratio": 2.0,
-                   "mobility": 0.1, "parallelism": "replicas" if world > 1 else "single",
+                   "mobility": 0.1, "scalar_scheme": args.scalar_scheme,
+                   "parallelism": "replicas" if world > 1 else "single",
                    "l2": "state %.2f GB > L2 (129 MB); no flush" % (lbdp.lb_device_bytes(box.params) / 1e9)},
         "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
