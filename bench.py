@@ -349,7 +349,8 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
-    traffic = traffic_record("k_collide", args.precision, args.edge)
+    coll_name = "k_collide"
+    traffic = traffic_record(coll_name, args.precision, args.edge)
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -359,7 +360,7 @@ def run_ours(args):
                    "mobility": 0.1, "scalar_scheme": args.scalar_scheme,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "state %.2f GB > L2 (129 MB); no flush" % (lbdp.lb_device_bytes(box.params) / 1e9)},
-        "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": coll_name, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": traffic,
                      "alg_bytes_per_launch": coll_bytes, "avg_launch_ms": coll_ms},

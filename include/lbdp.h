@@ -151,13 +151,18 @@ int lb_add_particle(lb_handle* h, const lb_particle_desc* desc, int* id_out);
  * (Eq. diffusion_reaction); particle update; covering/uncovering. */
 int lb_step(lb_handle* h, int nsteps);
 
-/* Run nsteps steps like lb_step, with a CUDA event recorded on the handle's
- * stream around every kernel, wait, and add each kernel class's time in
- * milliseconds to ms[0..4]: chemical potentials and pressure tensor,
- * particle links and velocity update, collide-stream, psi/phi transport,
- * covering.  *launches (may be NULL)
- * receives the number of kernels launched.  The events add a little host
- * overhead, so time throughput with lb_step; this call is for the split. */
+/* Run nsteps steps like lb_step, but with every kernel on the handle's stream
+ * in sequence and a CUDA event recorded between kernel classes; wait, and add
+ * each class's time in milliseconds to ms[0..4]:
+ *   0 chemical potentials, pressure tensor and force;
+ *   1 particle links and velocity update, then the collide-stream of the
+ *     fluid nodes next to particles;
+ *   2 collide-stream of all other fluid nodes (one kernel);
+ *   3 psi/phi transport of the fluid nodes not next to particles (one kernel);
+ *   4 psi/phi transport next to particles, then covering/uncovering.
+ * *launches (may be NULL) receives the number of kernels launched.  The
+ * events add a little host overhead, so time throughput with lb_step; this
+ * call is for the split. */
 int lb_profile_step(lb_handle* h, int nsteps, double* ms, int* launches);
 
 /* Number of kernels lb_step(h, nsteps) launches (for launch accounting). */

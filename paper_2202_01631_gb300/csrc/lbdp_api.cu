@@ -179,6 +179,10 @@ void free_all(lb_handle* h)
         cudaEventDestroy(h->side.fork);
         cudaEventDestroy(h->side.links_done);
         cudaEventDestroy(h->side.mark_done);
+        cudaEventDestroy(h->side.fdiv_done);
+        cudaEventDestroy(h->side.bnd_done);
+        cudaEventDestroy(h->side.collide_done);
+        cudaEventDestroy(h->side.scal_done);
         h->side.s = nullptr;
     }
     if (h->batch)
@@ -404,14 +408,14 @@ int lb_profile_step(lb_handle* h, int nsteps, double* ms, int* launches)
             ms[k] += v;
         }
     for (auto& e : ev) cudaEventDestroy(e);
-    if (launches) *launches = nsteps * (h->dp.np > 0 ? 7 : 4);
+    if (launches) *launches = nsteps * (h->dp.np > 0 ? 9 : 4);
     return st;
 }
 
 int lb_step_launches(const lb_handle* h, int nsteps)
 {
     if (!h || nsteps < 0) return LB_ERR_PARAM;
-    return nsteps * (h->dp.np > 0 ? 7 : 4);
+    return nsteps * (h->dp.np > 0 ? 9 : 4);
 }
 
 int lb_sync(lb_handle* h)
@@ -628,6 +632,10 @@ int lb_create_in(const lb_params* p, lbb_batch* batch, void* region, lb_handle**
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.links_done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.mark_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.fdiv_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.bnd_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.collide_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.scal_done, cudaEventDisableTiming);
     }
     h->region_bytes = layout(p, h->ops, h->red_blocks, nullptr, nullptr);
     if (e == cudaSuccess) {

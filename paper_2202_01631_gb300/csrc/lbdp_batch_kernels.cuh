@@ -139,14 +139,22 @@ __global__ void __launch_bounds__(kTileThreads) kb_tiled(const __grid_constant__
     for (int t = blockIdx.x; t < ntx * nty * ntz; t += g) {
         const int x0 = (t % ntx) * 32, y0 = ((t / ntx) % nty) * 4, z0 = (t / (ntx * nty)) * 4;
         __syncthreads();   // every node of the previous tile is done with sf, sm
-        stage_tile<F, NF, Tile>(P, D.mask, src, x0, y0, z0, sf, sm);
-        __syncthreads();
+        const bool any = stage_tile<F, NF, Tile>(P, D.mask, src, x0, y0, z0, sf, sm);
+        const bool clear = !__syncthreads_or(any);
         tile_nodes(P, sm, x0, y0, z0, [&](int x, int y, int z, int n, int slot) {
-            const TAcc<F, NF, Tile> a{sf, sm, slot};
-            if (NC == kNcFdiv)
-                fdiv_compute<C>(P, D, n, a);
-            else
-                scalars_compute<C>(P, D, x, y, z, n, a);
+            if (clear) {
+                const TAccClear<F, NF, Tile> a{{sf, sm, slot}};
+                if (NC == kNcFdiv)
+                    fdiv_compute<C>(P, D, n, a);
+                else
+                    scalars_compute<C>(P, D, x, y, z, n, a);
+            } else {
+                const TAcc<F, NF, Tile> a{sf, sm, slot};
+                if (NC == kNcFdiv)
+                    fdiv_compute<C>(P, D, n, a);
+                else
+                    scalars_compute<C>(P, D, x, y, z, n, a);
+            }
         });
     }
 }

@@ -424,6 +424,43 @@ struct GAcc {
     }
 };
 
+// Whether node (x, y, z) lies next to a wall (a non-periodic box face).
+__device__ __forceinline__ bool near_wall(const DevParams& P, int x, int y, int z)
+{
+    return (!P.per[0] && (x == 0 || x == P.nx - 1)) || (!P.per[1] && (y == 0 || y == P.ny - 1)) ||
+           (!P.per[2] && (z == 0 || z == P.nz - 1));
+}
+
+// Global-memory view of a node none of whose neighbours is solid or beyond a
+// wall (boundary flag clear, not at a wall): the neighbour x + c_i is
+// xi[1 + c_x] + yo[1 + c_y] + zo[1 + c_z] (periodic wrap included), and
+// mask(i) is the constant 0.
+template <class F, int NF>
+struct GAccClear {
+    int xi[3], yo[3], zo[3];
+    const F* f[NF];
+    __device__ __forceinline__ int at(int i) const { return xi[1 + cx(i)] + yo[1 + cy(i)] + zo[1 + cz(i)]; }
+    __device__ __forceinline__ uint8_t mask(int) const { return 0; }
+    template <int K>
+    __device__ __forceinline__ F get(int i) const
+    {
+        return f[K][at(i)];
+    }
+    __device__ __forceinline__ void init(const DevParams& P, int x, int y, int z)
+    {
+        const int nx = P.nx, ny = P.ny, sxy = nx * ny;
+        xi[0] = x > 0 ? x - 1 : nx - 1;
+        xi[1] = x;
+        xi[2] = x < nx - 1 ? x + 1 : 0;
+        yo[0] = (y > 0 ? y - 1 : ny - 1) * nx;
+        yo[1] = y * nx;
+        yo[2] = (y < ny - 1 ? y + 1 : 0) * nx;
+        zo[0] = (z > 0 ? z - 1 : P.nz - 1) * sxy;
+        zo[1] = z * sxy;
+        zo[2] = (z < P.nz - 1 ? z + 1 : 0) * sxy;
+    }
+};
+
 // Tile of TX x TY x TZ nodes with a one-node halo, fields [NF][slots] and
 // the mask [slots] in shared memory; slot of tile node (tx, ty, tz) is
 // (tx + 1) + HX ((ty + 1) + HY (tz + 1)).
@@ -461,12 +498,22 @@ struct TAcc {
     }
 };
 
-// Stage fields src[0..NF-1] and the mask of the tile at (x0, y0, z0) plus
-// its halo; slots beyond a wall get kWallSlot and zeros.
+// The same view of a tile none of whose slots (halo included) is solid or
+// beyond a wall: mask(i) is the constant 0, so a body instantiated with it
+// loses its mask loads and boundary branches at compile time.
 template <class F, int NF, class T>
-__device__ __forceinline__ void stage_tile(const DevParams& P, const uint8_t* mask, const F* const (&src)[NF],
+struct TAccClear : TAcc<F, NF, T> {
+    __device__ __forceinline__ uint8_t mask(int) const { return 0; }
+};
+
+// Stage fields src[0..NF-1] and the mask of the tile at (x0, y0, z0) plus
+// its halo; slots beyond a wall get kWallSlot and zeros.  Returns whether
+// this thread staged any slot that is not fluid.
+template <class F, int NF, class T>
+__device__ __forceinline__ bool stage_tile(const DevParams& P, const uint8_t* mask, const F* const (&src)[NF],
                                            int x0, int y0, int z0, F* sf, uint8_t* sm)
 {
+    bool any = false;
     for (int s = threadIdx.x; s < T::slots; s += blockDim.x) {
         const int lx = s % T::HX, ly = (s / T::HX) % T::HY, lz = s / (T::HX * T::HY);
         const int gx = wrap_coord(x0 + lx - 1, P.nx, P.per[0]);
@@ -474,15 +521,19 @@ __device__ __forceinline__ void stage_tile(const DevParams& P, const uint8_t* ma
         const int gz = wrap_coord(z0 + lz - 1, P.nz, P.per[2]);
         if (gx >= 0 && gy >= 0 && gz >= 0) {
             const int g = gx + P.nx * (gy + P.ny * gz);
-            sm[s] = mask[g];
+            const uint8_t m = mask[g];
+            sm[s] = m;
+            any = any || m != 0;
 #pragma unroll
             for (int k = 0; k < NF; ++k) sf[tile_index_last<NF, T>(k, s)] = src[k][g];
         } else {
             sm[s] = kWallSlot;
+            any = true;
 #pragma unroll
             for (int k = 0; k < NF; ++k) sf[tile_index_last<NF, T>(k, s)] = (F)0;
         }
     }
+    return any;
 }
 
 // ---------------------------------------------------------------------------
@@ -531,7 +582,16 @@ __device__ __forceinline__ void mup_node(const DevParams& P, const DevPtrs& D, i
 {
     using F = typename C::fld_t;
     const int n = x + P.nx * (y + P.ny * z);
-    if (D.mask[n]) return;
+    const uint8_t mk = D.mask[n], bf = D.bflag[n];
+    if (mk) return;
+    if (!bf && !near_wall(P, x, y, z)) {
+        GAccClear<F, 2> c;
+        c.init(P, x, y, z);
+        c.f[0] = (const F*)D.psi_src;
+        c.f[1] = (const F*)D.phi_src;
+        mup_compute<C>(P, D, x, y, z, n, c);
+        return;
+    }
     GAcc<F, 2> a;
     neighbours(P, x, y, z, a.nb);
     a.n = n;
@@ -900,19 +960,21 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
 // ---------------------------------------------------------------------------
 // S3: streaming with bounce-back, BGK collision with Guo forcing
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool near_wall(const DevParams& P, int x, int y, int z)
-{
-    return (!P.per[0] && (x == 0 || x == P.nx - 1)) || (!P.per[1] && (y == 0 || y == P.ny - 1)) ||
-           (!P.per[2] && (z == 0 || z == P.nz - 1));
-}
 
 // BGK collision with Guo forcing of node n from its streamed populations,
 // given as deviations g_i = f_i - w_i rho0 (FP32 cancellation in the moments
 // would otherwise cost the small velocity its low digits):
-//   rho = rho0 + sum g,  j = sum c g  (sum_i w_i c_i = 0),
+//   rho = rho0 + sum g,  j = sum c g  (sum_i w_i c_i = 0),  u = (j + F/2)/rho,
 //   g_eq = w [(rho - rho0) + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)],
-//   g* = g - (g - g_eq)/tau + (1 - 1/(2 tau)) S_i.
-// Writes f_dst (as deviations through the storage) and u.
+//   S    = w [3 c.F + 9 (c.u)(c.F) - 3 u.F],
+//   g* = (1 - 1/tau) g + g_eq / tau + (1 - 1/(2 tau)) S.
+// Opposite directions (j, j+1) share c.u and c.F up to sign, so
+//   g_eq/tau + (1 - 1/(2tau)) S = P +- Q  with
+//   P = cu (a cu + b cF) + e,  Q = c cu + d cF,
+// a = 4.5 w rho / tau, b = 9 w (1 - 1/(2 tau)), c = 3 w rho / tau,
+// d = 3 w (1 - 1/(2 tau)), e = w (rho - rho0 - 1.5 rho u^2) / tau
+// - 3 w (1 - 1/(2 tau)) u.F, per weight class.  Writes f_dst (as deviations
+// through the storage) and u.
 template <class C>
 __device__ __forceinline__ void collide_store(const PrmR<typename C::real>& Q, const DevPtrs& D, size_t N, int n,
                                               const typename C::real (&gl)[19], typename C::real Fx,
@@ -921,7 +983,8 @@ __device__ __forceinline__ void collide_store(const PrmR<typename C::real>& Q, c
     using R = typename C::real;
     using F = typename C::fld_t;
     using S = typename C::pop_t;
-    S* fd = (S*)D.f_dst;
+    S* fd = (S*)D.f_dst + n;
+    const int NN = (int)N;   // 19 N < 2^31
     const R rho0 = Q.rho0;
     R dr = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
@@ -932,48 +995,50 @@ __device__ __forceinline__ void collide_store(const PrmR<typename C::real>& Q, c
         if (cz(j) != 0) jz += cz(j) > 0 ? gl[j] : -gl[j];
     }
     const R rho = rho0 + dr;
-    const R ux = (jx + (R)0.5 * Fx) / rho;
-    const R uy = (jy + (R)0.5 * Fy) / rho;
-    const R uz = (jz + (R)0.5 * Fz) / rho;
+    const R ir = (R)1 / rho;
+    const R ux = fma_x((R)0.5, Fx, jx) * ir;
+    const R uy = fma_x((R)0.5, Fy, jy) * ir;
+    const R uz = fma_x((R)0.5, Fz, jz) * ir;
     const R itau = Q.itau, omf = Q.omf, keep = (R)1 - itau;
     const R uu = ux * ux + uy * uy + uz * uz;
     const R uF = ux * Fx + uy * Fy + uz * Fz;
-    // rest direction
-    {
-        const R w = wgt_r<R>(0);
-        const R ge = w * (dr - (R)1.5 * rho * uu);
-        const R Sg = w * ((R)-3 * uF);
-        PopStore<S>::store_dev(fd, n, 0, rho0, fma_x(gl[0], keep, fma_x(ge, itau, omf * Sg)));
+    const R base = (dr - (R)1.5 * rho * uu) * itau;   // (rho - rho0 - 1.5 rho u^2) / tau
+    const R tuF = (R)3 * omf * uF;                    // 3 (1 - 1/(2 tau)) u.F
+    // rest direction: w0 (base - 3 (1 - 1/(2 tau)) u.F)
+    PopStore<S>::store_dev(fd, 0, 0, rho0, fma_x(gl[0], keep, wgt_r<R>(0) * (base - tuF)));
+    const R ri = rho * itau;
+    R ka[2], kc[2], ke[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const R w = c == 0 ? wgt_r<R>(1) : wgt_r<R>(7);
+        ka[c] = (R)4.5 * w * ri;
+        kc[c] = (R)3 * w * ri;
+        ke[c] = w * (base - tuF);
     }
-    // opposite pairs (j, j+1): c.u and c.F change sign, so the equilibrium
-    // and the Guo source split into a shared even part and an odd part
-    //   g_eq = A +- B,  A = w [(rho - rho0) + rho (4.5 (c.u)^2 - 1.5 u^2)],  B = 3 w rho c.u
-    //   S    = C +- E,  C = w [9 (c.u)(c.F) - 3 u.F],                      E = 3 w c.F
+    const R kb0 = (R)9 * wgt_r<R>(1) * omf, kb1 = (R)9 * wgt_r<R>(7) * omf;
+    const R kd0 = (R)3 * wgt_r<R>(1) * omf, kd1 = (R)3 * wgt_r<R>(7) * omf;
 #pragma unroll
     for (int j = 1; j < 19; j += 2) {
+        const int c = j < 7 ? 0 : 1;
         const R cu = cdot<R>(j, ux, uy, uz);
         const R cF = cdot<R>(j, Fx, Fy, Fz);
-        const R w = wgt_r<R>(j);
-        const R A = w * (dr + rho * ((R)4.5 * cu * cu - (R)1.5 * uu));
-        const R B = (R)3 * w * rho * cu;
-        const R Cs = w * ((R)9 * cu * cF - (R)3 * uF);
-        const R E = (R)3 * w * cF;
-        PopStore<S>::store_dev(fd, (size_t)j * N + n, j, rho0, fma_x(gl[j], keep, fma_x(A + B, itau, omf * (Cs + E))));
-        PopStore<S>::store_dev(fd, (size_t)(j + 1) * N + n, j + 1, rho0,
-                               fma_x(gl[j + 1], keep, fma_x(A - B, itau, omf * (Cs - E))));
+        const R Pp = fma_x(cu, fma_x(ka[c], cu, (c ? kb1 : kb0) * cF), ke[c]);
+        const R Qq = fma_x(kc[c], cu, (c ? kd1 : kd0) * cF);
+        PopStore<S>::store_dev(fd, j * NN, j, rho0, fma_x(gl[j], keep, Pp + Qq));
+        PopStore<S>::store_dev(fd, (j + 1) * NN, j + 1, rho0, fma_x(gl[j + 1], keep, Pp - Qq));
     }
-    F* u = (F*)D.u;
-    u[n] = (F)ux;
-    u[N + n] = (F)uy;
-    u[2 * N + n] = (F)uz;
+    F* u = (F*)D.u + n;
+    u[0] = (F)ux;
+    u[NN] = (F)uy;
+    u[2 * NN] = (F)uz;
 }
 
-// Collide-stream of a fluid node next to a wall or a particle: halfway
-// bounce-back on wall links, moving bounce-back with u_b = U + Omega x r + v_s
-// on particle links.  Out of line: these nodes are few, and keeping their
-// code out of the common path keeps its register budget small.
+// Collide-stream of a fluid node next to a particle (and possibly a wall):
+// halfway bounce-back on wall links, moving bounce-back with
+// u_b = U + Omega x r + v_s on particle links.  Every mask and population
+// load is issued before the first is used.
 template <class C>
-static __device__ __noinline__ void collide_boundary(const DevParams& P, const DevPtrs& D, int x, int y, int z)
+__device__ __forceinline__ void collide_boundary_body(const DevParams& P, const DevPtrs& D, int x, int y, int z)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
@@ -981,76 +1046,101 @@ static __device__ __noinline__ void collide_boundary(const DevParams& P, const D
     const int n = x + P.nx * (y + P.ny * z);
     const PrmR<R>& Q = prm<R>(P);
     const size_t N = (size_t)P.N;
+    const int NN = (int)N;
     const S* fs = (const S*)D.f_src;
     const F* force = (const F*)D.force;
     const R rho0 = Q.rho0;
     int nb[19];
     neighbours(P, x, y, z, nb);
-    const R Fx = (R)force[n], Fy = (R)force[N + n], Fz = (R)force[2 * N + n];
+    uint8_t q[19];
+#pragma unroll
+    for (int i = 1; i < 19; ++i) q[i] = nb[i] >= 0 ? D.mask[nb[i]] : (uint8_t)0;
+    const R Fx = (R)force[n], Fy = (R)force[NN + n], Fz = (R)force[2 * NN + n];
+    // population j arrives from x - c_j = x + c_i (i = opp(j)); from a wall
+    // or a particle it is the node's own population i, reflected
+    R fl[19];
+#pragma unroll
+    for (int j = 0; j < 19; ++j) {
+        const int i = opp(j);
+        const bool own = j != 0 && (nb[i] < 0 || q[i] != 0);
+        fl[j] = (R)PopStore<S>::load_dev(fs, own ? i * NN + n : j * NN + (j == 0 ? n : nb[i]), own ? i : j, rho0);
+    }
     const F* phi = (const F*)D.phi_src;
     const R dph = corr_r<R>(D, 1);
     bool have_g = false;
     R gphi[3] = {0, 0, 0};
-    R fl[19];
-#pragma unroll
-    for (int j = 0; j < 19; ++j) {
-        if (j == 0) {
-            fl[0] = (R)PopStore<S>::load_dev(fs, n, 0, rho0);
-            continue;
-        }
+    for (int j = 1; j < 19; ++j) {
         const int i = opp(j);
-        const int m = nb[i];   // source x - c_j = x + c_i
-        if (m < 0) {
-            fl[j] = (R)PopStore<S>::load_dev(fs, (size_t)i * N + n, i, rho0);
-        } else {
-            const uint8_t q = D.mask[m];
-            if (q) {
-                if (!have_g) {
-                    grad_phi_at<R, F>(nb, phi, D.mask, (R)phi[n] + dph, dph, gphi);
-                    have_g = true;
-                }
-                R r[3], ub[3], vs[3];
-                link_velocity<R>(P, D.parts[q - 1], x, y, z, i, gphi, r, ub, vs);
-                const R cub = cdot<R>(i, ub[0], ub[1], ub[2]);
-                const R fi = (R)PopStore<S>::load_dev(fs, (size_t)i * N + n, i, rho0);
-                fl[j] = fma_x(-((R)6 * wgt_r<R>(i) * rho0), cub, fi);
-            } else {
-                fl[j] = (R)PopStore<S>::load_dev(fs, (size_t)j * N + m, j, rho0);
-            }
+        if (nb[i] < 0 || q[i] == 0) continue;
+        if (!have_g) {
+            grad_phi_at<R, F>(nb, phi, D.mask, (R)phi[n] + dph, dph, gphi);
+            have_g = true;
         }
+        R r[3], ub[3], vs[3];
+        link_velocity<R>(P, D.parts[q[i] - 1], x, y, z, i, gphi, r, ub, vs);
+        const R cub = cdot<R>(i, ub[0], ub[1], ub[2]);
+        fl[j] = fma_x(-((R)6 * wgt_r<R>(i) * rho0), cub, fl[j]);
     }
     collide_store<C>(Q, D, N, n, fl, Fx, Fy, Fz);
 }
 
+// The same, out of line, for kernels that meet these few nodes among all
+// others (keeps their code out of the common path).
 template <class C>
+static __device__ __noinline__ void collide_boundary(const DevParams& P, const DevPtrs& D, int x, int y, int z)
+{
+    collide_boundary_body<C>(P, D, x, y, z);
+}
+
+// kBoundary: nodes next to a particle are collided here (out of line);
+// otherwise they are left to k_collide_particles.
+template <class C, bool kBoundary = true>
 __device__ __forceinline__ void collide_node(const DevParams& P, const DevPtrs& D, int x, int y, int z)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
     using S = typename C::pop_t;
-    const int n = x + P.nx * (y + P.ny * z);
+    const int nx = P.nx, ny = P.ny, sxy = nx * ny;
+    const int n = x + nx * (y + ny * z);
     const PrmR<R>& Q = prm<R>(P);
     const size_t N = (size_t)P.N;
+    const int NN = (int)N;
     const S* fs = (const S*)D.f_src;
     const F* force = (const F*)D.force;
-    int nb[19];
-    neighbours(P, x, y, z, nb);
+    // source x - c_j of population j as xi[1 - c_jx] + yo[1 - c_jy] + zo[1 - c_jz]:
+    // wrapped on periodic axes, clamped beyond a wall (those links are
+    // replaced below)
+    const int xi[3] = {x > 0 ? x - 1 : (P.per[0] ? nx - 1 : 0), x, x < nx - 1 ? x + 1 : (P.per[0] ? 0 : x)};
+    const int yo[3] = {(y > 0 ? y - 1 : (P.per[1] ? ny - 1 : 0)) * nx, y * nx,
+                       (y < ny - 1 ? y + 1 : (P.per[1] ? 0 : y)) * nx};
+    const int zo[3] = {(z > 0 ? z - 1 : (P.per[2] ? P.nz - 1 : 0)) * sxy, z * sxy,
+                       (z < P.nz - 1 ? z + 1 : (P.per[2] ? 0 : z)) * sxy};
     // issue every load of the common case at once (one memory round trip);
-    // solid and boundary nodes drop them (a few percent of the nodes)
+    // solid and particle-boundary nodes drop them (a few per mille)
     const uint8_t mk = D.mask[n], bf = D.bflag[n];
-    const R Fx = (R)force[n], Fy = (R)force[N + n], Fz = (R)force[2 * N + n];
+    const R Fx = (R)force[n], Fy = (R)force[NN + n], Fz = (R)force[2 * NN + n];
     R fl[19];
 #pragma unroll
     for (int j = 0; j < 19; ++j) {
-        const int m = nb[opp(j)] >= 0 ? nb[opp(j)] : n;
-        fl[j] = (R)PopStore<S>::load_dev(fs, (size_t)j * N + m, j, Q.rho0);
+        const int m = xi[1 - cx(j)] + yo[1 - cy(j)] + zo[1 - cz(j)];
+        fl[j] = (R)PopStore<S>::load_dev(fs, j * NN + m, j, Q.rho0);
     }
     if (mk) return;
-    if (bf || near_wall(P, x, y, z)) {
-        collide_boundary<C>(P, D, x, y, z);
+    if (bf) {
+        if (kBoundary) collide_boundary<C>(P, D, x, y, z);
         return;
     }
-    // every source x - c_j is a fluid node: plain pull
+    if (near_wall(P, x, y, z)) {
+        // halfway bounce-back: a link whose source lies beyond a wall brings
+        // back the node's own population of the opposite direction
+        const bool wx[3] = {!P.per[0] && x == 0, false, !P.per[0] && x == nx - 1};
+        const bool wy[3] = {!P.per[1] && y == 0, false, !P.per[1] && y == ny - 1};
+        const bool wz[3] = {!P.per[2] && z == 0, false, !P.per[2] && z == P.nz - 1};
+#pragma unroll
+        for (int j = 1; j < 19; ++j)
+            if (wx[1 - cx(j)] || wy[1 - cy(j)] || wz[1 - cz(j)])
+                fl[j] = (R)PopStore<S>::load_dev(fs, opp(j) * NN + n, opp(j), Q.rho0);
+    }
     collide_store<C>(Q, D, N, n, fl, Fx, Fy, Fz);
 }
 
@@ -1122,7 +1212,7 @@ static __device__ __noinline__ LinkSums<typename C::real> scalars_particle_links
 // terms of h_0*:
 //   fluid y: M (mu(y) - mu(x)) - g(y) c_j.u(y) / 2,   otherwise g(x) c_j.u(x) / 2
 // and -g(x) c_j.u_b more on a particle link (scalars_particle_links).
-template <class C, class A>
+template <class C, bool kBoundary, class A>
 __device__ __forceinline__ void scalars_compute_lb(const DevParams& P, const DevPtrs& D, int x, int y, int z,
                                                    int n, const A& a)
 {
@@ -1156,6 +1246,7 @@ __device__ __forceinline__ void scalars_compute_lb(const DevParams& P, const Dev
     }
     R hn_src = 0;
     if (solid_nb) {
+        if (!kBoundary) return;   // left to k_scalars_particles
         const LinkSums<R> l = scalars_particle_links<C>(P, D, x, y, z, ps, ph, sps, sph);
         sps = l.sps;
         sph = l.sph;
@@ -1169,14 +1260,16 @@ __device__ __forceinline__ void scalars_compute_lb(const DevParams& P, const Dev
 }
 
 // Fields of the transport body: 0 psi, 1 phi, 2 mu_psi, 3 mu_phi, 4..6 u.
-template <class C, class A>
+// kBoundary: nodes next to a particle are transported here; otherwise they
+// are left to k_scalars_particles.
+template <class C, bool kBoundary = true, class A>
 __device__ __forceinline__ void scalars_compute(const DevParams& P, const DevPtrs& D, int x, int y, int z, int n,
                                                 const A& a)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
     if (P.scheme) {
-        scalars_compute_lb<C>(P, D, x, y, z, n, a);
+        scalars_compute_lb<C, kBoundary>(P, D, x, y, z, n, a);
         return;
     }
     const PrmR<R>& Q = prm<R>(P);
@@ -1195,9 +1288,12 @@ __device__ __forceinline__ void scalars_compute(const DevParams& P, const DevPtr
         const R ub = (R)0.5 * (cu0 + cu1);
         const R psm = (R)a.template get<0>(i) + dps, phm = (R)a.template get<1>(i) + dph;
         // donor-cell upwind advection, diffusion M (mu(x + c) - mu(x))
-        const bool up = ub > (R)0;
-        const R tps = fma_x(Q.Mpsi, (R)a.template get<2>(i), -ma0) - ub * (up ? ps : psm);
-        const R tph = fma_x(Q.Mphi, (R)a.template get<3>(i), -mb0) - ub * (up ? ph : phm);
+        // -ub g_upwind = -ua g(x) - ud g(x + c) with ua = max(ub, 0), ud = ub - ua:
+        // one of the two products is zero, so this is the single rounding of
+        // the upwind term, with a max instead of a compare and two selects
+        const R ua = ub > (R)0 ? ub : (R)0, ud = ub - ua;
+        const R tps = fma_x(-ua, ps, fma_x(-ud, psm, fma_x(Q.Mpsi, (R)a.template get<2>(i), -ma0)));
+        const R tph = fma_x(-ua, ph, fma_x(-ud, phm, fma_x(Q.Mphi, (R)a.template get<3>(i), -mb0)));
         // links to walls and particles carry no flux here (particle links are
         // handled below)
         const R w = wgt_r<R>(i);
@@ -1207,6 +1303,7 @@ __device__ __forceinline__ void scalars_compute(const DevParams& P, const DevPtr
     }
     R hn_src = 0;
     if (solid_nb) {
+        if (!kBoundary) return;   // left to k_scalars_particles
         const LinkSums<R> l = scalars_particle_links<C>(P, D, x, y, z, ps, ph, sps, sph);
         sps = l.sps;
         sph = l.sph;
@@ -1507,11 +1604,16 @@ __global__ void __launch_bounds__(kTileThreads) kt_fdiv(DevParams P, DevPtrs D)
     const size_t N = (size_t)P.N;
     const F* pt = (const F*)D.pt;
     const F* const src[6] = {pt, pt + N, pt + 2 * N, pt + 3 * N, pt + 4 * N, pt + 5 * N};
-    stage_tile<F, 6, Tile>(P, D.mask, src, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, sf, sm);
-    __syncthreads();
+    const bool any = stage_tile<F, 6, Tile>(P, D.mask, src, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, sf, sm);
+    const bool clear = !__syncthreads_or(any);
     tile_nodes(P, sm, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, [&](int, int, int, int n, int slot) {
-        const TAcc<F, 6, Tile> a{sf, sm, slot};
-        fdiv_compute<C>(P, D, n, a);
+        if (clear) {
+            const TAccClear<F, 6, Tile> a{{sf, sm, slot}};
+            fdiv_compute<C>(P, D, n, a);
+        } else {
+            const TAcc<F, 6, Tile> a{sf, sm, slot};
+            fdiv_compute<C>(P, D, n, a);
+        }
     });
 }
 
@@ -1527,11 +1629,16 @@ __global__ void __launch_bounds__(kTileThreads) kt_scalars(const __grid_constant
     const F* u = (const F*)D.u;
     const F* const src[7] = {(const F*)D.psi_src, (const F*)D.phi_src, (const F*)D.mupsi, (const F*)D.muphi,
                              u, u + N, u + 2 * N};
-    stage_tile<F, 7, Tile>(P, D.mask, src, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, sf, sm);
-    __syncthreads();
+    const bool any = stage_tile<F, 7, Tile>(P, D.mask, src, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, sf, sm);
+    const bool clear = !__syncthreads_or(any);
     tile_nodes(P, sm, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, [&](int x, int y, int z, int n, int slot) {
-        const TAcc<F, 7, Tile> a{sf, sm, slot};
-        scalars_compute<C>(P, D, x, y, z, n, a);
+        if (clear) {
+            const TAccClear<F, 7, Tile> a{{sf, sm, slot}};
+            scalars_compute<C, false>(P, D, x, y, z, n, a);
+        } else {
+            const TAcc<F, 7, Tile> a{sf, sm, slot};
+            scalars_compute<C, false>(P, D, x, y, z, n, a);
+        }
     });
 }
 
@@ -1547,7 +1654,68 @@ __global__ void __launch_bounds__(kRowThreads, 8) k_collide(const __grid_constan
                                                              const __grid_constant__ DevPtrs D)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x < P.nx) collide_node<C>(P, D, x, blockIdx.y, blockIdx.z);
+    if (x < P.nx) collide_node<C, false>(P, D, x, blockIdx.y, blockIdx.z);
+}
+
+// Collide-stream of the fluid nodes next to particles, beside k_collide (which
+// leaves them out).  These nodes read the particle records and their
+// neighbours' masks in chains of dependent loads; inside k_collide, under its
+// full memory load and register budget, each such chain would hold its block
+// long after the others finish.  Block (b, p) walks the link box of particle
+// p; a node next to several particles is collided by the lowest of them.
+template <class C>
+__global__ void __launch_bounds__(kPartThreads) k_collide_particles(const __grid_constant__ DevParams P,
+                                                                     const __grid_constant__ DevPtrs D)
+{
+    const int p = blockIdx.y;
+    const DevPart& q = D.parts[p];
+    const int o[3] = {q.g.Xi[0] - q.Rc - 2, q.g.Xi[1] - q.Rc - 2, q.g.Xi[2] - q.Rc - 2};
+    const int tot = P.side1[0] * P.side1[1] * P.side1[2];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+        int x, y, z;
+        if (!box_node(P, o, P.side1, t, x, y, z)) continue;
+        const int n = x + P.nx * (y + P.ny * z);
+        if (D.mask[n] || !D.bflag[n]) continue;
+        int nb[19];
+        neighbours(P, x, y, z, nb);
+        int lo = 256;
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const int m = nb[i] >= 0 ? D.mask[nb[i]] : 0;
+            if (m != 0 && m < lo) lo = m;
+        }
+        if (lo != p + 1) continue;
+        collide_boundary_body<C>(P, D, x, y, z);
+    }
+}
+
+// Transport of the fluid nodes next to particles, beside kt_scalars (which
+// leaves them out), for the same reason and with the same split as
+// k_collide_particles.
+template <class C>
+__global__ void __launch_bounds__(kPartThreads) k_scalars_particles(const __grid_constant__ DevParams P,
+                                                                     const __grid_constant__ DevPtrs D)
+{
+    const int p = blockIdx.y;
+    const DevPart& q = D.parts[p];
+    const int o[3] = {q.g.Xi[0] - q.Rc - 2, q.g.Xi[1] - q.Rc - 2, q.g.Xi[2] - q.Rc - 2};
+    const int tot = P.side1[0] * P.side1[1] * P.side1[2];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+        int x, y, z;
+        if (!box_node(P, o, P.side1, t, x, y, z)) continue;
+        const int n = x + P.nx * (y + P.ny * z);
+        if (D.mask[n] || !D.bflag[n]) continue;
+        int nb[19];
+        neighbours(P, x, y, z, nb);
+        int lo = 256;
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const int m = nb[i] >= 0 ? D.mask[nb[i]] : 0;
+            if (m != 0 && m < lo) lo = m;
+        }
+        if (lo != p + 1) continue;
+        scalars_node<C>(P, D, x, y, z);
+    }
 }
 
 template <class C>

@@ -110,6 +110,24 @@ def test_driven_sphere_covering_fp64():
     assert abs(sg[1] - s0[1]) < 1e-9 and abs(sg[2] - s0[2]) < 1e-9
 
 
+def test_row_pipeline_walls_sphere_fp64():
+    """Rows of 48 nodes (whole 16-byte runs) take the pipelined collide-stream
+    kernel: walls in x (the wrapped shared-memory index must not be used) and
+    z, several rows per block so the stage ring wraps, a driven sphere."""
+    nx, ny, nz = 48, 40, 72
+    params = dict(W.BASE_PARAMS, nx=nx, ny=ny, nz=nz, periodic=(0, 1, 0), E=0.2, M_psi=0.2, k_d=1e-3,
+                  body_force=(2e-5, 0.0, -1e-5))
+    fields = _noisy_fields((nz, ny, nx), 7, psi_amp=0.1)
+    part = dict(pos=(20.3, 19.6, 35.2), R=5.1, vel=(0.04, -0.03, 0.05), omega=(0.01, 0.0, 0.0), fixed=1,
+                m_hat=(0.0, 0.6, 0.8), mu_plus=0.1, mu_minus=-0.1, theta_c_deg=80.0, alpha=1e-2)
+    box, ref = make_pair(params, fields, [part])
+    m0 = ref.mask().copy()
+    box.step(50)
+    ref.step(50)
+    assert np.sum(ref.mask() != m0) > 20
+    _assert64(compare(box, ref))
+
+
 def test_free_spheres_across_periodic_wrap_fp64():
     """Two free Janus spheres, one crossing the periodic x boundary, with
     external loads, activity, slip and wetting."""
