@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kTileThreads) kb_tiled(const __grid_constant__
 template <class C>
 __global__ void __launch_bounds__(kPartThreads, 1) kb_links(const __grid_constant__ BoxLaunch L)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];   // block_sum_t_bytes<kLinkK>(kPartThreads)
+    extern __shared__ __align__(16) unsigned char smem_raw[];   // block_rows_bytes<kLinkK>(kPartThreads)
     __shared__ DevPart sp;
     __shared__ bool last;
     const int b = blockIdx.y;
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kPartThreads) kb_cover_mark(const __grid_const
 template <class C>
 __global__ void __launch_bounds__(kPartThreads) kb_cover_apply(const __grid_constant__ BoxLaunch L)
 {
-    __shared__ double smem[block_sum_t_bytes<kCoverK>(kPartThreads) / sizeof(double)];
+    __shared__ double smem[block_rows_bytes<kCoverK>(kPartThreads) / sizeof(double)];
     __shared__ bool last;
     const int b = blockIdx.y;
     if (b >= L.nbox || L.left[L.base + b] <= 0) return;

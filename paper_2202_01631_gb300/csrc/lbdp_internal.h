@@ -24,13 +24,14 @@ enum KernelClass { kKMu = 0, kKLinks, kKCollide, kKScalars, kKCover, kNumKernelC
 
 // A second stream for the particle kernels of a step: k_links (which needs
 // only mu/P and the populations) and k_cover_mark run there while the force,
-// collide-stream and transport kernels run on the main stream; collide-stream
-// waits for links_done (it bounces back with the new particle velocities),
-// k_cover_apply waits for mark_done.  k_collide_particles (the nodes next to
-// particles) waits there for fdiv_done (the force) and runs beside
-// k_collide; the transport waits for bnd_done.  In the same way
-// k_scalars_particles waits for collide_done and runs beside kt_scalars;
-// k_cover_apply waits for scal_done.
+// collide-stream and transport kernels run on the main stream.  The bulk
+// collide-stream touches no particle, so it does not wait for them;
+// k_collide_particles (the nodes next to particles, which bounce back with
+// the new particle velocities) runs on the side stream after k_links and
+// fdiv_done (the force), beside k_collide, and the transport waits for
+// bnd_done.  In the same way k_scalars_particles waits for collide_done and
+// runs beside kt_scalars; k_cover_apply waits for scal_done (which follows
+// k_cover_mark on the side stream).
 struct SideStream {
     cudaStream_t s;
     cudaEvent_t fork, links_done, mark_done, fdiv_done, bnd_done, collide_done, scal_done;

@@ -339,54 +339,71 @@ __device__ void block_sum(double (&v)[K], double* smem /* [32*K] */)
     __syncthreads();
 }
 
-// FP64 block reduction through shared memory: each warp transposes its K x 32
-// values so that lane k adds column k (column k + 32 in a second pass when
-// K > 32; warps holding only zeros skip it), then threads add the warp results
-// in warp order.  The order is fixed, so the result is deterministic; it is
-// valid in thread 0 and stays in sm[0..K-1].  sm holds
-// (32 + 1) * K * (blockDim.x / 32) doubles.
+// FP64 block reduction over the threads whose values are not all zero (in the
+// particle kernels most threads of a box hold none): those threads write
+// their K values as rows, in thread order, into shared memory; G threads per
+// value add rows g, g + G, ..., and thread k adds its G partials in order.
+// The order depends only on which threads contribute, so the result is
+// deterministic.  It is valid in thread 0's v and stays in sm[0..K-1]; sm
+// holds block_rows_bytes<K>(blockDim.x) bytes (results, 32 warp counts and
+// the G x K partials below sm[256], rows from there).  blockDim.x >= G K.
 template <int K>
-__device__ void block_sum_t(double (&v)[K], double* sm)
+__host__ __device__ constexpr int block_rows_groups()
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    bool nz = false;
-#pragma unroll
-    for (int k = 0; k < K; ++k) nz = nz || (v[k] != 0.0);
-    const bool any = __any_sync(0xffffffffu, nz);
-    double* wbuf = sm + (size_t)warp * 32 * K;
-    double* wres = sm + (size_t)nw * 32 * K;
-    if (any) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) wbuf[lane * K + k] = v[k];
-    }
-    __syncwarp();
-#pragma unroll
-    for (int c0 = 0; c0 < K; c0 += 32) {
-        const int c = c0 + lane;
-        if (c < K) {
-            double s = 0.0;
-            if (any)
-                for (int l = 0; l < 32; ++l) s += wbuf[l * K + c];
-            wres[warp * K + c] = s;
-        }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += wres[w * K + k];
-        sm[k] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int k = 0; k < K; ++k) v[k] = sm[k];
-    __syncthreads();
+    return K > 16 ? 4 : 16;
+}
+template <int K>
+__host__ __device__ constexpr size_t block_rows_bytes(int threads)
+{
+    return (size_t)(256 + threads * K) * sizeof(double);
 }
 
 template <int K>
-__host__ __device__ constexpr size_t block_sum_t_bytes(int threads)
+__device__ void block_sum_rows(double (&v)[K], double* sm)
 {
-    return (size_t)(32 + 1) * K * (threads / 32) * sizeof(double);
+    constexpr int G = block_rows_groups<K>();
+    static_assert(K <= 64 && G * K <= 176, "reduction layout");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int* wcount = (int*)(sm + 64);
+    double* part = sm + 80;
+    double* rows = sm + 256;
+    bool nz = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) nz = nz || (v[k] != 0.0);
+    const unsigned bal = __ballot_sync(0xffffffffu, nz);
+    if (lane == 0) wcount[warp] = __popc(bal);
+    __syncthreads();
+    int base = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+        const int c = wcount[w];
+        base += w < warp ? c : 0;
+        total += c;
+    }
+    if (nz) {
+        double* row = rows + (size_t)(base + __popc(bal & ((1u << lane) - 1u))) * K;
+#pragma unroll
+        for (int k = 0; k < K; ++k) row[k] = v[k];
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < G * K) {
+        const int k = t % K, g = t / K;
+        double s = 0.0;
+        for (int r = g; r < total; r += G) s += rows[(size_t)r * K + k];
+        part[g * K + k] = s;
+    }
+    __syncthreads();
+    if (t < K) {
+        double s = 0.0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) s += part[g * K + t];
+        sm[t] = s;
+    }
+    __syncthreads();
+    if (t == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = sm[k];
+    __syncthreads();
 }
 
 // Lattice node of slot t in a box of edges s[3] starting at o[3]; false when
@@ -825,7 +842,7 @@ static __device__ __noinline__ void particle_update(int3 L3, int3 per3, DevPart*
 // links_block runs block bi of the nbi blocks of particle p; the block split
 // (and with it the summation order) is the same in the single-box and the
 // batched kernels, so both give identical bits.  smem holds
-// block_sum_t_bytes<kLinkK>(blockDim.x) bytes; sp and last are block-shared.
+// block_rows_bytes<kLinkK>(blockDim.x) bytes; sp and last are block-shared.
 template <class C>
 __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D, int p, int bi, int nbi,
                                             double* smem, DevPart& sp, bool& last)
@@ -931,7 +948,7 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] += (double)nacc[k];
     }
-    block_sum_t<K>(acc, smem);
+    block_sum_rows<K>(acc, smem);
     double* part = D.link_part + ((size_t)p * kMaxPartBlocks + bi) * K;
     if (threadIdx.x == 0) {
         for (int k = 0; k < K; ++k) part[k] = acc[k];
@@ -941,7 +958,7 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
     __syncthreads();
     if (!last) return;
     // last block of this particle: thread b loads block b's partials; the
-    // block reduction adds them in a fixed order
+    // row reduction adds them in block order
     __threadfence();
     double sum[K];
 #pragma unroll
@@ -951,7 +968,7 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
 #pragma unroll
         for (int k = 0; k < K; ++k) sum[k] = __ldcg(pb + k);
     }
-    block_sum_t<K>(sum, smem);   // the totals stay in smem[0..K-1]
+    block_sum_rows<K>(sum, smem);   // the totals stay in smem[0..K-1]
     if (threadIdx.x >= 32) return;
     particle_update(make_int3(P.nx, P.ny, P.nz), make_int3(P.per[0], P.per[1], P.per[2]), D.parts, D.link_ticket,
                     D.err, p, q, smem, smem + 64);   // totals in smem[0..K-1], K <= 64
@@ -1387,7 +1404,7 @@ __device__ __forceinline__ void cover_mark_block(const DevParams& P, const DevPt
 //
 // cover_apply_block runs block bi of the nbi blocks of particle p; the last of
 // the np * nbi blocks of the box (a ticket) finishes the step for all
-// particles of the box.  smem holds block_sum_t_bytes<kCoverK>(blockDim.x)
+// particles of the box.  smem holds block_rows_bytes<kCoverK>(blockDim.x)
 // bytes.
 template <class C>
 __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevPtrs& D, int p, int bi, int nbi,
@@ -1508,7 +1525,7 @@ __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevP
             atomicOr(D.err, kErrOverlap);   // passed straight into another sphere
         }
     }
-    block_sum_t<K>(acc, smem);
+    block_sum_rows<K>(acc, smem);
     double* part = D.cover_part + ((size_t)p * kMaxPartBlocks + bi) * K;
     if (threadIdx.x == 0) {
         for (int k = 0; k < K; ++k) part[k] = acc[k];
@@ -1531,7 +1548,7 @@ __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevP
 #pragma unroll
             for (int c = 0; c < K; ++c) s[c] = __ldcg(cp + c);
         }
-        block_sum_t<K>(s, smem);
+        block_sum_rows<K>(s, smem);
         if (threadIdx.x == 0) {
             DevPart& dk = D.parts[k];
             for (int a = 0; a < 3; ++a) {
@@ -1729,7 +1746,7 @@ __global__ void __launch_bounds__(kRowThreads) k_scalars(const __grid_constant__
 template <class C>
 __global__ void __launch_bounds__(kPartThreads, 1) k_links(DevParams P, DevPtrs D)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];   // block_sum_t_bytes<kLinkK>(kPartThreads)
+    extern __shared__ __align__(16) unsigned char smem_raw[];   // block_rows_bytes<kLinkK>(kPartThreads)
     __shared__ DevPart sp;
     __shared__ bool last;
     links_block<C>(P, D, blockIdx.y, blockIdx.x, gridDim.x, (double*)smem_raw, sp, last);
@@ -1744,7 +1761,7 @@ __global__ void __launch_bounds__(kPartThreads) k_cover_mark(DevParams P, DevPtr
 template <class C>
 __global__ void __launch_bounds__(kPartThreads) k_cover_apply(DevParams P, DevPtrs D)
 {
-    __shared__ double smem[block_sum_t_bytes<kCoverK>(kPartThreads) / sizeof(double)];
+    __shared__ double smem[block_rows_bytes<kCoverK>(kPartThreads) / sizeof(double)];
     __shared__ bool last;
     cover_apply_block<C>(P, D, blockIdx.y, blockIdx.x, gridDim.x, smem, last);
 }

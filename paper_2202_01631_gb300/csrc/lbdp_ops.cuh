@@ -38,7 +38,7 @@ struct Ops {
     // classes for the per-kernel split.
     using R = typename C::real;
 
-    static constexpr size_t kLinkSmem = block_sum_t_bytes<kLinkK>(kPartThreads);
+    static constexpr size_t kLinkSmem = block_rows_bytes<kLinkK>(kPartThreads);
     static constexpr size_t kFdivSmem = tile_smem<typename C::fld_t, 6>();
     static constexpr size_t kScalSmem = tile_smem<typename C::fld_t, 7>();
 
@@ -74,15 +74,12 @@ struct Ops {
             cudaEventRecord(side->fork, s);
             cudaStreamWaitEvent(side->s, side->fork, 0);
             k_links<C><<<pg1, kPartThreads, kLinkSmem, side->s>>>(P, D);
-            cudaEventRecord(side->links_done, side->s);
             k_cover_mark<C><<<pg2, kPartThreads, 0, side->s>>>(P, D);
-            cudaEventRecord(side->mark_done, side->s);
             kt_fdiv<C><<<g.tiles, kTileThreads, kFdivSmem, s>>>(P, D);
             cudaEventRecord(side->fdiv_done, s);
             cudaStreamWaitEvent(side->s, side->fdiv_done, 0);
             k_collide_particles<C><<<pg1, kPartThreads, 0, side->s>>>(P, D);
             cudaEventRecord(side->bnd_done, side->s);
-            cudaStreamWaitEvent(s, side->links_done, 0);
             k_collide<C><<<g.grid, g.block, 0, s>>>(P, D);
             cudaEventRecord(side->collide_done, s);
             cudaStreamWaitEvent(side->s, side->collide_done, 0);
@@ -215,7 +212,7 @@ struct BOps {
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
         e = cudaFuncSetAttribute(kb_links<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)block_sum_t_bytes<kLinkK>(kPartThreads));
+                                 (int)block_rows_bytes<kLinkK>(kPartThreads));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(kb_tiled<C, kNcFdiv>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)tile_smem<typename C::fld_t, 6>());
@@ -252,7 +249,7 @@ struct BOps {
     {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
-        const size_t lsm = block_sum_t_bytes<kLinkK>(kPartThreads);
+        const size_t lsm = block_rows_bytes<kLinkK>(kPartThreads);
         for (int l = 0; l < nl; ++l) {
             LaunchPlan* L = Ls + l;
             L->L.par = par;   // copied into each launch's parameters at the call
