@@ -1216,6 +1216,29 @@ static __device__ __noinline__ LinkSums<typename C::real> scalars_particle_links
     return {sps, sph, src};
 }
 
+// psi and phi side by side: on sm_100-class GPUs two FP32 values go through
+// one packed instruction (each lane rounds as the scalar operation does);
+// FP64 keeps two scalar operations.
+template <class R>
+struct Two {
+    R a, b;
+};
+__device__ __forceinline__ Two<float> fma2(Two<float> x, Two<float> y, Two<float> z)
+{
+    const float2 r = __ffma2_rn(make_float2(x.a, x.b), make_float2(y.a, y.b), make_float2(z.a, z.b));
+    return {r.x, r.y};
+}
+__device__ __forceinline__ Two<double> fma2(Two<double> x, Two<double> y, Two<double> z)
+{
+    return {fma_x(x.a, y.a, z.a), fma_x(x.b, y.b, z.b)};
+}
+__device__ __forceinline__ Two<float> add2(Two<float> x, Two<float> y)
+{
+    const float2 r = __fadd2_rn(make_float2(x.a, x.b), make_float2(y.a, y.b));
+    return {r.x, r.y};
+}
+__device__ __forceinline__ Two<double> add2(Two<double> x, Two<double> y) { return {add_x(x.a, y.a), add_x(x.b, y.b)}; }
+
 // Lattice-Boltzmann transport (scalar_scheme 1): D3Q7, weights 1/4 (rest)
 // and 1/8, c_s^2 = 1/4, relaxation time 1, Gamma = 2M.  The post-collision
 // distributions are then the equilibrium of the node's own fields,
@@ -1295,7 +1318,8 @@ __device__ __forceinline__ void scalars_compute(const DevParams& P, const DevPtr
     const R a0 = (R)a.template get<2>(0), b0 = (R)a.template get<3>(0);
     const R ux = (R)a.template get<4>(0), uy = (R)a.template get<5>(0), uz = (R)a.template get<6>(0);
     const R ma0 = Q.Mpsi * a0, mb0 = Q.Mphi * b0;
-    R sps = 0, sph = 0;
+    const Two<R> g0{ps, ph}, corr{dps, dph}, mob{Q.Mpsi, Q.Mphi}, nmu0{-ma0, -mb0};
+    Two<R> sg{0, 0};
     bool solid_nb = false;
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
@@ -1303,21 +1327,23 @@ __device__ __forceinline__ void scalars_compute(const DevParams& P, const DevPtr
         const R cu0 = cdot<R>(i, ux, uy, uz);
         const R cu1 = cdot<R>(i, (R)a.template get<4>(i), (R)a.template get<5>(i), (R)a.template get<6>(i));
         const R ub = (R)0.5 * (cu0 + cu1);
-        const R psm = (R)a.template get<0>(i) + dps, phm = (R)a.template get<1>(i) + dph;
-        // donor-cell upwind advection, diffusion M (mu(x + c) - mu(x))
+        const Two<R> gm = add2(Two<R>{(R)a.template get<0>(i), (R)a.template get<1>(i)}, corr);
+        // donor-cell upwind advection, diffusion M (mu(x + c) - mu(x)), for
+        // psi and phi together
         // -ub g_upwind = -ua g(x) - ud g(x + c) with ua = max(ub, 0), ud = ub - ua:
         // one of the two products is zero, so this is the single rounding of
         // the upwind term, with a max instead of a compare and two selects
         const R ua = ub > (R)0 ? ub : (R)0, ud = ub - ua;
-        const R tps = fma_x(-ua, ps, fma_x(-ud, psm, fma_x(Q.Mpsi, (R)a.template get<2>(i), -ma0)));
-        const R tph = fma_x(-ua, ph, fma_x(-ud, phm, fma_x(Q.Mphi, (R)a.template get<3>(i), -mb0)));
+        Two<R> t = fma2(mob, Two<R>{(R)a.template get<2>(i), (R)a.template get<3>(i)}, nmu0);
+        t = fma2(Two<R>{-ud, -ud}, gm, t);
+        t = fma2(Two<R>{-ua, -ua}, g0, t);
         // links to walls and particles carry no flux here (particle links are
         // handled below)
         const R w = wgt_r<R>(i);
-        sps = fma_x(w, mk ? (R)0 : tps, sps);
-        sph = fma_x(w, mk ? (R)0 : tph, sph);
+        sg = fma2(Two<R>{w, w}, mk ? Two<R>{0, 0} : t, sg);
         solid_nb = solid_nb || (mk != 0 && mk != kWallSlot);
     }
+    R sps = sg.a, sph = sg.b;
     R hn_src = 0;
     if (solid_nb) {
         if (!kBoundary) return;   // left to k_scalars_particles
