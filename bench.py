@@ -495,9 +495,6 @@ def run_batched(args):
         "mlups": mlups,
         "one_by_one": {"sims_per_hour": alone_sims_h, "ms_per_step_all_boxes": alone_ms,
                        "speedup": sims_h / alone_sims_h},
-        "kernel_rooflines": {k: {"achieved": v["achieved"], "frac": v["achieved"] / peak,
-                                 "avg_launch_ms": v["avg_launch_ms"], "unit": "GB/s"}
-                             for k, v in per_kernel.items()},
         "step_roofline": {"alg_bytes_per_node": ALG_BYTES_STEP[args.precision], "achieved": step_gbs,
                           "peak": peak, "unit": "GB/s", "frac": step_gbs / peak, "peak_kind": peak_kind},
         "clocks": clk.summary(),

@@ -134,11 +134,13 @@ def precision(seed: int = 0, edge: int = 256, n_spheres: int = 8, R: float = 6.0
 def _sweep_box(rng: np.random.Generator, edge: int, n_spheres: int, r_range, name: str,
                steps: int) -> Workload:
     """A cubic box (periodic x/y, walls in z) with a flat interface at
-    mid-height and n_spheres spheres straddling it, kept 4 nodes apart;
-    contact angle, solubility ratio and mobility drawn uniformly."""
+    mid-height and n_spheres spheres straddling it, kept 4 nodes apart and
+    at least edge/4 from the walls (an active sphere can leave the interface
+    and swim a few radii in a run); contact angle, solubility ratio and
+    mobility (within the paper's +-0.1) drawn uniformly."""
     theta = float(rng.uniform(45.0, 135.0))
     ratio = float(rng.uniform(0.25, 4.0))
-    mob = float(rng.uniform(-0.2, 0.2))
+    mob = float(rng.uniform(-0.1, 0.1))
     params = dict(BASE_PARAMS, nx=edge, ny=edge, nz=edge, periodic=(1, 1, 0),
                   solubility_ratio=ratio, phi_b=1.0)
     z0 = edge / 2.0
@@ -151,7 +153,7 @@ def _sweep_box(rng: np.random.Generator, edge: int, n_spheres: int, r_range, nam
             raise RuntimeError("could not place the spheres")
         R = float(rng.uniform(*r_range))
         pos = np.array([rng.uniform(0, edge), rng.uniform(0, edge), z0 + 0.3 + rng.uniform(-0.5, 0.5) * R])
-        ok = pos[2] - R >= 3.0 and pos[2] + R <= edge - 4.0
+        ok = pos[2] - R >= edge / 4.0 and pos[2] + R <= edge - edge / 4.0
         for q in parts:
             d = pos - np.array(q["pos"])
             d[:2] -= edge * np.round(d[:2] / edge)
@@ -168,7 +170,8 @@ def batched(seed: int = 0, n_boxes: int = 64, edge_range=(32, 96), steps: int = 
     out = []
     for k in range(n_boxes):
         edge = int(rng.integers(edge_range[0], edge_range[1] + 1))
-        out.append(_sweep_box(rng, edge, 1, (4.0, 8.0), "batched_%d_%d" % (k, edge), steps))
+        out.append(_sweep_box(rng, edge, 1, (4.0, max(4.0, min(8.0, edge / 8.0))), "batched_%d_%d" % (k, edge),
+                              steps))
     return out
 
 
@@ -183,7 +186,7 @@ def serving_requests(seed: int = 0, n: int = 32, rate: float = 20.0, edge_range=
         edge = int(rng.integers(edge_range[0], edge_range[1] + 1))
         steps = int(round(math.exp(rng.uniform(math.log(steps_range[0]), math.log(steps_range[1])))))
         ns = int(rng.integers(spheres[0], spheres[1] + 1))
-        rmax = min(8.0, edge / 6.0)
+        rmax = min(8.0, edge / 8.0)
         out.append((t, _sweep_box(rng, edge, ns, (min(3.0, rmax), rmax), "request_%d_%d" % (k, edge), steps)))
     return out
 
