@@ -65,22 +65,65 @@ template <class R>
 struct PartR;
 template <>
 struct PartR<float> {
-    static __device__ __forceinline__ float U(const DevPart& q, int a) { return q.Uf[a]; }
-    static __device__ __forceinline__ float W(const DevPart& q, int a) { return q.Wf[a]; }
-    static __device__ __forceinline__ float mu_m(const DevPart& q) { return q.mu_mf; }
-    static __device__ __forceinline__ float mu_p(const DevPart& q) { return q.mu_pf; }
-    static __device__ __forceinline__ float Hk(const DevPart& q) { return q.Hk_f; }
-    static __device__ __forceinline__ float alpha(const DevPart& q) { return q.alpha_f; }
+    template <class Q>
+    static __device__ __forceinline__ float U(const Q& q, int a) { return q.Uf[a]; }
+    template <class Q>
+    static __device__ __forceinline__ float W(const Q& q, int a) { return q.Wf[a]; }
+    template <class Q>
+    static __device__ __forceinline__ float mu_m(const Q& q) { return q.mu_mf; }
+    template <class Q>
+    static __device__ __forceinline__ float mu_p(const Q& q) { return q.mu_pf; }
+    template <class Q>
+    static __device__ __forceinline__ float Hk(const Q& q) { return q.Hk_f; }
+    template <class Q>
+    static __device__ __forceinline__ float alpha(const Q& q) { return q.alpha_f; }
 };
 template <>
 struct PartR<double> {
-    static __device__ __forceinline__ double U(const DevPart& q, int a) { return q.U[a]; }
-    static __device__ __forceinline__ double W(const DevPart& q, int a) { return q.W[a]; }
-    static __device__ __forceinline__ double mu_m(const DevPart& q) { return q.mu_m; }
-    static __device__ __forceinline__ double mu_p(const DevPart& q) { return q.mu_p; }
-    static __device__ __forceinline__ double Hk(const DevPart& q) { return q.Hk; }
-    static __device__ __forceinline__ double alpha(const DevPart& q) { return q.alpha; }
+    template <class Q>
+    static __device__ __forceinline__ double U(const Q& q, int a) { return q.U[a]; }
+    template <class Q>
+    static __device__ __forceinline__ double W(const Q& q, int a) { return q.W[a]; }
+    template <class Q>
+    static __device__ __forceinline__ double mu_m(const Q& q) { return q.mu_m; }
+    template <class Q>
+    static __device__ __forceinline__ double mu_p(const Q& q) { return q.mu_p; }
+    template <class Q>
+    static __device__ __forceinline__ double Hk(const Q& q) { return q.Hk; }
+    template <class Q>
+    static __device__ __forceinline__ double alpha(const Q& q) { return q.alpha; }
 };
+
+// The fields of one particle that its boundary links use, copied from the
+// device record into registers with independent loads (one memory round
+// trip), for a kernel that reads them for many links of one node.
+struct LinkPart {
+    Geo g;
+    float mf[3], smarg;
+    float Uf[3], Wf[3], mu_pf, mu_mf;
+    double m[3], U[3], W[3], mu_p, mu_m;
+};
+
+__device__ __forceinline__ LinkPart link_part(const DevPart& q)
+{
+    LinkPart l;
+    l.g = q.g;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        l.mf[a] = q.mf[a];
+        l.Uf[a] = q.Uf[a];
+        l.Wf[a] = q.Wf[a];
+        l.m[a] = q.m[a];
+        l.U[a] = q.U[a];
+        l.W[a] = q.W[a];
+    }
+    l.smarg = q.smarg;
+    l.mu_pf = q.mu_pf;
+    l.mu_mf = q.mu_mf;
+    l.mu_p = q.mu_p;
+    l.mu_m = q.mu_m;
+    return l;
+}
 
 // ---------------------------------------------------------------------------
 // shared device helpers
@@ -158,7 +201,8 @@ __device__ __forceinline__ bool solid_test(const Geo& g, const int D[3], float R
 
 // m . r <= 0 for r = (x - X) + c_i/2 (i = 0: the node itself), the oracle's
 // decision (Eq. MuJ, Eq. activity: the cap side takes mu_- and produces).
-__device__ __forceinline__ bool cap_minus(const DevPart& q, const Geo& g, const int D[3], int i)
+template <class Q>
+__device__ __forceinline__ bool cap_minus(const Q& q, const Geo& g, const int D[3], int i)
 {
     const float r0 = ((float)D[0] + 0.5f * (float)cx(i)) - g.fr[0];
     const float r1 = ((float)D[1] + 0.5f * (float)cy(i)) - g.fr[1];
@@ -194,8 +238,8 @@ __device__ __forceinline__ void link_offset_r<double>(const Geo& g, const int D[
 // Boundary velocity at the midpoint of link x -> x + c_i of particle q:
 // u_b = U + Omega x r + v_s, v_s = mu (1 - n n) . grad phi, mu = mu_- where
 // m.r <= 0 else mu_+ (Eq. MuJ).  Returns r (midpoint offset), u_b and v_s.
-template <class R>
-__device__ __forceinline__ void link_velocity(const DevParams& P, const DevPart& q, int x, int y, int z, int i,
+template <class R, class Q>
+__device__ __forceinline__ void link_velocity(const DevParams& P, const Q& q, int x, int y, int z, int i,
                                               const R gphi[3], R r[3], R ub[3], R vs[3])
 {
     int D[3];
@@ -1101,6 +1145,78 @@ __device__ __forceinline__ void collide_boundary_body(const DevParams& P, const 
     collide_store<C>(Q, D, N, n, fl, Fx, Fy, Fz);
 }
 
+// The same node with every load of the node issued before any is used (masks,
+// both candidate sources of each population, phi around the node, the
+// force; then the record of the node's lowest adjacent particle), for
+// k_collide_particles, which has the registers for it.  nb and q (the masks
+// of the neighbours) come from the caller.  Same arithmetic, same bits as
+// collide_boundary_body.
+template <class C>
+__device__ __forceinline__ void collide_boundary_wide(const DevParams& P, const DevPtrs& D, int x, int y, int z,
+                                                      const int (&nb)[19], const uint8_t (&q)[19], int lo)
+{
+    using R = typename C::real;
+    using F = typename C::fld_t;
+    using S = typename C::pop_t;
+    const int n = x + P.nx * (y + P.ny * z);
+    const PrmR<R>& Q = prm<R>(P);
+    const size_t N = (size_t)P.N;
+    const int NN = (int)N;
+    const S* fs = (const S*)D.f_src;
+    const F* force = (const F*)D.force;
+    const F* phi = (const F*)D.phi_src;
+    const R rho0 = Q.rho0;
+    const R dph = corr_r<R>(D, 1);
+    const LinkPart lp = link_part(D.parts[lo - 1]);
+    const R Fx = (R)force[n], Fy = (R)force[NN + n], Fz = (R)force[2 * NN + n];
+    const R phn = (R)phi[n];
+    R fl[19], fo[19], pv[19];
+#pragma unroll
+    for (int j = 0; j < 19; ++j) {
+        const int i = opp(j);
+        const int m = nb[i] >= 0 ? nb[i] : n;
+        fl[j] = (R)PopStore<S>::load_dev(fs, j * NN + (j == 0 ? n : m), j, rho0);
+        fo[j] = j == 0 ? (R)0 : (R)PopStore<S>::load_dev(fs, i * NN + n, i, rho0);
+        pv[j] = j == 0 ? (R)0 : (R)phi[nb[j] >= 0 ? nb[j] : n];
+    }
+    // population j arrives from x - c_j = x + c_i (i = opp(j)); from a wall
+    // or a particle it is the node's own population i, reflected
+#pragma unroll
+    for (int j = 1; j < 19; ++j) {
+        const int i = opp(j);
+        if (nb[i] < 0 || q[i] != 0) fl[j] = fo[j];
+    }
+    // grad phi as grad_phi_at, from the values loaded above
+    R gphi[3] = {0, 0, 0};
+    {
+        const R own = phn + dph;
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const R v = (nb[i] < 0 || q[i]) ? (R)0 : add_x(pv[i] + dph, -own);
+            const R w = wgt_r<R>(i);
+            if (cx(i) != 0) gphi[0] = fma_x(cx(i) > 0 ? w : -w, v, gphi[0]);
+            if (cy(i) != 0) gphi[1] = fma_x(cy(i) > 0 ? w : -w, v, gphi[1]);
+            if (cz(i) != 0) gphi[2] = fma_x(cz(i) > 0 ? w : -w, v, gphi[2]);
+        }
+        gphi[0] = mul_x(gphi[0], (R)3);
+        gphi[1] = mul_x(gphi[1], (R)3);
+        gphi[2] = mul_x(gphi[2], (R)3);
+    }
+#pragma unroll
+    for (int j = 1; j < 19; ++j) {
+        const int i = opp(j);
+        if (nb[i] < 0 || q[i] == 0) continue;
+        R r[3], ub[3], vs[3];
+        if (q[i] == lo)
+            link_velocity<R>(P, lp, x, y, z, i, gphi, r, ub, vs);
+        else
+            link_velocity<R>(P, D.parts[q[i] - 1], x, y, z, i, gphi, r, ub, vs);
+        const R cub = cdot<R>(i, ub[0], ub[1], ub[2]);
+        fl[j] = fma_x(-((R)6 * wgt_r<R>(i) * rho0), cub, fl[j]);
+    }
+    collide_store<C>(Q, D, N, n, fl, Fx, Fy, Fz);
+}
+
 // The same, out of line, for kernels that meet these few nodes among all
 // others (keeps their code out of the common path).
 template <class C>
@@ -1721,14 +1837,16 @@ __global__ void __launch_bounds__(kPartThreads) k_collide_particles(const __grid
         if (D.mask[n] || !D.bflag[n]) continue;
         int nb[19];
         neighbours(P, x, y, z, nb);
+        uint8_t qm[19];
+        qm[0] = 0;
         int lo = 256;
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
-            const int m = nb[i] >= 0 ? D.mask[nb[i]] : 0;
-            if (m != 0 && m < lo) lo = m;
+            qm[i] = nb[i] >= 0 ? D.mask[nb[i]] : (uint8_t)0;
+            if (qm[i] != 0 && qm[i] < lo) lo = qm[i];
         }
         if (lo != p + 1) continue;
-        collide_boundary_body<C>(P, D, x, y, z);
+        collide_boundary_wide<C>(P, D, x, y, z, nb, qm, lo);
     }
 }
 

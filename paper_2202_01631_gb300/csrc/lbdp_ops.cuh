@@ -74,12 +74,12 @@ struct Ops {
             cudaEventRecord(side->fork, s);
             cudaStreamWaitEvent(side->s, side->fork, 0);
             k_links<C><<<pg1, kPartThreads, kLinkSmem, side->s>>>(P, D);
-            k_cover_mark<C><<<pg2, kPartThreads, 0, side->s>>>(P, D);
             kt_fdiv<C><<<g.tiles, kTileThreads, kFdivSmem, s>>>(P, D);
             cudaEventRecord(side->fdiv_done, s);
             cudaStreamWaitEvent(side->s, side->fdiv_done, 0);
             k_collide_particles<C><<<pg1, kPartThreads, 0, side->s>>>(P, D);
             cudaEventRecord(side->bnd_done, side->s);
+            k_cover_mark<C><<<pg2, kPartThreads, 0, side->s>>>(P, D);
             k_collide<C><<<g.grid, g.block, 0, s>>>(P, D);
             cudaEventRecord(side->collide_done, s);
             cudaStreamWaitEvent(side->s, side->collide_done, 0);
