@@ -75,7 +75,7 @@ size_t layout(const lb_params* p, const PrecOps* ops, int red_blocks, lb_handle*
     t->pt = take(6 * N * fb);
     t->bflag = (uint8_t*)take(N);
     t->parts = (DevPart*)take(kMaxParticles * sizeof(DevPart));
-    t->corr = (double*)take(4 * sizeof(double));
+    t->corr = (double*)take(8 * sizeof(double));   // [step parity][psi, phi FP64; psi, phi FP32]
     t->err = (int*)take(sizeof(int));
     t->link_part = (double*)take((size_t)kMaxParticles * kMaxPartBlocks * kLinkK * sizeof(double));
     t->link_ticket = (unsigned*)take(kMaxParticles * sizeof(unsigned));
@@ -113,8 +113,10 @@ DevPtrs ptrs(const lb_handle* h, int src)
     d.mask = h->mask[src];
     d.mask_next = h->mask[dst];
     d.parts = h->parts;
-    d.corr = h->corr;
-    d.corr_f = (float*)(h->corr + 2);
+    d.corr = h->corr + 4 * src;
+    d.corr_f = (float*)(h->corr + 4 * src + 2);
+    d.corr_next = h->corr + 4 * dst;
+    d.corr_f_next = (float*)(h->corr + 4 * dst + 2);
     d.err = h->err;
     d.pt = h->pt;
     d.force = h->force;
@@ -255,7 +257,7 @@ int lb_set_fields(lb_handle* h, const double* rho, const double* u, const double
     // correction), populations to equilibrium; then the correction is spent
     LB_TRY(h->ops->set_fields(h->dp, cur_ptrs(h), s, rho ? st_rho : nullptr, u ? st_u : nullptr,
                               psi ? st_psi : nullptr, phi ? st_phi : nullptr));
-    LB_TRY(cudaMemsetAsync(h->corr, 0, 4 * sizeof(double), s));
+    LB_TRY(cudaMemsetAsync(h->corr, 0, 8 * sizeof(double), s));
     return LB_OK;
 }
 
@@ -659,7 +661,7 @@ int lb_create_in(const lb_params* p, lbb_batch* batch, void* region, lb_handle**
     long long nf = P.N;
     e = cudaMemsetAsync(h->mask[0], 0, N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->mask[1], 0, N, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->corr, 0, 4 * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->corr, 0, 8 * sizeof(double), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->link_ticket, 0, kMaxParticles * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->cover_ticket, 0, sizeof(unsigned), s);

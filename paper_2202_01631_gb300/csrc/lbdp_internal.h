@@ -29,9 +29,9 @@ enum KernelClass { kKMu = 0, kKLinks, kKCollide, kKScalars, kKCover, kNumKernelC
 // k_collide_particles (the nodes next to particles, which bounce back with
 // the new particle velocities) runs on the side stream after k_links and
 // fdiv_done (the force), beside k_collide, and the transport waits for
-// bnd_done.  In the same way k_scalars_particles waits for collide_done and
-// runs beside kt_scalars; k_cover_apply waits for scal_done (which follows
-// k_cover_mark on the side stream).
+// bnd_done.  In the same way k_scalars_particles and then k_cover_apply wait
+// for collide_done and run beside kt_scalars; the main stream ends the step
+// by waiting for scal_done.
 struct SideStream {
     cudaStream_t s;
     cudaEvent_t fork, links_done, mark_done, fdiv_done, bnd_done, collide_done, scal_done;

@@ -1709,10 +1709,10 @@ __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevP
     if (threadIdx.x != 0) return;
     const long long nf = *D.nfluid + (long long)dcnt;
     *D.nfluid = nf;
-    D.corr[0] = dsum_psi / (double)nf;
-    D.corr[1] = dsum_phi / (double)nf;
-    D.corr_f[0] = (float)D.corr[0];
-    D.corr_f[1] = (float)D.corr[1];
+    D.corr_next[0] = dsum_psi / (double)nf;
+    D.corr_next[1] = dsum_phi / (double)nf;
+    D.corr_f_next[0] = (float)D.corr_next[0];
+    D.corr_f_next[1] = (float)D.corr_next[1];
     *D.cover_ticket = 0u;
 }
 

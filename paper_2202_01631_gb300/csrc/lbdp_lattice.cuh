@@ -221,6 +221,9 @@ struct DevPtrs {
     DevPart* parts;
     double* corr;         // [2]: uniform psi/phi correction still to be added
     float* corr_f;        // [2]: the same in FP32
+    double* corr_next;    // [2]: the correction the covering of this step leaves
+    float* corr_f_next;   //      for the next one (a second buffer, so that the
+                          //      covering can run beside the transport)
     int* err;
     double* link_part;    // [np][kMaxPartBlocks][kLinkK]
     unsigned* link_ticket;   // [np]

@@ -84,11 +84,14 @@ struct Ops {
             cudaEventRecord(side->collide_done, s);
             cudaStreamWaitEvent(side->s, side->collide_done, 0);
             k_scalars_particles<C><<<pg1, kPartThreads, 0, side->s>>>(P, D);
+            // covering touches only nodes next to particles, whose fields the
+            // side-stream kernels wrote, and leaves the next step's uniform
+            // correction in the other buffer: it runs beside the transport
+            k_cover_apply<C><<<pg2, kPartThreads, 0, side->s>>>(P, D);
             cudaEventRecord(side->scal_done, side->s);
             cudaStreamWaitEvent(s, side->bnd_done, 0);
             kt_scalars<C><<<g.tiles, kTileThreads, kScalSmem, s>>>(P, D);
-            cudaStreamWaitEvent(s, side->scal_done, 0);
-            k_cover_apply<C><<<pg2, kPartThreads, 0, s>>>(P, D);
+            cudaStreamWaitEvent(s, side->scal_done, 0);   // the step ends with the side stream
             return cudaGetLastError();
         }
         if (ev) cudaEventRecord(ev[0], s);
