@@ -164,14 +164,38 @@ def _sweep_box(rng: np.random.Generator, edge: int, n_spheres: int, r_range, nam
     return Workload(name, params, fields, parts, steps)
 
 
+def _slab_box(rng: np.random.Generator, edge: int, r_range, name: str, steps: int) -> Workload:
+    """A cubic box periodic on every axis holding a slab of water between two
+    flat interfaces (z = edge/4 and 3 edge/4), one sphere straddling the lower
+    one; radius, contact angle, solubility ratio and mobility drawn uniformly.
+    With no wall an active sphere may swim anywhere during the run."""
+    R = float(rng.uniform(*r_range))
+    theta = float(rng.uniform(45.0, 135.0))
+    ratio = float(rng.uniform(0.25, 4.0))
+    mob = float(rng.uniform(-0.2, 0.2))
+    params = dict(BASE_PARAMS, nx=edge, ny=edge, nz=edge, periodic=(1, 1, 1),
+                  solubility_ratio=ratio, phi_b=1.0)
+    z = np.arange(edge, dtype=np.float64)
+    z1, z2 = edge / 4.0, 3.0 * edge / 4.0
+    prof = np.tanh((z - z1) / 2.0) - np.tanh((z - z2) / 2.0) - 1.0
+    fields = dict(rho=np.ones((edge, edge, edge)), u=np.zeros((3, edge, edge, edge)),
+                  psi=np.ascontiguousarray(np.broadcast_to(prof[:, None, None], (edge, edge, edge))),
+                  phi=np.zeros((edge, edge, edge)))
+    pos = (float(rng.uniform(0, edge)), float(rng.uniform(0, edge)), z1 + 0.3 + float(rng.uniform(-0.5, 0.5)) * R)
+    parts = [dict(pos=pos, R=R, m_hat=tuple(random_unit_vector(rng)), alpha=1e-3, mu_plus=mob, mu_minus=mob,
+                  theta_c_deg=theta, rho_p=1.0)]
+    return Workload(name, params, fields, parts, steps)
+
+
 def batched(seed: int = 0, n_boxes: int = 64, edge_range=(32, 96), steps: int = 5000) -> List[Workload]:
-    """Independent boxes for the batched form, one sphere each."""
+    """Independent boxes for the batched form, one sphere each with R in
+    [4, 8], contact angle in [45, 135] degrees, solubility ratio in [0.25, 4]
+    and mobility in [-0.2, 0.2]."""
     rng = np.random.default_rng(seed)
     out = []
     for k in range(n_boxes):
         edge = int(rng.integers(edge_range[0], edge_range[1] + 1))
-        out.append(_sweep_box(rng, edge, 1, (4.0, max(4.0, min(8.0, edge / 8.0))), "batched_%d_%d" % (k, edge),
-                              steps))
+        out.append(_slab_box(rng, edge, (4.0, 8.0), "batched_%d_%d" % (k, edge), steps))
     return out
 
 

@@ -24,13 +24,22 @@ def _check_box(wl):
 
 
 def test_batched_boxes():
+    """Periodic boxes (no wall to swim into) with the drawn ranges of the
+    batched form; the psi slab has its two interfaces where stated."""
     wls = W.batched(seed=0, n_boxes=64)
     assert len(wls) == 64
     for wl in wls:
         L = wl.params["nx"]
         assert 32 <= L <= 96 and len(wl.particles) == 1
-        assert 4.0 <= wl.particles[0]["R"] <= max(4.0, L / 8.0)
-        _check_box(wl)
+        assert wl.params["periodic"] == (1, 1, 1)
+        d = wl.particles[0]
+        assert 4.0 <= d["R"] <= 8.0 and abs(d["mu_plus"]) <= 0.2 and 45.0 <= d["theta_c_deg"] <= 135.0
+        assert 2.0 * d["R"] + 4.0 <= L   # the sphere and its periodic image stay apart
+        psi = wl.fields["psi"][:, 0, 0]
+        assert abs(psi[0] + 1) < 1e-2 and abs(psi[L // 2] - 1) < 1e-2
+        crossings = np.nonzero(np.diff((psi > 0).astype(int)))[0]
+        assert len(crossings) == 2
+        assert abs(crossings[0] + 0.5 - L / 4.0) <= 1.0 and abs(crossings[1] + 0.5 - 3 * L / 4.0) <= 1.0
 
 
 def test_serving_requests():
