@@ -1721,7 +1721,7 @@ __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevP
 // bodies; grid (blocks per particle, particles) for the particle bodies
 // ---------------------------------------------------------------------------
 template <class C>
-__global__ void __launch_bounds__(kRowThreads) k_mup(DevParams P, DevPtrs D)
+__global__ void __launch_bounds__(kRowThreads, 10) k_mup(DevParams P, DevPtrs D)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x < P.nx) mup_node<C>(P, D, x, blockIdx.y, blockIdx.z);
