@@ -3,17 +3,18 @@
 //   k_mup          one thread per node: chemical potentials (Eq.
 //                  chem_potentials, wetting ghosts) and the chemical pressure
 //                  tensor P (Eq. free_energy)
-//   k_fdiv         one thread per node: force on the fluid F = g - div P
+//   kt_fdiv        32x4x4 tiles: force on the fluid F = g - div P
 //   k_links        per particle: bounce-back and chemical-stress momentum sums
 //                  over its boundary links, implicit velocity update, new
 //                  position and orientation (Sec. "Particles")
-//   k_collide      D3Q19 pull streaming, halfway bounce-back on walls, moving
-//                  bounce-back plus phoretic slip on particle links, BGK + Guo
-//                  with F; nodes away from walls and particles take a
-//                  branch-free path
-//   k_scalars      one thread per node: psi/phi transport (Eq.
-//                  diffusion_reaction), Janus production (Eq. activity) and the
-//                  k_d sink
+//   k_collide      D3Q19 pull streaming, halfway bounce-back on walls, BGK +
+//                  Guo with F, for every fluid node not next to a particle
+//   k_collide_particles  the same for the nodes next to particles: moving
+//                  bounce-back plus phoretic slip on their particle links
+//   kt_scalars     32x4x4 tiles: psi/phi transport (Eq. diffusion_reaction),
+//                  and the k_d sink, for nodes not next to a particle
+//   k_scalars_particles  the same next to particles, with Janus production
+//                  (Eq. activity) and the flux into the moving surfaces
 //   k_cover_mark   per particle: solid mask at the new positions
 //   k_cover_apply  per particle: covering/uncovering and boundary flags; the
 //                  last block folds the psi/phi deficits into the uniform
@@ -1280,7 +1281,7 @@ __device__ __forceinline__ void collide_node(const DevParams& P, const DevPtrs& 
 // ---------------------------------------------------------------------------
 // S4: psi and phi transport, production and sink, one thread per node
 // ---------------------------------------------------------------------------
-// Links of fluid node x into particles (k_scalars): no diffusive flux; the
+// Links of fluid node x into particles (transport): no diffusive flux; the
 // scalars leave with the boundary velocity of the bounce-back rule,
 // c.u_b g(x) -- weighted w_i on the D3Q19 links of the finite-difference
 // scheme, 1 on the six D3Q7 links of the lattice-Boltzmann one; Janus
@@ -1802,13 +1803,6 @@ __global__ void __launch_bounds__(kTileThreads) kt_scalars(const __grid_constant
 }
 
 template <class C>
-__global__ void __launch_bounds__(kRowThreads) k_fdiv(DevParams P, DevPtrs D)
-{
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x < P.nx) fdiv_node<C>(P, D, x, blockIdx.y, blockIdx.z);
-}
-
-template <class C>
 __global__ void __launch_bounds__(kRowThreads, 8) k_collide(const __grid_constant__ DevParams P,
                                                              const __grid_constant__ DevPtrs D)
 {
@@ -1877,14 +1871,6 @@ __global__ void __launch_bounds__(kPartThreads) k_scalars_particles(const __grid
         if (lo != p + 1) continue;
         scalars_node<C>(P, D, x, y, z);
     }
-}
-
-template <class C>
-__global__ void __launch_bounds__(kRowThreads) k_scalars(const __grid_constant__ DevParams P,
-                                                          const __grid_constant__ DevPtrs D)
-{
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x < P.nx) scalars_node<C>(P, D, x, blockIdx.y, blockIdx.z);
 }
 
 template <class C>
