@@ -395,7 +395,8 @@ def lbb_run(b, nsteps: int) -> int:
 
 
 def lbb_tune(b, reps: int = 10):
-    """Autotune the node kernels; returns (configs[4], ms[4])."""
+    """Autotune the node kernels; returns the chosen candidate per kernel class
+    and its time in ms (four of each)."""
     cfg = (C.c_int * 4)()
     ms = np.zeros(4)
     _check(_lib.lbb_tune(b, int(reps), cfg, _dptr(ms)), "lbb_tune")
