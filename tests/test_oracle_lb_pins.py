@@ -137,3 +137,48 @@ def test_unknown_scheme_rejected():
     import pytest
     with pytest.raises(ValueError):
         Oracle(dict(nx=4, ny=4, nz=4, scalar_scheme=2))
+
+
+def test_lb_wall_bounce_back_is_zero_flux():
+    """At rest, halfway bounce-back of the D3Q7 distributions at a wall
+    returns what left: the update is the 7-point Laplacian with zero-flux
+    walls, whose modes cos(pi k (z + 1/2) / L) decay by exactly
+    1 + D 2 (cos(pi k / L) - 1) per step (D = C M_phi); the total stays."""
+    L, steps, Cc, Mphi = 16, 60, 0.0625, 1.6
+    o = Oracle(dict(nx=4, ny=3, nz=L, periodic=(1, 1, 0), C=Cc, M_phi=Mphi, k_d=0.0, **PASSIVE))
+    z = np.arange(L, dtype=float)
+    mode = np.cos(np.pi * 3 * (z + 0.5) / L)
+    phi0 = 1.0 + 0.5 * np.cos(np.pi * (z + 0.5) / L) + 0.25 * mode
+    o.set_fields(phi=np.ascontiguousarray(np.broadcast_to(phi0[:, None, None], (L, 3, 4))))
+    tot0 = o.conservation()[2]
+    o.step(steps)
+    g1 = 1.0 + Cc * Mphi * 2 * (np.cos(np.pi / L) - 1)
+    g3 = 1.0 + Cc * Mphi * 2 * (np.cos(3 * np.pi / L) - 1)
+    want = 1.0 + 0.5 * g1 ** steps * np.cos(np.pi * (z + 0.5) / L) + 0.25 * g3 ** steps * mode
+    got = o.fields()["phi"]
+    assert np.max(np.abs(got - want[:, None, None])) < 1e-12
+    assert abs(o.conservation()[2] - tot0) < 1e-11
+
+
+def test_lb_moving_wall_matches_comoving_fluid():
+    """A uniform solute in a fluid moving at U, with a sphere moving at the
+    same U: the moving-wall bounce-back hands back h*(x) - g c.U, which is
+    exactly what a fluid neighbour at velocity U would send, so phi stays
+    uniform over the fluid (covering shifts it as a whole, keeping the total);
+    a wrong sign or factor in the surface term leaves a ring around the
+    sphere."""
+    n = 16
+    U = np.array([0.02, -0.01, 0.015])
+    o = Oracle(dict(nx=n, ny=n, nz=n, A=0.0, kappa=0.0, E=0.0, phi_b=1.0, k_d=0.0, thermo_force=0,
+                    scalar_scheme=1))
+    u = np.broadcast_to(U[:, None, None, None], (3, n, n, n)).copy()
+    o.set_fields(u=u, phi=np.ones((n, n, n)))
+    o.add_particle(pos=(8.3, 7.9, 8.1), R=3.3, vel=tuple(U), fixed=1, alpha=0.0, mu_plus=0.0, mu_minus=0.0,
+                   theta_c_deg=90.0, m_hat=(0, 0, 1))
+    tot0 = o.conservation()[2]
+    for _ in range(4):
+        o.step(1)
+        fluid = o.mask() == 0
+        phi = o.fields()["phi"][fluid]
+        assert np.max(phi) - np.min(phi) < 1e-13
+        assert abs(o.conservation()[2] - tot0) < 1e-12 * n ** 3
