@@ -550,3 +550,24 @@ def test_capillary_restoring_force():
     assert abs(up + down) < 1e-9 * abs(up)
     rigid = 2 * math.pi * 0.0454 * 1.5
     assert 0.35 * rigid < abs(up) < 1.0 * rigid
+
+
+def test_surface_flux_matches_comoving_fluid():
+    """A uniform solute in a fluid moving at U past a sphere moving at U: the
+    advective flux into the surface, c.u_b g(x) (reading C7b), equals what
+    the donor-cell flux to a fluid neighbour moving at U would be, so phi
+    stays uniform over the fluid and its total stays; a dropped or
+    mis-signed surface flux leaves a ring around the sphere."""
+    n = 16
+    U = np.array([0.02, -0.01, 0.015])
+    o = Oracle(dict(nx=n, ny=n, nz=n, A=0.0, kappa=0.0, E=0.0, phi_b=1.0, k_d=0.0, thermo_force=0))
+    u = np.broadcast_to(U[:, None, None, None], (3, n, n, n)).copy()
+    o.set_fields(u=u, phi=np.ones((n, n, n)))
+    o.add_particle(pos=(8.3, 7.9, 8.1), R=3.3, vel=tuple(U), fixed=1, alpha=0.0, mu_plus=0.0, mu_minus=0.0,
+                   theta_c_deg=90.0, m_hat=(0, 0, 1))
+    tot0 = o.conservation()[2]
+    for _ in range(4):
+        o.step(1)
+        phi = o.fields()["phi"][o.mask() == 0]
+        assert np.max(phi) - np.min(phi) < 1e-13
+        assert abs(o.conservation()[2] - tot0) < 1e-12 * n ** 3
