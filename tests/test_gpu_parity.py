@@ -110,10 +110,10 @@ def test_driven_sphere_covering_fp64():
     assert abs(sg[1] - s0[1]) < 1e-9 and abs(sg[2] - s0[2]) < 1e-9
 
 
-def test_row_pipeline_walls_sphere_fp64():
-    """Rows of 48 nodes (whole 16-byte runs) take the pipelined collide-stream
-    kernel: walls in x (the wrapped shared-memory index must not be used) and
-    z, several rows per block so the stage ring wraps, a driven sphere."""
+def test_walls_in_x_and_z_driven_sphere_fp64():
+    """Walls on two axes (bounce-back links replaced in the bulk collide, the
+    clamped source index never used), a box larger than one block in every
+    direction, and a driven sphere covering and uncovering nodes."""
     nx, ny, nz = 48, 40, 72
     params = dict(W.BASE_PARAMS, nx=nx, ny=ny, nz=nz, periodic=(0, 1, 0), E=0.2, M_psi=0.2, k_d=1e-3,
                   body_force=(2e-5, 0.0, -1e-5))
