@@ -3,10 +3,13 @@
 
 A step is one full pass of the coupled update (chemical potentials, collide-
 stream with particle bounce-back, psi/phi transport, particle update,
-covering) over the 128^3 single-particle interface workload (one Janus sphere
-R=8 straddling a flat interface, contact angle 60 degrees, solubility ratio 2,
-phoretic mobility 0.1), FP32 arithmetic and storage.  Inputs are synthetic
-and seeded; the state (0.4 GB) is larger than L2, so no L2 flush is needed.
+covering).  The default workload is the 256^3 eight-sphere box (spheres R=6
+at seeded positions in the slab 20 < z < 60 below a flat interface at
+z=128, tanh width 2, contact angle 90 degrees, phoretic mobility 0.1, cap
+production 1e-3), FP32 arithmetic and storage; ``--precision fp16``/``bf16``
+stores the populations as 16-bit deviations, ``--workload interface`` runs
+the 128^3 single-sphere interface box instead.  Inputs are synthetic and
+seeded; the state (several GB) is larger than L2, so no L2 flush is needed.
 
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle (the
 reference implementation written from the paper) on the host cores instead.
@@ -42,10 +45,9 @@ import numpy as np  # noqa: E402
 # algorithmic bytes per node and step (populations read+write, psi/phi
 # read+write): FP32 19*4*2 + 2*4*2
 ALG_BYTES_STEP = {"fp64": 336, "fp32": 168, "fp16": 92, "bf16": 92}
-# algorithmic bytes per node of the collide-stream kernel: populations
-# read+write and psi, phi read
-ALG_BYTES_COLLIDE = {"fp64": 19 * 8 * 2 + 16, "fp32": 19 * 4 * 2 + 8, "fp16": 19 * 2 * 2 + 8,
-                     "bf16": 19 * 2 * 2 + 8}
+# algorithmic bytes per node of the collide-stream kernel: the populations it
+# reads and writes (the part of the step's algorithmic bytes it carries)
+ALG_BYTES_COLLIDE = {"fp64": 19 * 8 * 2, "fp32": 19 * 4 * 2, "fp16": 19 * 2 * 2, "bf16": 19 * 2 * 2}
 # algorithmic bytes per node of the tiled transport kernel: psi, phi, mu_psi,
 # mu_phi, u read, psi, phi written
 ALG_BYTES_SCALARS = {"fp64": 9 * 8, "fp32": 9 * 4, "fp16": 9 * 4, "bf16": 9 * 4}
@@ -60,7 +62,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
-    ap.add_argument("--edge", type=int, default=128)
+    ap.add_argument("--workload", default="precision", choices=["precision", "interface"],
+                    help="precision: 256^3, 8 spheres R=6 below an interface; interface: 128^3, one "
+                         "sphere R=8 straddling it")
+    ap.add_argument("--edge", type=int, default=0, help="box edge (default 256 / 128 by workload)")
     ap.add_argument("--scalar-scheme", type=int, default=0, choices=[0, 1],
                     help="psi/phi transport: 0 finite differences, 1 D3Q7 lattice Boltzmann")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -71,9 +76,25 @@ def parse():
     return ap.parse_args()
 
 
-def workload(edge, scalar_scheme=0):
+# physical settings of each bench workload (reported in the JSON config)
+WORKLOAD_SETTINGS = {
+    "precision": {"theta_c_deg": 90.0, "solubility_ratio": 1.0, "mobility": 0.1, "spheres": "8 x R=6",
+                  "default_edge": 256},
+    "interface": {"theta_c_deg": 60.0, "solubility_ratio": 2.0, "mobility": 0.1, "spheres": "1 x R=8",
+                  "default_edge": 128},
+}
+
+
+def edge_of(args):
+    return args.edge if args.edge > 0 else WORKLOAD_SETTINGS[args.workload]["default_edge"]
+
+
+def workload(kind, edge, scalar_scheme=0):
     from paper_2202_01631_gb300 import workloads as W
-    wl = W.interface(theta_c_deg=60.0, solubility_ratio=2.0, mobility=0.1, seed=0, edge=edge)
+    if kind == "precision":
+        wl = W.precision(seed=0, edge=edge)
+    else:
+        wl = W.interface(theta_c_deg=60.0, solubility_ratio=2.0, mobility=0.1, seed=0, edge=edge)
     if scalar_scheme:
         wl.params = dict(wl.params, scalar_scheme=scalar_scheme)
     return wl
@@ -116,23 +137,89 @@ def max_over_ranks(value, group):
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    """SM clock and clock-event (throttle) reasons sampled during a region.
 
+    Polls NVML through ctypes every 2 ms (the timed region of a short run
+    lasts tens of milliseconds); falls back to ``nvidia-smi -lms 20`` where
+    the NVML library cannot be loaded.  Reading clocks changes nothing.
+    """
+
+    # NVML clock-event reason bits (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
-        self.index = index
+    def __init__(self, index, period_s=0.002):
+        self.index = self._nvml_index(index)
+        self.period = period_s
+        self.samples = []          # (sm_mhz, reason bits)
+        self.max_mhz = None
+        self.source = None
         self.proc = None
         self.lines = []
+        self._stop = threading.Event()
+        self._nvml = None
+
+    @staticmethod
+    def _nvml_index(local):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if ids and local < len(ids) and ids[local].isdigit():
+            return int(ids[local])
+        return local
+
+    def _open_nvml(self):
+        import ctypes
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                lib = ctypes.CDLL(name)
+                break
+            except OSError:
+                lib = None
+        if lib is None or lib.nvmlInit_v2() != 0:
+            return False
+        h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) != 0:
+            return False
+        mx = ctypes.c_uint(0)
+        if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:   # NVML_CLOCK_SM
+            self.max_mhz = float(mx.value)
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None)
+        self._nvml = (ctypes, lib, h, reasons)
+        return True
+
+    def _poll(self):
+        ctypes, lib, h, reasons = self._nvml
+        clk = ctypes.c_uint(0)
+        bits = ctypes.c_ulonglong(0)
+        while not self._stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0:
+                r = 0
+                if reasons is not None and reasons(h, ctypes.byref(bits)) == 0:
+                    r = bits.value
+                self.samples.append((float(clk.value), r))
+            time.sleep(self.period)
 
     def __enter__(self):
         try:
+            ok = self._open_nvml()
+        except (OSError, AttributeError):
+            ok = False
+        if ok:
+            self.source = "nvml %.0f ms" % (self.period * 1e3)
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+            time.sleep(3 * self.period)   # first samples before the region starts
+            return self
+        try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi 20 ms"
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, FileNotFoundError):
@@ -144,6 +231,9 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *a):
+        self._stop.set()
+        if self._nvml is not None:
+            self.t.join(timeout=1.0)
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -152,7 +242,14 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        sm, reasons = [], set()
+        mx = self.max_mhz
+        if self._nvml is not None:
+            for mhz, bits in self.samples:
+                sm.append(mhz)
+                for b, nm in self.REASONS.items():
+                    if bits & b:
+                        reasons.add(nm)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for l in self.lines:
             parts = [p.strip() for p in l.split(",")]
@@ -167,9 +264,9 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0, "source": self.source}
+        return {"sm_mhz": statistics.median(sm), "sm_min_mhz": min(sm), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm), "source": self.source}
 
 
 def measured_peak():
@@ -182,7 +279,7 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def traffic_record(kernel, precision, edge):
+def traffic_record(kernel, precision, workload_name):
     """DRAM bytes per launch of a kernel from the committed ncu summary, valid
     only while the kernel sources are unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -193,7 +290,7 @@ def traffic_record(kernel, precision, edge):
         return None
     src = source_hash()
     for r in recs:
-        if (r.get("kernel") == kernel and r.get("precision") == precision and r.get("edge") == edge
+        if (r.get("kernel") == kernel and r.get("precision") == precision and r.get("workload") == workload_name
                 and r.get("source_sha") == src):
             return float(r["bytes_per_launch"])
     return None
@@ -218,64 +315,95 @@ def build_box(wl, precision, stream):
     return box
 
 
-def cpu_baseline(wl, budget_s=12.0):
-    """The FP64 oracle as it stands on the host, on a bounded number of steps
-    of the same workload."""
+def _oracle_for(wl):
     from oracle.lbref import Oracle
     ref = Oracle(wl.params)
     ref.set_fields(**wl.fields)
     for p in wl.particles:
         ref.add_particle(**p)
+    return ref
+
+
+def _time_oracle(ref, budget_s, max_steps=20):
+    """One untimed step, then as many steps as fit in budget_s (at least one,
+    at most max_steps); returns (steps, seconds)."""
     t0 = time.perf_counter()
     ref.step(1)
-    t1 = time.perf_counter()
-    per = t1 - t0
-    k = max(1, min(20, int(budget_s / max(per, 1e-6))))
+    per = time.perf_counter() - t0
+    k = max(1, min(max_steps, int(budget_s / max(per, 1e-6))))
     t0 = time.perf_counter()
     ref.step(k)
-    dt = time.perf_counter() - t0
-    return {"value": wl.nodes * k / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%d steps of the %d^3 workload (after 1 untimed step), FP64, 1 thread"
-                      % (k, wl.params["nx"])}
+    return k, time.perf_counter() - t0
+
+
+def cpu_baseline(wl, budget_s=10.0):
+    """The FP64 oracle as it stands on the host cores, on a bounded number of
+    steps of the same workload: all cores (the reported figure) and one
+    thread (alongside)."""
+    from oracle import lbref
+    ref = _oracle_for(wl)
+    cores = lbref.set_threads(0)
+    k, dt = _time_oracle(ref, budget_s)
+    lbref.set_threads(1)
+    k1, dt1 = _time_oracle(ref, budget_s)
+    lbref.set_threads(0)
+    edge = "%dx%dx%d" % (wl.params["nx"], wl.params["ny"], wl.params["nz"])
+    return {"value": wl.nodes * k / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "nproc": os.cpu_count(),
+            "sample": "%d steps of the %s workload (after 1 untimed step), FP64, %d threads"
+                      % (k, edge, cores),
+            "single_thread": {"value": wl.nodes * k1 / dt1 / 1e6, "unit": "MLUPS", "cores": 1,
+                              "sample": "%d steps of the same box (after 1 untimed step), FP64, 1 thread"
+                                        % k1}}
 
 
 def run_reference(args):
+    """The FP64 oracle written from the paper (the paper ships no code) on the
+    host cores, on the same workload as our arm: W warm-up steps (at most
+    one) and K timed steps, bounded so that the run ends within about three
+    minutes (the sample is stated in the line)."""
     world, rank, local, group = dist_setup(args)
     if rank != 0:
         return 0
-    from oracle.lbref import Oracle
-    from paper_2202_01631_gb300 import workloads as W
-    wl_full = workload(args.edge)
-    # each step of this arm is one oracle step on a box scaled so that the
-    # whole run stays within about two minutes
-    t_node = 1.2e-6
-    budget = 120.0 / max(args.steps + args.warmup, 1)
-    edge = int(max(16, min(args.edge, round((budget / t_node) ** (1 / 3)))))
-    edge -= edge % 2
-    wl = W.interface(theta_c_deg=60.0, solubility_ratio=2.0, mobility=0.1, seed=0, edge=edge)
-    ref = Oracle(wl.params)
-    ref.set_fields(**wl.fields)
-    for p in wl.particles:
-        ref.add_particle(**p)
-    ref.step(args.warmup)
+    from oracle import lbref
+    wl = workload(args.workload, edge_of(args))
+    ref = _oracle_for(wl)
+    cores = lbref.set_threads(0)
     t0 = time.perf_counter()
-    ref.step(args.steps)
+    ref.step(1 if args.warmup > 0 else 0)
+    per = max(time.perf_counter() - t0, 1e-6) if args.warmup > 0 else None
+    if per is None:
+        t0 = time.perf_counter()
+        ref.step(1)
+        per = max(time.perf_counter() - t0, 1e-6)
+    k = max(1, min(args.steps, int(150.0 / per)))
+    t0 = time.perf_counter()
+    ref.step(k)
     dt = time.perf_counter() - t0
-    mlups = wl.nodes * args.steps / dt / 1e6
+    mlups = wl.nodes * k / dt / 1e6
+    edge = "%dx%dx%d" % (wl.params["nx"], wl.params["ny"], wl.params["nz"])
+    sample = ("%d of the %d requested steps of the %s workload after %d warm-up step (FP64 oracle, %d threads)"
+              % (k, args.steps, edge, min(args.warmup, 1), cores))
     line = {
         "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / max(args.steps, 1) * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / k * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": wl_full.name, "sample_edge": edge, "precision": "fp64",
-                   "particles": len(wl.particles)},
-        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": "%d steps of the workload scaled to %d^3 (FP64 oracle, 1 thread)"
-                                   % (args.steps, edge)},
+        "config": dict(workload_config(args, wl), precision="fp64", timed_steps=k),
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "nproc": os.cpu_count(), "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def workload_config(args, wl):
+    st = WORKLOAD_SETTINGS[args.workload]
+    return {"workload": wl.name, "nodes": wl.nodes, "particles": len(wl.particles),
+            "spheres": st["spheres"], "theta_c_deg": st["theta_c_deg"],
+            "solubility_ratio": st["solubility_ratio"], "mobility": st["mobility"],
+            "scalar_scheme": args.scalar_scheme}
 
 
 def run_ours(args):
@@ -288,7 +416,7 @@ def run_ours(args):
     build.build()
     from paper_2202_01631_gb300 import lbdp
 
-    wl = workload(args.edge, args.scalar_scheme)
+    wl = workload(args.workload, edge_of(args), args.scalar_scheme)
     N = wl.nodes
     stream = torch.cuda.Stream()
     box = build_box(wl, args.precision, stream.cuda_stream)
@@ -361,16 +489,14 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
-    traffic = traffic_record(coll_name, args.precision, args.edge)
+    traffic = traffic_record(coll_name, args.precision, wl.name)
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
-        "config": {"workload": wl.name, "nodes": N, "precision": args.precision,
-                   "particles": len(wl.particles), "theta_c_deg": 60.0, "solubility_ratio": 2.0,
-                   "mobility": 0.1, "scalar_scheme": args.scalar_scheme,
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "state %.2f GB > L2 (129 MB); no flush" % (lbdp.lb_device_bytes(box.params) / 1e9)},
+        "config": dict(workload_config(args, wl), precision=args.precision,
+                       parallelism="replicas" if world > 1 else "single",
+                       l2="state %.2f GB > L2 (129 MB); no flush" % (lbdp.lb_device_bytes(box.params) / 1e9)),
         "roofline": {"bound": "hbm", "kernel": coll_name, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": traffic,

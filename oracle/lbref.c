@@ -27,12 +27,21 @@
  * Built with -ffp-contract=off so that no multiply-add is fused; the
  * geometric decisions (solid or fluid, active or inactive) are then taken with
  * exactly the products and sums written here.
+ *
+ * Threads (OpenMP, when the compiler has it): the node loops whose nodes are
+ * independent run in parallel over z.  Every sum over nodes (particle link
+ * sums, the flux into the moving surfaces, covering) is taken by one thread in
+ * the node order x fastest, then y, then z, so the result is bit-identical for
+ * any thread count.
  */
 #include "lbref.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define REF_MAXP 255
 
@@ -68,6 +77,7 @@ struct ref_sim {
     double *psi, *phi, *mupsi, *muphi, *u, *psin, *phin;
     double* pt;   /* [6][N] chemical pressure tensor xx yy zz xy xz yz */
     unsigned char *mask, *maskn;
+    unsigned char* lk;   /* [N] 1: fluid node with a particle neighbour (work flags) */
     int np;
     ref_part part[REF_MAXP];
     long nfluid;
@@ -215,6 +225,7 @@ static void step_mu(ref_sim* s)
 {
     const ref_params* p = &s->p;
     const long N = s->N;
+#pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
@@ -296,6 +307,26 @@ static void pt_dot(const ref_sim* s, long n, const double c[3], double out[3])
 /* S5 + S6a: momentum exchange sums and the implicit velocity update   */
 /* ------------------------------------------------------------------ */
 
+/* lk[n] = 1 for the fluid nodes with a neighbour inside a particle (the nodes
+ * whose links the sums below visit, in node order). */
+static void mark_particle_neighbours(ref_sim* s)
+{
+    const ref_params* p = &s->p;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long n = nidx(s, x, y, z);
+                unsigned char f = 0;
+                if (!s->mask[n])
+                    for (int i = 1; i < 19 && !f; ++i) {
+                        long m = nbr(s, x, y, z, CX[i], CY[i], CZ[i]);
+                        f = (unsigned char)(m >= 0 && s->mask[m]);
+                    }
+                s->lk[n] = f;
+            }
+}
+
 /* Gaussian elimination with partial pivoting on a 6x6 system. */
 static int solve6(double A[6][6], double b[6], double x[6])
 {
@@ -347,11 +378,12 @@ static void step_links(ref_sim* s)
         memset(P->zeta, 0, sizeof(P->zeta));
     }
     if (s->np == 0) return;
+    mark_particle_neighbours(s);
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
                 long n = nidx(s, x, y, z);
-                if (s->mask[n]) continue;
+                if (!s->lk[n]) continue;
                 for (int i = 1; i < 19; ++i) {
                     long m = nbr(s, x, y, z, CX[i], CY[i], CZ[i]);
                     if (m < 0 || !s->mask[m]) continue;
@@ -424,6 +456,7 @@ static void step_collide(ref_sim* s)
 {
     const ref_params* p = &s->p;
     const long N = s->N;
+#pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
@@ -519,6 +552,7 @@ static void step_scalars(ref_sim* s)
     const long N = s->N;
     s->wall_psi = 0.0;
     s->wall_phi = 0.0;
+#pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
@@ -552,8 +586,6 @@ static void step_scalars(ref_sim* s)
                         double aps = cub * ps, aph = cub * ph;
                         dps += W[i] * (0.0 - aps);
                         dph += W[i] * (0.0 - aph);
-                        s->wall_psi += 6.0 * W[i] * aps;
-                        s->wall_phi += 6.0 * W[i] * aph;
                         continue;
                     }
                     double cu0 = CX[i] * u0[0] + CY[i] * u0[1] + CZ[i] * u0[2];
@@ -578,6 +610,29 @@ static void step_scalars(ref_sim* s)
                 }
                 s->phin[n] = pn;
             }
+    /* what the moving surfaces carried out of the fluid, summed in node and
+     * link order (the same advective fluxes as above) */
+    if (s->np > 0) {
+        mark_particle_neighbours(s);
+        for (int z = 0; z < p->nz; ++z)
+            for (int y = 0; y < p->ny; ++y)
+                for (int x = 0; x < p->nx; ++x) {
+                    long n = nidx(s, x, y, z);
+                    if (!s->lk[n]) continue;
+                    double ps = s->psi[n], ph = s->phi[n];
+                    for (int i = 1; i < 19; ++i) {
+                        long m = nbr(s, x, y, z, CX[i], CY[i], CZ[i]);
+                        if (m < 0 || !s->mask[m]) continue;
+                        const ref_part* P = &s->part[s->mask[m] - 1];
+                        double r[3], ub[3], vs[3];
+                        link_velocity(s, P, x, y, z, i, r, ub, vs);
+                        double cub = CX[i] * ub[0] + CY[i] * ub[1] + CZ[i] * ub[2];
+                        double aps = cub * ps, aph = cub * ph;
+                        s->wall_psi += 6.0 * W[i] * aps;
+                        s->wall_phi += 6.0 * W[i] * aph;
+                    }
+                }
+    }
     double* t = s->psi;
     s->psi = s->psin;
     s->psin = t;
@@ -613,6 +668,7 @@ static void step_scalars_lb(ref_sim* s)
     /* collision (relaxation time 1: the post-collision populations are the
      * equilibrium), with the sink and the Janus production added to the rest
      * population of phi */
+#pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
@@ -647,6 +703,7 @@ static void step_scalars_lb(ref_sim* s)
     /* pull streaming: from the fluid node x - c_i; halfway bounce-back from a
      * wall; from a particle, moving-wall bounce-back that carries g c.u_b into
      * the surface (c the direction from x into the particle) */
+#pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
@@ -679,8 +736,6 @@ static void step_scalars_lb(ref_sim* s)
                             /* 2 w_j g c_j.u_b / c_s^2 = g c_j.u_b */
                             a = s->hs[j * N + n] - s->psi[n] * cub;
                             b = s->hs[(7 + j) * N + n] - s->phi[n] * cub;
-                            s->wall_psi += s->psi[n] * cub;
-                            s->wall_phi += s->phi[n] * cub;
                         }
                     }
                     s->h[i * N + n] = a;
@@ -691,6 +746,28 @@ static void step_scalars_lb(ref_sim* s)
                 s->psin[n] = sp;
                 s->phin[n] = sh;
             }
+    /* what the moving surfaces carried out of the fluid, in node and link
+     * order (the same terms as the particle links above) */
+    if (s->np > 0) {
+        mark_particle_neighbours(s);
+        for (int z = 0; z < p->nz; ++z)
+            for (int y = 0; y < p->ny; ++y)
+                for (int x = 0; x < p->nx; ++x) {
+                    long n = nidx(s, x, y, z);
+                    if (!s->lk[n]) continue;
+                    for (int i = 1; i < 7; ++i) {
+                        const int j = opp(i);
+                        long m = nbr(s, x, y, z, CX[j], CY[j], CZ[j]);
+                        if (m < 0 || !s->mask[m]) continue;
+                        const ref_part* P = &s->part[s->mask[m] - 1];
+                        double r[3], ub[3], vs[3];
+                        link_velocity(s, P, x, y, z, j, r, ub, vs);
+                        double cub = CX[j] * ub[0] + CY[j] * ub[1] + CZ[j] * ub[2];
+                        s->wall_psi += s->psi[n] * cub;
+                        s->wall_phi += s->phi[n] * cub;
+                    }
+                }
+    }
     double* t = s->psi;
     s->psi = s->psin;
     s->psin = t;
@@ -758,6 +835,7 @@ static void step_cover(ref_sim* s)
     const ref_params* p = &s->p;
     const long N = s->N;
     if (s->np == 0) return;
+#pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) s->maskn[nidx(s, x, y, z)] = owner(s, x, y, z);
@@ -850,6 +928,7 @@ static void step_cover(ref_sim* s)
      * amount (covering, uncovering and the flux into the moving surfaces)
      * uniformly over every fluid node */
     double cps = dpsi / (double)s->nfluid, cph = dphi / (double)s->nfluid;
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
         if (s->mask[n]) continue;
         s->psi[n] += cps;
@@ -886,8 +965,9 @@ ref_sim* ref_create(const ref_params* p)
     s->u = (double*)calloc((size_t)(3 * N), sizeof(double));
     s->mask = (unsigned char*)calloc((size_t)N, 1);
     s->maskn = (unsigned char*)calloc((size_t)N, 1);
+    s->lk = (unsigned char*)calloc((size_t)N, 1);
     if (!s->f || !s->fn || !s->psi || !s->phi || !s->psin || !s->phin || !s->mupsi || !s->muphi ||
-        !s->u || !s->mask || !s->maskn || !s->pt) {
+        !s->u || !s->mask || !s->maskn || !s->lk || !s->pt) {
         ref_destroy(s);
         return NULL;
     }
@@ -923,6 +1003,7 @@ void ref_destroy(ref_sim* s)
     free(s->u);
     free(s->mask);
     free(s->maskn);
+    free(s->lk);
     free(s->h);
     free(s->hs);
     free(s);
@@ -1080,6 +1161,18 @@ int ref_conservation(const ref_sim* s, double sums[3])
 }
 
 int ref_error(const ref_sim* s) { return s->err; }
+
+int ref_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n < 1) n = omp_get_num_procs();
+    omp_set_num_threads(n);
+    return n;
+#else
+    (void)n;
+    return 1;
+#endif
+}
 long ref_fluid_count(const ref_sim* s) { return s->nfluid; }
 
 /* cos(theta_c) = [(1+h)^{3/2} - (1-h)^{3/2}] / 2 (Sec. Particles, wetting);

@@ -70,6 +70,9 @@ int  ref_read_particles(const ref_sim* s, ref_particle_state* out, int cap);
 int  ref_conservation(const ref_sim* s, double sums[3]);
 int  ref_error(const ref_sim* s);
 long ref_fluid_count(const ref_sim* s);
+/* threads of the node loops (0: all cores); returns the count in use, 1
+ * without OpenMP.  Results are bit-identical for any count. */
+int  ref_set_threads(int n);
 /* contact angle (degrees) -> h = H / sqrt(kappa A) by bisection */
 double ref_wetting_h(double theta_deg);
 

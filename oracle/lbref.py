@@ -5,7 +5,9 @@ the CUDA library is checked against.  Only ``tests/``, the smoke check and the
 CPU-baseline leg of the benchmark import this module; the library never does.
 
 The C source is compiled on first use with ``gcc -O2 -ffp-contract=off`` (no
-fused multiply-adds, so the oracle gives the same bits on x86_64 and aarch64).
+fused multiply-adds, so the oracle gives the same bits on x86_64 and aarch64),
+with ``-fopenmp`` where the compiler supports it: ``set_threads`` then runs
+the independent node loops on several cores, with bit-identical results.
 """
 from __future__ import annotations
 
@@ -67,7 +69,9 @@ def build(force: bool = False) -> str:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off",
                "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        r = subprocess.run(cmd[:-1] + ["-fopenmp", "-lm"], capture_output=True, text=True)
+        if r.returncode != 0:   # no OpenMP runtime: one thread
+            subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
         return _LIB_PATH
 
@@ -94,6 +98,8 @@ def _load():
     lib.ref_error.argtypes = [C.c_void_p]
     lib.ref_fluid_count.argtypes = [C.c_void_p]
     lib.ref_fluid_count.restype = C.c_long
+    lib.ref_set_threads.argtypes = [C.c_int]
+    lib.ref_set_threads.restype = C.c_int
     lib.ref_wetting_h.argtypes = [C.c_double]
     lib.ref_wetting_h.restype = C.c_double
     _lib = lib
@@ -104,6 +110,12 @@ def _ptr(a):
     if a is None:
         return None
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's node loops (0: all cores); returns the count in
+    use (1 when the oracle was built without OpenMP)."""
+    return int(_load().ref_set_threads(int(n)))
 
 
 def wetting_h(theta_deg: float) -> float:

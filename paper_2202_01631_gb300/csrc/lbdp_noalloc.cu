@@ -71,14 +71,26 @@ __global__ void __launch_bounds__(kThreads) k_totals_partial(long long N, const 
     }
 }
 
-// Pass 2: one thread adds the partials in block order into out[3].
-__global__ void k_totals_final(const double* part, int nblocks, double* out)
+// Pass 2: one 256-thread block adds the partials in a fixed order: thread t
+// sums blocks t, t + 256, t + 512, ... in turn, then a tree over the threads
+// (pairs at distance 128, 64, ..., 1) gives out[3].  The order depends only
+// on the block count, so every call gives the same bits for the same inputs.
+constexpr int kFinalThreads = 256;
+__global__ void __launch_bounds__(kFinalThreads) k_totals_final(const double* part, int nblocks, double* out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double sm[3][kFinalThreads];
+    const int t = threadIdx.x;
     double s[3] = {0.0, 0.0, 0.0};
-    for (int b = 0; b < nblocks; ++b)
+    for (int b = t; b < nblocks; b += kFinalThreads)
         for (int c = 0; c < 3; ++c) s[c] += part[3 * b + c];
-    for (int c = 0; c < 3; ++c) out[c] = s[c];
+    for (int c = 0; c < 3; ++c) sm[c][t] = s[c];
+    __syncthreads();
+    for (int h = kFinalThreads / 2; h > 0; h >>= 1) {
+        if (t < h)
+            for (int c = 0; c < 3; ++c) sm[c][t] += sm[c][t + h];
+        __syncthreads();
+    }
+    if (t < 3) out[t] = sm[t][0];
 }
 
 // Device address of the scratch array on the current device, looked up once
@@ -115,12 +127,15 @@ extern "C" int lb_totals_noalloc(int precision, int nx, int ny, int nz, const vo
     if (st != LB_OK) return st;
     const int nblocks = (int)((N + kNodesPerBlock - 1) / kNodesPerBlock);
     cudaStream_t s = (cudaStream_t)stream;
-    if (precision == LB_FP64)
-        k_totals_partial<double><<<nblocks, kThreads, 0, s>>>(N, (const double*)f, (const double*)psi,
-                                                               (const double*)phi, mask, part);
-    else
-        k_totals_partial<float><<<nblocks, kThreads, 0, s>>>(N, (const float*)f, (const float*)psi,
-                                                              (const float*)phi, mask, part);
-    k_totals_final<<<1, 32, 0, s>>>(part, nblocks, sums);
-    return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ERR_CUDA;
+    // cudaLaunchKernel reports the status of this launch itself, not an error
+    // some earlier, unrelated call left behind on the thread
+    void* pargs[] = {(void*)&N, (void*)&f, (void*)&psi, (void*)&phi, (void*)&mask, (void*)&part};
+    const void* fn = precision == LB_FP64 ? (const void*)k_totals_partial<double>
+                                          : (const void*)k_totals_partial<float>;
+    if (cudaLaunchKernel(fn, dim3(nblocks), dim3(kThreads), pargs, 0, s) != cudaSuccess) return LB_ERR_CUDA;
+    const double* cpart = part;
+    void* fargs[] = {(void*)&cpart, (void*)&nblocks, (void*)&sums};
+    if (cudaLaunchKernel((const void*)k_totals_final, dim3(1), dim3(kFinalThreads), fargs, 0, s) != cudaSuccess)
+        return LB_ERR_CUDA;
+    return LB_OK;
 }
