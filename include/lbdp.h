@@ -75,8 +75,14 @@ typedef struct {
     int periodic[3];        /* 1 periodic; 0 halfway bounce-back walls at
                                -1/2 and n-1/2 with neutral wetting          */
     int precision;          /* LB_FP64 ... LB_BF16_SHIFT                    */
-    int thermo_force;       /* 1 (default model): fluid force
-                               -psi grad mu_psi - phi grad mu_phi;
+    int thermo_force;       /* 1 (default model): fluid force g - div P,
+                               P the pressure tensor of the free energy
+                               (Eq. free_energy), in link form
+                               -6 sum_i w_i [(P(x) + P(x+c_i))/2] . c_i with
+                               P(x) standing in at solid and wall
+                               neighbours; its continuum value is
+                               -psi grad mu_psi - phi grad mu_phi, and each
+                               boundary link hands a particle 6 w_i P(x).c_i;
                                0: psi and phi are passive scalars           */
     double tau, rho0;       /* BGK relaxation time (> 1/2), reference density */
     double body_force[3];   /* uniform force density g on the fluid         */
@@ -154,12 +160,14 @@ int lb_step(lb_handle* h, int nsteps);
 /* Run nsteps steps like lb_step, but with every kernel on the handle's stream
  * in sequence and a CUDA event recorded between kernel classes; wait, and add
  * each class's time in milliseconds to ms[0..4]:
- *   0 chemical potentials, pressure tensor and force;
- *   1 particle links and velocity update, then the collide-stream of the
- *     fluid nodes next to particles;
- *   2 collide-stream of all other fluid nodes (one kernel);
- *   3 psi/phi transport of the fluid nodes not next to particles (one kernel);
- *   4 psi/phi transport next to particles, then covering/uncovering.
+ *   0 the particle kernels before the bulk: pressure tensor and force at the
+ *     fluid nodes next to particles, particle links and velocity update,
+ *     collide-stream of the fluid nodes next to particles;
+ *   1 chemical potentials, pressure tensor, force and collide-stream of all
+ *     other fluid nodes (one fused kernel);
+ *   2 psi/phi transport of the fluid nodes not next to particles (one kernel);
+ *   3 psi/phi transport of the fluid nodes next to particles;
+ *   4 covering/uncovering.
  * *launches (may be NULL) receives the number of kernels launched.  The
  * events add a little host overhead, so time throughput with lb_step; this
  * call is for the split. */

@@ -72,7 +72,7 @@ size_t layout(const lb_params* p, const PrecOps* ops, int red_blocks, lb_handle*
     t->muphi = take(N * fb);
     t->u = take(3 * N * fb);
     t->force = take(3 * N * fb);
-    t->pt = take(6 * N * fb);
+    t->pt = take(kPtFields * N * fb);
     t->bflag = (uint8_t*)take(N);
     t->parts = (DevPart*)take(kMaxParticles * sizeof(DevPart));
     t->corr = (double*)take(8 * sizeof(double));   // [step parity][psi, phi FP64; psi, phi FP32]
@@ -144,10 +144,18 @@ DevPtrs cur_ptrs(const lb_handle* h)
 RowGrid row_grid(const DevParams& P)
 {
     RowGrid g;
-    int bx = P.nx >= 128 ? 128 : ((P.nx + 31) / 32) * 32;
-    g.block = dim3(bx, 1, 1);
-    g.grid = dim3((P.nx + bx - 1) / bx, P.ny, P.nz);
-    g.tiles = dim3((P.nx + 31) / 32, (P.ny + 3) / 4, (P.nz + 3) / 4);
+    // z-marching kernels: enough z chunks for about eight waves of two blocks
+    // per SM on 152 SMs, each chunk at least 8 planes long
+    const long long cols = (long long)((P.nx + 31) / 32) * ((P.ny + 7) / 8);
+    const long long target = 152LL * 2 * 8;
+    long long chunks = (target + cols - 1) / cols;
+    const long long max_chunks = P.nz / 8 > 1 ? P.nz / 8 : 1;
+    if (chunks > max_chunks) chunks = max_chunks;
+    if (chunks < 1) chunks = 1;
+    // no empty chunk: ceil(nz / chunks) planes each
+    const int zc = (int)((P.nz + chunks - 1) / chunks);
+    chunks = (P.nz + zc - 1) / zc;
+    g.zgrid = dim3((P.nx + 31) / 32, (P.ny + 7) / 8, (unsigned)chunks);
     return g;
 }
 
@@ -410,14 +418,14 @@ int lb_profile_step(lb_handle* h, int nsteps, double* ms, int* launches)
             ms[k] += v;
         }
     for (auto& e : ev) cudaEventDestroy(e);
-    if (launches) *launches = nsteps * (h->dp.np > 0 ? 9 : 4);
+    if (launches) *launches = nsteps * (h->dp.np > 0 ? 9 : 2);
     return st;
 }
 
 int lb_step_launches(const lb_handle* h, int nsteps)
 {
     if (!h || nsteps < 0) return LB_ERR_PARAM;
-    return nsteps * (h->dp.np > 0 ? 9 : 4);
+    return nsteps * (h->dp.np > 0 ? 9 : 2);
 }
 
 int lb_sync(lb_handle* h)
@@ -666,7 +674,7 @@ int lb_create_in(const lb_params* p, lbb_batch* batch, void* region, lb_handle**
     if (e == cudaSuccess) e = cudaMemsetAsync(h->link_ticket, 0, kMaxParticles * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->cover_ticket, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->force, 0, 3 * N * fb, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->pt, 0, 6 * N * fb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->pt, 0, kPtFields * N * fb, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->bflag, 0, N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->u, 0, 3 * N * fb, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->mupsi, 0, N * fb, s);

@@ -110,7 +110,7 @@ template <class C, int NC>
 __global__ void __launch_bounds__(kTileThreads) kb_tiled(const __grid_constant__ BoxLaunch L)
 {
     using F = typename C::fld_t;
-    constexpr int NF = NC == kNcFdiv ? 6 : 7;
+    constexpr int NF = NC == kNcFdiv ? kPtFields : 7;
     extern __shared__ __align__(16) unsigned char smem_raw[];   // tile_smem<F, NF>()
     F* sf = (F*)smem_raw;
     uint8_t* sm = (uint8_t*)(sf + NF * Tile::slots);

@@ -13,14 +13,16 @@ struct lbb_batch;
 
 namespace lbdp {
 
-// Launch geometry of the row kernels: one thread per node, blocks along x.
+// Launch geometry of the bulk kernels of one box.
 struct RowGrid {
-    dim3 grid, block;
-    dim3 tiles;   // grid of the 32 x 4 x 4 tiled kernels
+    dim3 zgrid;   // grid of the z-marching kernels: 32 x 8 column tiles x z chunks
 };
 
-// Kernel classes of one step, in launch order.
-enum KernelClass { kKMu = 0, kKLinks, kKCollide, kKScalars, kKCover, kNumKernelClasses };
+// Kernel classes of one step, in the order of the sequential profile: the
+// particle kernels before the bulk (pressure tensor and force next to the
+// particles, link sums and particle update, boundary collide-stream), the
+// fused bulk kernel, the bulk transport, the boundary transport, covering.
+enum KernelClass { kKParticles = 0, kKFused, kKScalars, kKScalarsParticles, kKCover, kNumKernelClasses };
 
 // A second stream for the particle kernels of a step: k_links (which needs
 // only mu/P and the populations) and k_cover_mark run there while the force,

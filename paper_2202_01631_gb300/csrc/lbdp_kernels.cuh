@@ -1,28 +1,29 @@
-// lbdp_kernels.cuh -- the per-step kernels of the lattice update, templated on
-// the precision configuration.  One step is
-//   k_mup          one thread per node: chemical potentials (Eq.
-//                  chem_potentials, wetting ghosts) and the chemical pressure
-//                  tensor P (Eq. free_energy)
-//   kt_fdiv        32x4x4 tiles: force on the fluid F = g - div P
+// lbdp_kernels.cuh -- the node and particle bodies of the lattice update and
+// the particle kernels, templated on the precision configuration.  One step
+// of a single box is
+//   k_pt_part, k_f_part   per particle: chemical stress and force at the fluid
+//                  nodes next to the particle (Eqs. chem_potentials,
+//                  free_energy; the link-form divergence)
 //   k_links        per particle: bounce-back and chemical-stress momentum sums
 //                  over its boundary links, implicit velocity update, new
 //                  position and orientation (Sec. "Particles")
-//   k_collide      D3Q19 pull streaming, halfway bounce-back on walls, BGK +
-//                  Guo with F, for every fluid node not next to a particle
-//   k_collide_particles  the same for the nodes next to particles: moving
+//   k_collide_particles  collide-stream of the nodes next to particles: moving
 //                  bounce-back plus phoretic slip on their particle links
-//   kt_scalars     32x4x4 tiles: psi/phi transport (Eq. diffusion_reaction),
-//                  and the k_d sink, for nodes not next to a particle
-//   k_scalars_particles  the same next to particles, with Janus production
-//                  (Eq. activity) and the flux into the moving surfaces
+//   kz_fused       (lbdp_zmarch.cuh) chemical potentials, stress, force and
+//                  D3Q19 pull collide-stream of every other fluid node
+//   k_scalars_particles  psi/phi transport next to particles, with Janus
+//                  production (Eq. activity) and the flux into the moving
+//                  surfaces
+//   kz_scalars     (lbdp_zmarch.cuh) psi/phi transport (Eq.
+//                  diffusion_reaction) and the k_d sink of every other node
 //   k_cover_mark   per particle: solid mask at the new positions
 //   k_cover_apply  per particle: covering/uncovering and boundary flags; the
 //                  last block folds the psi/phi deficits into the uniform
 //                  correction and moves the particles
 // Every kernel is stencil or streaming work: no tensor cores.  Each body is a
 // __device__ function of (parameters, pointers, node), so the single-box
-// kernels (grid over the box) and the batched kernels (persistent loop over a
-// tile list of many boxes) run the same arithmetic.
+// kernels and the batched kernels (lbdp_batch_kernels.cuh) run the same
+// arithmetic.
 //
 // Precision: node and link arithmetic runs in the mode's real type R.  FP64
 // is kept where the method needs it in every mode -- the solid/fluid and
@@ -259,19 +260,20 @@ __device__ __forceinline__ void link_velocity(const DevParams& P, const Q& q, in
     ub[2] = add_x(add_x(U2, cross_x(W0, r[1], W1, r[0])), vs[2]);
 }
 
-// Wetting ghost of psi at the solid neighbour x + c_i of fluid node x:
-// psi(x) + (H/kappa) c_i . n_hat at the link midpoint.
+// Wetting ghost of psi at the solid neighbour x + c_i of fluid node x,
+// psi(x) + (H/kappa) c_i . n_hat at the link midpoint, as its difference
+// from psi(x).
 template <class R>
-__device__ __forceinline__ R psi_ghost(const DevParams& P, const DevPart& q, int x, int y, int z, int i, R ps)
+__device__ __forceinline__ R psi_ghost_diff(const DevParams& P, const DevPart& q, int x, int y, int z, int i)
 {
-    if (PartR<R>::Hk(q) == (R)0) return ps;
+    if (PartR<R>::Hk(q) == (R)0) return (R)0;
     int D[3];
     int_offset(P, q.g, x, y, z, D);
     R r[3];
     link_offset_r<R>(q.g, D, i, r);
     const R rn = sqrt(dot_x(r[0], r[1], r[2], r[0], r[1], r[2]));
     const R cn = cdot<R>(i, r[0], r[1], r[2]) / rn;
-    return fma_x(PartR<R>::Hk(q), cn, ps);
+    return mul_x(PartR<R>::Hk(q), cn);
 }
 
 // Equilibrium population i of (rho, u) as its deviation from the rest
@@ -288,74 +290,108 @@ __device__ __forceinline__ Real geq_i(int i, Real rho, Real rho0, Real ux, Real 
 
 __device__ __forceinline__ float tanh_r(float v) { return tanhf(v); }
 __device__ __forceinline__ double tanh_r(double v) { return tanh(v); }
+__device__ __forceinline__ float rcp_rn(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double rcp_rn(double v) { return __drcp_rn(v); }
 
-// Chemical potentials and (optionally) the pressure tensor at one fluid node
-// from v[0] = psi(x) and v[i] = psi at neighbour i (ghost-resolved), ph = phi(x):
+// phi0 = phi_b + E tanh psi (Eq. free_energy); with E = 0 it is phi_b and tanh
+// is not evaluated.
+template <class R>
+__device__ __forceinline__ R phi0_of(const PrmR<R>& Q, R ps)
+{
+    return Q.E != (R)0 ? Q.phib + Q.E * tanh_r(ps) : Q.phib;
+}
+
+// Chemical potentials and (optionally) the chemical stress at one fluid node
+// from ps = psi(x), d[i] = psi(x + c_i) - psi(x) (ghost-resolved; d[0] is not
+// read) and ph = phi(x):
 //   mu_psi = A(psi^3 - psi) - kappa lap psi - C E (phi - phi0)/cosh^2 psi,
 //   mu_phi = C (phi - phi0),  phi0 = phi_b + E tanh psi          (Eq. chem_potentials)
-//   P = [psi mu_psi + phi mu_phi - f - kappa |grad psi|^2/2] I + kappa grad psi grad psi,
+//   P = p_iso I + kappa grad psi grad psi,
+//   p_iso = psi mu_psi + phi mu_phi - f - kappa |grad psi|^2/2,
 //   f = A psi^4/4 - A psi^2/2 + C (phi - phi0)^2/2.               (Eq. free_energy)
-// 1/cosh^2 is taken as 1 - tanh^2.  P is returned as xx yy zz xy xz yz.
+// P is returned by its four independent numbers: pt = (p_iso, grad psi).
+// 1/cosh^2 is taken as 1 - tanh^2; with E = 0, phi0 = phi_b and the
+// coupling term vanish, and tanh is not evaluated.  The 19-point Laplacian
+// 6 sum_i w_i (psi(x+c_i) - psi(x)) sums the differences per weight class;
+// the gradient 3 sum_i w_i c_i psi(x+c_i) sums the differences of opposite
+// neighbours.
 // Written for FP32: A psi (psi^2 - 1) and f + A/4 = A (psi^2 - 1)^2 / 4 + ...
-// do not cancel in the bulk phases, the stencils act on differences from the
-// node's own value (sum_i w_i c_i = 0), and P is returned less the bulk
-// pressure A/4 on its diagonal.  A constant part of P exerts no force: the
-// link-form divergence sums w_i c_i over all 18 directions of a node, and the
-// particle stress sums w_i c_i and w_i r_b x c_i over the boundary links of a
-// sphere, which vanish for the same reason.
+// do not cancel in the bulk phases, the stencils act on differences, and
+// p_iso is returned less the bulk pressure A/4.  A constant part of P exerts
+// no force: the link-form divergence sums w_i c_i over all 18 directions of a
+// node, and the particle stress sums w_i c_i and w_i r_b x c_i over the
+// boundary links of a sphere, which vanish for the same reason.
 template <class R>
-__device__ __forceinline__ void mu_pressure(const PrmR<R>& Q, const R v[19], R ph, bool want_p, R& mps, R& mph,
-                                            R pt[6])
+__device__ __forceinline__ void mu_pressure(const PrmR<R>& Q, R ps, const R d[19], R ph, bool want_p, R& mps,
+                                            R& mph, R pt[kPtFields])
 {
-    const R ps = v[0];
-    R lap = 0, g0 = 0, g1 = 0, g2 = 0;
+    // the two weight classes summed in two halves each (shorter chains)
+    const R sa = (d[1] + d[2] + d[3]) + (d[4] + d[5] + d[6]);
+    const R sd = ((d[7] + d[8]) + (d[9] + d[10]) + (d[11] + d[12])) +
+                 ((d[13] + d[14]) + (d[15] + d[16]) + (d[17] + d[18]));
+    const R lap = fma_x(sa, (R)(1.0 / 3.0), sd * (R)(1.0 / 6.0));
+    // opposite pairs (j, j + 1), j odd: c_j = -c_{j+1}
+    R ga[3] = {0, 0, 0}, gd[3] = {0, 0, 0};
 #pragma unroll
-    for (int i = 1; i < 19; ++i) {
-        const R w = wgt_r<R>(i);
-        const R wv = w * (v[i] - ps);
-        lap += wv;
-        if (cx(i) != 0) g0 += cx(i) > 0 ? wv : -wv;
-        if (cy(i) != 0) g1 += cy(i) > 0 ? wv : -wv;
-        if (cz(i) != 0) g2 += cz(i) > 0 ? wv : -wv;
+    for (int j = 1; j < 19; j += 2) {
+        const R df = d[j] - d[j + 1];
+        R* acc = j < 7 ? ga : gd;
+        if (cx(j) != 0) acc[0] += cx(j) > 0 ? df : -df;
+        if (cy(j) != 0) acc[1] += cy(j) > 0 ? df : -df;
+        if (cz(j) != 0) acc[2] += cz(j) > 0 ? df : -df;
     }
-    lap *= (R)6;
-    g0 *= (R)3;
-    g1 *= (R)3;
-    g2 *= (R)3;
-    const R th = tanh_r(ps);
-    const R dphi = ph - (Q.phib + Q.E * th);
-    mph = Q.C * dphi;
+    const R g0 = fma_x(ga[0], (R)(1.0 / 6.0), gd[0] * (R)(1.0 / 12.0));
+    const R g1 = fma_x(ga[1], (R)(1.0 / 6.0), gd[1] * (R)(1.0 / 12.0));
+    const R g2 = fma_x(ga[2], (R)(1.0 / 6.0), gd[2] * (R)(1.0 / 12.0));
     const R t = fma_x(ps, ps, (R)-1);   // psi^2 - 1
-    mps = Q.A * ps * t - Q.kappa * lap - Q.C * Q.E * dphi * ((R)1 - th * th);
+    R dphi;
+    if (Q.E != (R)0) {
+        const R th = tanh_r(ps);
+        dphi = ph - (Q.phib + Q.E * th);
+        mps = Q.A * ps * t - Q.kappa * lap - Q.C * Q.E * dphi * ((R)1 - th * th);
+    } else {
+        dphi = ph - Q.phib;
+        mps = Q.A * ps * t - Q.kappa * lap;
+    }
+    mph = Q.C * dphi;
     if (!want_p) return;
     const R fs = (R)0.25 * Q.A * t * t + (R)0.5 * Q.C * dphi * dphi;   // f + A/4
     const R gg = g0 * g0 + g1 * g1 + g2 * g2;
-    const R piso = ps * mps + ph * mph - fs - (R)0.5 * Q.kappa * gg;   // less A/4
-    pt[0] = piso + Q.kappa * g0 * g0;
-    pt[1] = piso + Q.kappa * g1 * g1;
-    pt[2] = piso + Q.kappa * g2 * g2;
-    pt[3] = Q.kappa * g0 * g1;
-    pt[4] = Q.kappa * g0 * g2;
-    pt[5] = Q.kappa * g1 * g2;
+    pt[0] = ps * mps + ph * mph - fs - (R)0.5 * Q.kappa * gg;   // less A/4
+    pt[1] = g0;
+    pt[2] = g1;
+    pt[3] = g2;
 }
 
-// Gather the 19 ghost-resolved psi values of fluid node n from global memory.
-template <class R, class F>
-__device__ __forceinline__ void gather_psi(const DevParams& P, const DevPtrs& D, const F* psi, int x, int y, int z,
-                                           const int nb[19], R v[19])
+// P . c_i of the stress pt = (p_iso, grad psi): p_iso c_i + kappa g (g . c_i).
+template <class R>
+__device__ __forceinline__ void pt_dot_c(int i, R kappa, const R pt[kPtFields], R out[3])
 {
-    const R dps = corr_r<R>(D, 0);
-    v[0] = (R)psi[nb[0]] + dps;
+    const R ks = kappa * cdot<R>(i, pt[1], pt[2], pt[3]);
+    out[0] = fma_x(ks, pt[1], cx(i) == 0 ? (R)0 : (cx(i) > 0 ? pt[0] : -pt[0]));
+    out[1] = fma_x(ks, pt[2], cy(i) == 0 ? (R)0 : (cy(i) > 0 ? pt[0] : -pt[0]));
+    out[2] = fma_x(ks, pt[3], cz(i) == 0 ? (R)0 : (cz(i) > 0 ? pt[0] : -pt[0]));
+}
+
+// psi(x) (with the correction) and the 18 ghost-resolved differences
+// psi(x + c_i) - psi(x) of fluid node n, from global memory.
+template <class R, class F>
+__device__ __forceinline__ R gather_psi(const DevParams& P, const DevPtrs& D, const F* psi, int x, int y, int z,
+                                        const int nb[19], R d[19])
+{
+    const R p0 = (R)psi[nb[0]];
+    d[0] = (R)0;
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
         const int m = nb[i];
         if (m < 0) {
-            v[i] = v[0];
+            d[i] = (R)0;
         } else {
             const uint8_t q = D.mask[m];
-            v[i] = q ? psi_ghost<R>(P, D.parts[q - 1], x, y, z, i, v[0]) : (R)psi[m] + dps;
+            d[i] = q ? psi_ghost_diff<R>(P, D.parts[q - 1], x, y, z, i) : (R)psi[m] - p0;
         }
     }
+    return p0 + corr_r<R>(D, 0);
 }
 
 // FP64 block reduction: sums K values per thread over the block in a fixed
@@ -603,39 +639,53 @@ __device__ __forceinline__ bool stage_tile(const DevParams& P, const uint8_t* ma
 // neighbour load is issued before any decision (walls clamp to the node
 // itself), so the loads overlap instead of waiting behind mask branches.
 // ---------------------------------------------------------------------------
-// Fields of the chemical-potential body: 0 psi, 1 phi.
+// Fields of the chemical-potential body: 0 psi, 1 phi.  mup_values returns
+// mu_psi, mu_phi and (when P.thermo) the pressure tensor of fluid node
+// (x, y, z); mup_compute stores them.
+// dps, dph: the uniform psi/phi correction still to be added (corr_r); a
+// kernel that loops over many nodes reads them once.
+template <class C, class A>
+__device__ __forceinline__ void mup_values(const DevParams& P, const DevPtrs& D, int x, int y, int z, const A& a,
+                                           typename C::real dps, typename C::real dph, typename C::real& mps,
+                                           typename C::real& mph, typename C::real (&pt)[kPtFields])
+{
+    using R = typename C::real;
+    const PrmR<R>& Q = prm<R>(P);
+    // differences from psi(x): the uniform correction cancels in them
+    R d[19];
+    uint8_t mk[19];
+    const R p0 = (R)a.template get<0>(0);
+    d[0] = (R)0;
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        mk[i] = a.mask(i);
+        d[i] = (R)a.template get<0>(i) - p0;
+    }
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        if (mk[i] == kWallSlot)
+            d[i] = (R)0;
+        else if (mk[i])
+            d[i] = psi_ghost_diff<R>(P, D.parts[mk[i] - 1], x, y, z, i);
+    }
+    mu_pressure<R>(Q, p0 + dps, d, (R)a.template get<1>(0) + dph, P.thermo != 0, mps, mph, pt);
+}
+
 template <class C, class A>
 __device__ __forceinline__ void mup_compute(const DevParams& P, const DevPtrs& D, int x, int y, int z, int n,
                                             const A& a)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
-    const PrmR<R>& Q = prm<R>(P);
     const size_t N = (size_t)P.N;
-    const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
-    R v[19];
-    uint8_t mk[19];
-    v[0] = (R)a.template get<0>(0) + dps;
-#pragma unroll
-    for (int i = 1; i < 19; ++i) {
-        mk[i] = a.mask(i);
-        v[i] = (R)a.template get<0>(i) + dps;
-    }
-#pragma unroll
-    for (int i = 1; i < 19; ++i) {
-        if (mk[i] == kWallSlot)
-            v[i] = v[0];
-        else if (mk[i])
-            v[i] = psi_ghost<R>(P, D.parts[mk[i] - 1], x, y, z, i, v[0]);
-    }
-    R mps, mph, pt[6];
-    mu_pressure<R>(Q, v, (R)a.template get<1>(0) + dph, P.thermo != 0, mps, mph, pt);
+    R mps, mph, pt[kPtFields];
+    mup_values<C>(P, D, x, y, z, a, corr_r<R>(D, 0), corr_r<R>(D, 1), mps, mph, pt);
     ((F*)D.mupsi)[n] = (F)mps;
     ((F*)D.muphi)[n] = (F)mph;
     if (P.thermo) {
         F* ptg = (F*)D.pt;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) ptg[k * N + n] = (F)pt[k];
+        for (int k = 0; k < kPtFields; ++k) ptg[k * N + n] = (F)pt[k];
     }
 }
 
@@ -666,37 +716,59 @@ __device__ __forceinline__ void mup_node(const DevParams& P, const DevPtrs& D, i
 // ---------------------------------------------------------------------------
 // S2: force on the fluid, F = g - div P in the link form
 //   -6 sum_i w_i [(P(x) + P~_i)/2] . c_i = -3 sum_i w_i P~_i . c_i
-// (sum_i w_i c_i = 0), with P~_i = P(x) at solid and wall neighbours.
+// (sum_i w_i c_i = 0), with P~_i = P(x) at solid and wall neighbours, and
+// P~_i . c_i = p_iso c_i + kappa g (g . c_i) from the stress (p_iso, g) of
+// mu_pressure.
 // ---------------------------------------------------------------------------
+// fdiv_values returns the force of a fluid node (rounded to the field type, as
+// stored); fdiv_compute stores it.  Fields of the accessor: the stress
+// (p_iso, g_x, g_y, g_z).
+template <class C, class A>
+__device__ __forceinline__ void fdiv_values(const DevParams& P, const A& a, typename C::real& Fxo,
+                                            typename C::real& Fyo, typename C::real& Fzo)
+{
+    using R = typename C::real;
+    using F = typename C::fld_t;
+    const PrmR<R>& Q = prm<R>(P);
+    R Fx = Q.g[0], Fy = Q.g[1], Fz = Q.g[2];
+    if (P.thermo) {
+        const R o0 = (R)a.template get<0>(0), o1 = (R)a.template get<1>(0), o2 = (R)a.template get<2>(0);
+        const R o3 = (R)a.template get<3>(0);
+        R d0 = 0, d1 = 0, d2 = 0;   // sum_i w_i (g . c_i) g
+        R e0 = 0, e1 = 0, e2 = 0;   // sum_i w_i c_i p_iso
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const bool own = a.mask(i) != 0;
+            const R pi = own ? o0 : (R)a.template get<0>(i);
+            const R gx = own ? o1 : (R)a.template get<1>(i);
+            const R gy = own ? o2 : (R)a.template get<2>(i);
+            const R gz = own ? o3 : (R)a.template get<3>(i);
+            const R w = wgt_r<R>(i);
+            const R ws = w * cdot<R>(i, gx, gy, gz);
+            d0 = fma_x(ws, gx, d0);
+            d1 = fma_x(ws, gy, d1);
+            d2 = fma_x(ws, gz, d2);
+            if (cx(i) != 0) e0 = fma_x(cx(i) > 0 ? w : -w, pi, e0);
+            if (cy(i) != 0) e1 = fma_x(cy(i) > 0 ? w : -w, pi, e1);
+            if (cz(i) != 0) e2 = fma_x(cz(i) > 0 ? w : -w, pi, e2);
+        }
+        Fx -= (R)3 * fma_x(Q.kappa, d0, e0);
+        Fy -= (R)3 * fma_x(Q.kappa, d1, e1);
+        Fz -= (R)3 * fma_x(Q.kappa, d2, e2);
+    }
+    Fxo = (R)(F)Fx;
+    Fyo = (R)(F)Fy;
+    Fzo = (R)(F)Fz;
+}
+
 template <class C, class A>
 __device__ __forceinline__ void fdiv_compute(const DevParams& P, const DevPtrs& D, int n, const A& a)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
-    const PrmR<R>& Q = prm<R>(P);
     const size_t N = (size_t)P.N;
-    R Fx = Q.g[0], Fy = Q.g[1], Fz = Q.g[2];
-    if (P.thermo) {
-        const R o0 = (R)a.template get<0>(0), o1 = (R)a.template get<1>(0), o2 = (R)a.template get<2>(0);
-        const R o3 = (R)a.template get<3>(0), o4 = (R)a.template get<4>(0), o5 = (R)a.template get<5>(0);
-        R d0 = 0, d1 = 0, d2 = 0;
-#pragma unroll
-        for (int i = 1; i < 19; ++i) {
-            const bool own = a.mask(i) != 0;
-            // components multiplied by a zero velocity component are never
-            // loaded (the unrolled cdot drops them)
-            const R xx = own ? o0 : (R)a.template get<0>(i), yy = own ? o1 : (R)a.template get<1>(i);
-            const R zz = own ? o2 : (R)a.template get<2>(i), xy = own ? o3 : (R)a.template get<3>(i);
-            const R xz = own ? o4 : (R)a.template get<4>(i), yz = own ? o5 : (R)a.template get<5>(i);
-            const R w = wgt_r<R>(i);
-            d0 += w * cdot<R>(i, xx, xy, xz);
-            d1 += w * cdot<R>(i, xy, yy, yz);
-            d2 += w * cdot<R>(i, xz, yz, zz);
-        }
-        Fx -= (R)3 * d0;
-        Fy -= (R)3 * d1;
-        Fz -= (R)3 * d2;
-    }
+    R Fx, Fy, Fz;
+    fdiv_values<C>(P, a, Fx, Fy, Fz);
     F* force = (F*)D.force;
     force[n] = (F)Fx;
     force[N + n] = (F)Fy;
@@ -711,12 +783,12 @@ __device__ __forceinline__ void fdiv_node(const DevParams& P, const DevPtrs& D, 
     if (D.mask[n]) return;
     const size_t N = (size_t)P.N;
     const F* pt = (const F*)D.pt;
-    GAcc<F, 6> a;
+    GAcc<F, kPtFields> a;
     neighbours(P, x, y, z, a.nb);
     a.n = n;
     a.mk = D.mask;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) a.f[k] = pt + k * N;
+    for (int k = 0; k < kPtFields; ++k) a.f[k] = pt + k * N;
     fdiv_compute<C>(P, D, n, a);
 }
 
@@ -936,12 +1008,12 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
         const R ps = (R)psi[n] + dps, ph = (R)phi[n] + dph;
         R gphi[3];
         grad_phi_at<R, F>(nb, phi, D.mask, ph, dph, gphi);
-        R pt[6] = {0, 0, 0, 0, 0, 0};
+        R pt[kPtFields] = {0, 0, 0, 0};
         if (P.thermo) {
-            // the pressure tensor the fluid's force used this step
+            // the stress the fluid's force used this step
             const F* ptg = (const F*)D.pt;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) pt[k] = (R)ptg[k * N + n];
+            for (int k = 0; k < kPtFields; ++k) pt[k] = (R)ptg[k * N + n];
         }
         R nacc[K];   // this node's links, added to the FP64 sums once
 #pragma unroll
@@ -959,9 +1031,11 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
             R dP[3] = {mul_x(c[0], mag), mul_x(c[1], mag), mul_x(c[2], mag)};
             if (P.thermo) {
                 // chemical stress flux through the link, 6 w_i P(x) . c_i
-                dP[0] = fma_x(w6, cdot<R>(i, pt[0], pt[3], pt[4]), dP[0]);
-                dP[1] = fma_x(w6, cdot<R>(i, pt[3], pt[1], pt[5]), dP[1]);
-                dP[2] = fma_x(w6, cdot<R>(i, pt[4], pt[5], pt[2]), dP[2]);
+                R pc[3];
+                pt_dot_c<R>(i, Q.kappa, pt, pc);
+                dP[0] = fma_x(w6, pc[0], dP[0]);
+                dP[1] = fma_x(w6, pc[1], dP[1]);
+                dP[2] = fma_x(w6, pc[2], dP[2]);
             }
             nacc[0] = add_x(nacc[0], dP[0]);
             nacc[1] = add_x(nacc[1], dP[1]);
@@ -1057,7 +1131,7 @@ __device__ __forceinline__ void collide_store(const PrmR<typename C::real>& Q, c
         if (cz(j) != 0) jz += cz(j) > 0 ? gl[j] : -gl[j];
     }
     const R rho = rho0 + dr;
-    const R ir = (R)1 / rho;
+    const R ir = rcp_rn(rho);   // IEEE 1 / rho
     const R ux = fma_x((R)0.5, Fx, jx) * ir;
     const R uy = fma_x((R)0.5, Fy, jy) * ir;
     const R uz = fma_x((R)0.5, Fz, jz) * ir;
@@ -1226,6 +1300,53 @@ static __device__ __noinline__ void collide_boundary(const DevParams& P, const D
     collide_boundary_body<C>(P, D, x, y, z);
 }
 
+// Pull sources of every population of node (x, y, z) loaded as deviations
+// into fl (wrapped on periodic axes, clamped to the node itself beyond a wall,
+// where bulk_wall_links replaces them): one memory round trip.
+template <class C>
+__device__ __forceinline__ void pull_loads(const DevParams& P, const DevPtrs& D, int x, int y, int z,
+                                           typename C::real (&fl)[19])
+{
+    using R = typename C::real;
+    using S = typename C::pop_t;
+    const int nx = P.nx, ny = P.ny, sxy = nx * ny;
+    const int NN = (int)P.N;
+    const S* fs = (const S*)D.f_src;
+    const R rho0 = prm<R>(P).rho0;
+    // source x - c_j of population j as xi[1 - c_jx] + yo[1 - c_jy] + zo[1 - c_jz]
+    const int xi[3] = {x > 0 ? x - 1 : (P.per[0] ? nx - 1 : 0), x, x < nx - 1 ? x + 1 : (P.per[0] ? 0 : x)};
+    const int yo[3] = {(y > 0 ? y - 1 : (P.per[1] ? ny - 1 : 0)) * nx, y * nx,
+                       (y < ny - 1 ? y + 1 : (P.per[1] ? 0 : y)) * nx};
+    const int zo[3] = {(z > 0 ? z - 1 : (P.per[2] ? P.nz - 1 : 0)) * sxy, z * sxy,
+                       (z < P.nz - 1 ? z + 1 : (P.per[2] ? 0 : z)) * sxy};
+#pragma unroll
+    for (int j = 0; j < 19; ++j) {
+        const int m = xi[1 - cx(j)] + yo[1 - cy(j)] + zo[1 - cz(j)];
+        fl[j] = (R)PopStore<S>::load_dev(fs, j * NN + m, j, rho0);
+    }
+}
+
+// Halfway bounce-back of a bulk node next to a wall: a link whose source lies
+// beyond a wall brings back the node's own population of the opposite
+// direction.
+template <class C>
+__device__ __forceinline__ void bulk_wall_links(const DevParams& P, const DevPtrs& D, int x, int y, int z,
+                                                typename C::real (&fl)[19])
+{
+    using R = typename C::real;
+    using S = typename C::pop_t;
+    const int n = x + P.nx * (y + P.ny * z);
+    const int NN = (int)P.N;
+    const S* fs = (const S*)D.f_src;
+    const bool wx[3] = {!P.per[0] && x == 0, false, !P.per[0] && x == P.nx - 1};
+    const bool wy[3] = {!P.per[1] && y == 0, false, !P.per[1] && y == P.ny - 1};
+    const bool wz[3] = {!P.per[2] && z == 0, false, !P.per[2] && z == P.nz - 1};
+#pragma unroll
+    for (int j = 1; j < 19; ++j)
+        if (wx[1 - cx(j)] || wy[1 - cy(j)] || wz[1 - cz(j)])
+            fl[j] = (R)PopStore<S>::load_dev(fs, opp(j) * NN + n, opp(j), prm<R>(P).rho0);
+}
+
 // kBoundary: nodes next to a particle are collided here (out of line);
 // otherwise they are left to k_collide_particles.
 template <class C, bool kBoundary = true>
@@ -1371,12 +1492,11 @@ __device__ __forceinline__ Two<double> add2(Two<double> x, Two<double> y) { retu
 // and -g(x) c_j.u_b more on a particle link (scalars_particle_links).
 template <class C, bool kBoundary, class A>
 __device__ __forceinline__ void scalars_compute_lb(const DevParams& P, const DevPtrs& D, int x, int y, int z,
-                                                   int n, const A& a)
+                                                   int n, const A& a, typename C::real dps, typename C::real dph)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
     const PrmR<R>& Q = prm<R>(P);
-    const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
     const R ps = (R)a.template get<0>(0) + dps, ph = (R)a.template get<1>(0) + dph;
     const R a0 = (R)a.template get<2>(0), b0 = (R)a.template get<3>(0);
     const R ux = (R)a.template get<4>(0), uy = (R)a.template get<5>(0), uz = (R)a.template get<6>(0);
@@ -1410,7 +1530,7 @@ __device__ __forceinline__ void scalars_compute_lb(const DevParams& P, const Dev
         hn_src = l.src;
     }
     const R pn = ps + sps;
-    R hn = ph + sph - Q.kd * (ph - (Q.phib + Q.E * tanh_r(ps)));
+    R hn = ph + sph - Q.kd * (ph - phi0_of(Q, ps));
     hn += hn_src;
     ((F*)D.psi_dst)[n] = (F)pn;
     ((F*)D.phi_dst)[n] = (F)hn;
@@ -1419,18 +1539,18 @@ __device__ __forceinline__ void scalars_compute_lb(const DevParams& P, const Dev
 // Fields of the transport body: 0 psi, 1 phi, 2 mu_psi, 3 mu_phi, 4..6 u.
 // kBoundary: nodes next to a particle are transported here; otherwise they
 // are left to k_scalars_particles.
-template <class C, bool kBoundary = true, class A>
-__device__ __forceinline__ void scalars_compute(const DevParams& P, const DevPtrs& D, int x, int y, int z, int n,
-                                                const A& a)
+// dps, dph as for mup_values.
+template <class C, bool kBoundary, class A>
+__device__ __forceinline__ void scalars_compute_c(const DevParams& P, const DevPtrs& D, int x, int y, int z, int n,
+                                                  const A& a, typename C::real dps, typename C::real dph)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
     if (P.scheme) {
-        scalars_compute_lb<C, kBoundary>(P, D, x, y, z, n, a);
+        scalars_compute_lb<C, kBoundary>(P, D, x, y, z, n, a, dps, dph);
         return;
     }
     const PrmR<R>& Q = prm<R>(P);
-    const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
     const R ps = (R)a.template get<0>(0) + dps, ph = (R)a.template get<1>(0) + dph;
     const R a0 = (R)a.template get<2>(0), b0 = (R)a.template get<3>(0);
     const R ux = (R)a.template get<4>(0), uy = (R)a.template get<5>(0), uz = (R)a.template get<6>(0);
@@ -1470,10 +1590,18 @@ __device__ __forceinline__ void scalars_compute(const DevParams& P, const DevPtr
         hn_src = l.src;
     }
     const R pn = ps + (R)6 * sps;
-    R hn = ph + (R)6 * sph - Q.kd * (ph - (Q.phib + Q.E * tanh_r(ps)));
+    R hn = ph + (R)6 * sph - Q.kd * (ph - phi0_of(Q, ps));
     hn += hn_src;
     ((F*)D.psi_dst)[n] = (F)pn;
     ((F*)D.phi_dst)[n] = (F)hn;
+}
+
+template <class C, bool kBoundary = true, class A>
+__device__ __forceinline__ void scalars_compute(const DevParams& P, const DevPtrs& D, int x, int y, int z, int n,
+                                                const A& a)
+{
+    using R = typename C::real;
+    scalars_compute_c<C, kBoundary>(P, D, x, y, z, n, a, corr_r<R>(D, 0), corr_r<R>(D, 1));
 }
 
 template <class C>
@@ -1718,19 +1846,13 @@ __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevP
 }
 
 // ---------------------------------------------------------------------------
-// single-box kernels: a row grid (x blocks, y, z) over the box for the node
-// bodies; grid (blocks per particle, particles) for the particle bodies
+// particle kernels of the single box: grid (blocks per particle, particles)
+// (the bulk kernels of the single box are in lbdp_zmarch.cuh)
 // ---------------------------------------------------------------------------
-template <class C>
-__global__ void __launch_bounds__(kRowThreads, 10) k_mup(DevParams P, DevPtrs D)
-{
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x < P.nx) mup_node<C>(P, D, x, blockIdx.y, blockIdx.z);
-}
-
-// Tiled force and transport kernels: a 256-thread block stages the inputs
-// of a 32 x 4 x 4 tile and its halo in shared memory once, then each thread
-// computes two nodes, reading all neighbours at fixed shared-memory offsets.
+// Shared-memory tiles of the batched force and transport kernels: a
+// 256-thread block stages the inputs of a 32 x 4 x 4 tile and its halo once,
+// then each thread computes two nodes, reading all neighbours at fixed
+// shared-memory offsets.
 using Tile = TileShape<32, 4, 4>;
 constexpr int kTileThreads = 256;
 
@@ -1754,67 +1876,11 @@ __device__ __forceinline__ void tile_nodes(const DevParams& P, const uint8_t* sm
     }
 }
 
-template <class C>
-__global__ void __launch_bounds__(kTileThreads) kt_fdiv(DevParams P, DevPtrs D)
-{
-    using F = typename C::fld_t;
-    extern __shared__ __align__(16) unsigned char smem_raw[];   // tile_smem<F, 6>()
-    F* sf = (F*)smem_raw;
-    uint8_t* sm = (uint8_t*)(sf + 6 * Tile::slots);
-    const size_t N = (size_t)P.N;
-    const F* pt = (const F*)D.pt;
-    const F* const src[6] = {pt, pt + N, pt + 2 * N, pt + 3 * N, pt + 4 * N, pt + 5 * N};
-    const bool any = stage_tile<F, 6, Tile>(P, D.mask, src, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, sf, sm);
-    const bool clear = !__syncthreads_or(any);
-    tile_nodes(P, sm, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, [&](int, int, int, int n, int slot) {
-        if (clear) {
-            const TAccClear<F, 6, Tile> a{{sf, sm, slot}};
-            fdiv_compute<C>(P, D, n, a);
-        } else {
-            const TAcc<F, 6, Tile> a{sf, sm, slot};
-            fdiv_compute<C>(P, D, n, a);
-        }
-    });
-}
-
-template <class C>
-__global__ void __launch_bounds__(kTileThreads) kt_scalars(const __grid_constant__ DevParams P,
-                                                            const __grid_constant__ DevPtrs D)
-{
-    using F = typename C::fld_t;
-    extern __shared__ __align__(16) unsigned char smem_raw[];   // tile_smem<F, 7>()
-    F* sf = (F*)smem_raw;
-    uint8_t* sm = (uint8_t*)(sf + 7 * Tile::slots);
-    const size_t N = (size_t)P.N;
-    const F* u = (const F*)D.u;
-    const F* const src[7] = {(const F*)D.psi_src, (const F*)D.phi_src, (const F*)D.mupsi, (const F*)D.muphi,
-                             u, u + N, u + 2 * N};
-    const bool any = stage_tile<F, 7, Tile>(P, D.mask, src, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, sf, sm);
-    const bool clear = !__syncthreads_or(any);
-    tile_nodes(P, sm, blockIdx.x * 32, blockIdx.y * 4, blockIdx.z * 4, [&](int x, int y, int z, int n, int slot) {
-        if (clear) {
-            const TAccClear<F, 7, Tile> a{{sf, sm, slot}};
-            scalars_compute<C, false>(P, D, x, y, z, n, a);
-        } else {
-            const TAcc<F, 7, Tile> a{sf, sm, slot};
-            scalars_compute<C, false>(P, D, x, y, z, n, a);
-        }
-    });
-}
-
-template <class C>
-__global__ void __launch_bounds__(kRowThreads, 8) k_collide(const __grid_constant__ DevParams P,
-                                                             const __grid_constant__ DevPtrs D)
-{
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x < P.nx) collide_node<C, false>(P, D, x, blockIdx.y, blockIdx.z);
-}
-
-// Collide-stream of the fluid nodes next to particles, beside k_collide (which
-// leaves them out).  These nodes read the particle records and their
-// neighbours' masks in chains of dependent loads; inside k_collide, under its
-// full memory load and register budget, each such chain would hold its block
-// long after the others finish.  Block (b, p) walks the link box of particle
+// Collide-stream of the fluid nodes next to particles, beside the bulk kernel
+// (which leaves them out).  These nodes read the particle records and their
+// neighbours' masks in chains of dependent loads; inside the bulk kernel,
+// under its full memory load and register budget, each such chain would hold
+// its block long after the others finish.  Block (b, p) walks the link box of particle
 // p; a node next to several particles is collided by the lowest of them.
 template <class C>
 __global__ void __launch_bounds__(kPartThreads) k_collide_particles(const __grid_constant__ DevParams P,
@@ -1844,7 +1910,7 @@ __global__ void __launch_bounds__(kPartThreads) k_collide_particles(const __grid
     }
 }
 
-// Transport of the fluid nodes next to particles, beside kt_scalars (which
+// Transport of the fluid nodes next to particles, beside kz_scalars (which
 // leaves them out), for the same reason and with the same split as
 // k_collide_particles.
 template <class C>
@@ -1957,9 +2023,9 @@ __global__ void k_mu_now(DevParams P, DevPtrs D)
             const int x = (int)(n % P.nx), y = (int)((n / P.nx) % P.ny), z = (int)(n / ((size_t)P.nx * P.ny));
             int nb[19];
             neighbours(P, x, y, z, nb);
-            R v[19], pt[6];
-            gather_psi<R, F>(P, D, psi, x, y, z, nb, v);
-            mu_pressure<R>(prm<R>(P), v, (R)phi[n] + dph, false, mps, mph, pt);
+            R d[19], pt[kPtFields];
+            const R ps = gather_psi<R, F>(P, D, psi, x, y, z, nb, d);
+            mu_pressure<R>(prm<R>(P), ps, d, (R)phi[n] + dph, false, mps, mph, pt);
         }
         ((F*)D.mupsi)[n] = (F)mps;
         ((F*)D.muphi)[n] = (F)mph;

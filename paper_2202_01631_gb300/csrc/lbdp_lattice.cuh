@@ -20,6 +20,9 @@
 namespace lbdp {
 
 constexpr int kMaxParticles = 64;
+// The chemical pressure tensor P = p_iso I + kappa grad psi grad psi of a node
+// is kept as its four independent numbers (p_iso, grad psi).
+constexpr int kPtFields = 4;
 
 // Arithmetic with its rounding written out.  The particle sums and solve,
 // the boundary velocities and the refill of uncovered nodes are inlined into
@@ -212,7 +215,7 @@ struct DevPtrs {
     void* phi_dst;
     void* mupsi;
     void* muphi;
-    void* pt;             // [6][N] chemical pressure tensor xx yy zz xy xz yz
+    void* pt;             // [kPtFields][N] chemical stress: p_iso (less A/4), grad psi
     void* force;          // [3][N] force on the fluid, g - div P
     void* u;
     const uint8_t* mask;

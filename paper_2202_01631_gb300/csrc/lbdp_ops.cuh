@@ -6,6 +6,7 @@
 #include "lbdp_batch_kernels.cuh"
 #include "lbdp_internal.h"
 #include "lbdp_kernels.cuh"
+#include "lbdp_zmarch.cuh"
 
 namespace lbdp {
 
@@ -33,14 +34,12 @@ constexpr int kFdivBlocks = 5, kScalBlocks = 4;
 
 template <class C>
 struct Ops {
-    // One time step: mu/P, particle velocities, collide-stream, psi/phi
-    // transport, covering.  ev (optional, 6 events) brackets the kernel
-    // classes for the per-kernel split.
     using R = typename C::real;
+    using F = typename C::fld_t;
 
     static constexpr size_t kLinkSmem = block_rows_bytes<kLinkK>(kPartThreads);
-    static constexpr size_t kFdivSmem = tile_smem<typename C::fld_t, 6>();
-    static constexpr size_t kScalSmem = tile_smem<typename C::fld_t, 7>();
+    static constexpr size_t kFusedSmem = sizeof(FusedSmem<F>);
+    static constexpr size_t kZScalSmem = sizeof(ScalSmem<F>);
 
     // Opt the kernels that use more than 48 KiB of shared memory in, once per
     // device.
@@ -53,34 +52,57 @@ struct Ops {
         if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
         e = cudaFuncSetAttribute(k_links<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinkSmem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(kt_fdiv<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFdivSmem);
+            e = cudaFuncSetAttribute(kz_fused<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(kt_scalars<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScalSmem);
-        if (e == cudaSuccess) e = set_carveout((const void*)kt_fdiv<C>, kFdivBlocks, kFdivSmem);
-        if (e == cudaSuccess) e = set_carveout((const void*)kt_scalars<C>, kScalBlocks, kScalSmem);
+            e = cudaFuncSetAttribute(kz_scalars<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kZScalSmem);
         if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
         return e;
     }
 
+    // Blocks per particle of a box of the given edges (about one node per
+    // thread, at most kMaxPartBlocks).
+    static int part_blocks(long long nodes)
+    {
+        const long long b = (nodes + kPartThreads - 1) / kPartThreads;
+        return (int)(b < 1 ? 1 : (b > kMaxPartBlocks ? kMaxPartBlocks : b));
+    }
+
+    static dim3 pt_grid(const DevParams& P)
+    {
+        long long t = 1;
+        const int L[3] = {P.nx, P.ny, P.nz};
+        for (int a = 0; a < 3; ++a) {
+            int s = P.side1[a] + 2;
+            if (P.per[a] && s > L[a]) s = L[a];
+            t *= s;
+        }
+        return dim3(part_blocks(t), P.np);
+    }
+
+    // One time step.  With particles and a side stream: the particle kernels
+    // (pressure tensor and force next to the particles, link sums and the
+    // particle update, collide-stream of the nodes next to particles, the new
+    // mask) run on the side stream beside kz_fused; the transport of the bulk
+    // waits for the boundary collide-stream (it reads u there), and the
+    // boundary transport and covering wait for kz_fused and run beside it.
+    // ev (optional, 6 events): the same kernels in sequence, an event before
+    // the first and after each kernel class.
     static cudaError_t launch_step(const DevParams& P, const DevPtrs& D, const RowGrid& g, cudaStream_t s,
                                    cudaEvent_t* ev, const SideStream* side)
     {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
-        const dim3 pg1(P.nb1, P.np), pg2(P.nb2, P.np);
+        const dim3 pg1(P.nb1, P.np), pg2(P.nb2, P.np), pgt = pt_grid(P);
         if (P.np > 0 && side && !ev) {
-            // particle kernels on the side stream, overlapping the fluid kernels
-            k_mup<C><<<g.grid, g.block, 0, s>>>(P, D);
             cudaEventRecord(side->fork, s);
             cudaStreamWaitEvent(side->s, side->fork, 0);
+            k_pt_part<C><<<pgt, kPartThreads, 0, side->s>>>(P, D);
+            k_f_part<C><<<pg1, kPartThreads, 0, side->s>>>(P, D);
             k_links<C><<<pg1, kPartThreads, kLinkSmem, side->s>>>(P, D);
-            kt_fdiv<C><<<g.tiles, kTileThreads, kFdivSmem, s>>>(P, D);
-            cudaEventRecord(side->fdiv_done, s);
-            cudaStreamWaitEvent(side->s, side->fdiv_done, 0);
             k_collide_particles<C><<<pg1, kPartThreads, 0, side->s>>>(P, D);
             cudaEventRecord(side->bnd_done, side->s);
             k_cover_mark<C><<<pg2, kPartThreads, 0, side->s>>>(P, D);
-            k_collide<C><<<g.grid, g.block, 0, s>>>(P, D);
+            kz_fused<C><<<g.zgrid, kZThreads, kFusedSmem, s>>>(P, D);
             cudaEventRecord(side->collide_done, s);
             cudaStreamWaitEvent(side->s, side->collide_done, 0);
             k_scalars_particles<C><<<pg1, kPartThreads, 0, side->s>>>(P, D);
@@ -90,25 +112,25 @@ struct Ops {
             k_cover_apply<C><<<pg2, kPartThreads, 0, side->s>>>(P, D);
             cudaEventRecord(side->scal_done, side->s);
             cudaStreamWaitEvent(s, side->bnd_done, 0);
-            kt_scalars<C><<<g.tiles, kTileThreads, kScalSmem, s>>>(P, D);
+            kz_scalars<C><<<g.zgrid, kZThreads, kZScalSmem, s>>>(P, D);
             cudaStreamWaitEvent(s, side->scal_done, 0);   // the step ends with the side stream
             return cudaGetLastError();
         }
         if (ev) cudaEventRecord(ev[0], s);
-        k_mup<C><<<g.grid, g.block, 0, s>>>(P, D);
-        kt_fdiv<C><<<g.tiles, kTileThreads, kFdivSmem, s>>>(P, D);
-        if (ev) cudaEventRecord(ev[1], s);
         if (P.np > 0) {
+            k_pt_part<C><<<pgt, kPartThreads, 0, s>>>(P, D);
+            k_f_part<C><<<pg1, kPartThreads, 0, s>>>(P, D);
             k_links<C><<<pg1, kPartThreads, kLinkSmem, s>>>(P, D);
             k_collide_particles<C><<<pg1, kPartThreads, 0, s>>>(P, D);
         }
+        if (ev) cudaEventRecord(ev[1], s);
+        kz_fused<C><<<g.zgrid, kZThreads, kFusedSmem, s>>>(P, D);
         if (ev) cudaEventRecord(ev[2], s);
-        k_collide<C><<<g.grid, g.block, 0, s>>>(P, D);
+        kz_scalars<C><<<g.zgrid, kZThreads, kZScalSmem, s>>>(P, D);
         if (ev) cudaEventRecord(ev[3], s);
-        kt_scalars<C><<<g.tiles, kTileThreads, kScalSmem, s>>>(P, D);
+        if (P.np > 0) k_scalars_particles<C><<<pg1, kPartThreads, 0, s>>>(P, D);
         if (ev) cudaEventRecord(ev[4], s);
         if (P.np > 0) {
-            k_scalars_particles<C><<<pg1, kPartThreads, 0, s>>>(P, D);
             k_cover_mark<C><<<pg2, kPartThreads, 0, s>>>(P, D);
             k_cover_apply<C><<<pg2, kPartThreads, 0, s>>>(P, D);
         }
@@ -218,12 +240,12 @@ struct BOps {
                                  (int)block_rows_bytes<kLinkK>(kPartThreads));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(kb_tiled<C, kNcFdiv>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)tile_smem<typename C::fld_t, 6>());
+                                     (int)tile_smem<typename C::fld_t, kPtFields>());
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(kb_tiled<C, kNcScalars>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)tile_smem<typename C::fld_t, 7>());
         if (e == cudaSuccess)
-            e = set_carveout((const void*)kb_tiled<C, kNcFdiv>, kFdivBlocks, tile_smem<typename C::fld_t, 6>());
+            e = set_carveout((const void*)kb_tiled<C, kNcFdiv>, kFdivBlocks, tile_smem<typename C::fld_t, kPtFields>());
         if (e == cudaSuccess)
             e = set_carveout((const void*)kb_tiled<C, kNcScalars>, kScalBlocks, tile_smem<typename C::fld_t, 7>());
         if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
@@ -237,7 +259,7 @@ struct BOps {
         if (cfg == 4) {
             if (nc == kNcFdiv)
                 return cudaLaunchKernel((const void*)kb_tiled<C, kNcFdiv>, L->tiles, dim3(kTileThreads), args,
-                                        tile_smem<typename C::fld_t, 6>(), s);
+                                        tile_smem<typename C::fld_t, kPtFields>(), s);
             if (nc == kNcScalars)
                 return cudaLaunchKernel((const void*)kb_tiled<C, kNcScalars>, L->tiles, dim3(kTileThreads), args,
                                         tile_smem<typename C::fld_t, 7>(), s);

@@ -216,7 +216,12 @@ def lb_step(h, nsteps: int) -> None:
     _check(_lib.lb_step(h, int(nsteps)), "lb_step")
 
 
-KERNEL_CLASSES = ("k_mu", "k_links", "k_collide", "k_scalars", "k_cover")
+# kernel classes of lb_profile_step, in its sequential order: the particle
+# kernels before the bulk (pressure tensor and force next to the particles,
+# link sums and particle update, boundary collide-stream), the fused bulk
+# kernel (chemical potentials, force, collide-stream), the bulk transport,
+# the boundary transport, covering
+KERNEL_CLASSES = ("k_particles", "k_fused", "k_scalars", "k_scalars_particles", "k_cover")
 
 
 def lb_profile_step(h, nsteps: int):
