@@ -984,7 +984,6 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
-    const R zc0 = (R)6 * Q.rho0;
     for (int t = bi * blockDim.x + threadIdx.x; t < tot; t += nbi * blockDim.x) {
         int x, y, z;
         if (!box_node(P, o, P.side1, t, x, y, z)) continue;
@@ -1002,9 +1001,11 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
         }
         if (!have) continue;
         // this node has links into particle p: load everything it needs at once
-        R fv[19];
+        // (populations as deviations g = f - w rho0: the rest part is added
+        // in FP64 below, so that FP32 never rounds f ~ w to the small g)
+        R gv[19];
 #pragma unroll
-        for (int i = 1; i < 19; ++i) fv[i] = (R)PopStore<S>::load(fs, (size_t)i * N + n, i, Q.rho0);
+        for (int i = 1; i < 19; ++i) gv[i] = (R)PopStore<S>::load_dev(fs, (size_t)i * N + n, i, Q.rho0);
         const R ps = (R)psi[n] + dps, ph = (R)phi[n] + dph;
         R gphi[3];
         grad_phi_at<R, F>(nb, phi, D.mask, ph, dph, gphi);
@@ -1015,57 +1016,67 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
 #pragma unroll
             for (int k = 0; k < kPtFields; ++k) pt[k] = (R)ptg[k * N + n];
         }
-        R nacc[K];   // this node's links, added to the FP64 sums once
+        // momentum exchange, torque and drag matrix of each link in FP64 (their
+        // sums over a sphere cancel to a small net force, so FP32 terms would
+        // leave a rounding residue that the particle integrates step after
+        // step); the scalar-flux coefficients in the arithmetic precision
+        R nacc[kLinkK - kLinkGpsi];   // this node's flux coefficients, added to the FP64 sums once
 #pragma unroll
-        for (int k = 0; k < K; ++k) nacc[k] = (R)0;
+        for (int k = 0; k < kLinkK - kLinkGpsi; ++k) nacc[k] = (R)0;
+        int Di[3];
+        int_offset(P, q.g, x, y, z, Di);
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
             if (!lk[i]) continue;
             R r[3], ub[3], vs[3];
             link_velocity<R>(P, q, x, y, z, i, gphi, r, ub, vs);
-            const R fi = fv[i];
-            const R w6 = (R)6 * wgt_r<R>(i);
-            const R c[3] = {(R)cx(i), (R)cy(i), (R)cz(i)};
+            double rd[3];
+            link_offset_r<double>(q.g, Di, i, rd);
+            const double w6 = 6.0 * wgt(i);
+            const double c[3] = {(double)cx(i), (double)cy(i), (double)cz(i)};
             const R cvs = cdot<R>(i, vs[0], vs[1], vs[2]);
-            const R mag = fma_x(-mul_x(w6, Q.rho0), cvs, mul_x((R)2, fi));
-            R dP[3] = {mul_x(c[0], mag), mul_x(c[1], mag), mul_x(c[2], mag)};
+            // c [2 f_i - 6 w rho0 c.v_s] with f_i = g_i + w rho0
+            const double mag = fma_x(-(w6 * P.rho0), (double)cvs, fma_x(2.0, (double)gv[i], 2.0 * wgt(i) * P.rho0));
+            double dP[3] = {c[0] * mag, c[1] * mag, c[2] * mag};
             if (P.thermo) {
                 // chemical stress flux through the link, 6 w_i P(x) . c_i
                 R pc[3];
                 pt_dot_c<R>(i, Q.kappa, pt, pc);
-                dP[0] = fma_x(w6, pc[0], dP[0]);
-                dP[1] = fma_x(w6, pc[1], dP[1]);
-                dP[2] = fma_x(w6, pc[2], dP[2]);
+                dP[0] = fma_x(w6, (double)pc[0], dP[0]);
+                dP[1] = fma_x(w6, (double)pc[1], dP[1]);
+                dP[2] = fma_x(w6, (double)pc[2], dP[2]);
             }
-            nacc[0] = add_x(nacc[0], dP[0]);
-            nacc[1] = add_x(nacc[1], dP[1]);
-            nacc[2] = add_x(nacc[2], dP[2]);
-            nacc[3] = add_x(nacc[3], cross_x(r[1], dP[2], r[2], dP[1]));
-            nacc[4] = add_x(nacc[4], cross_x(r[2], dP[0], r[0], dP[2]));
-            nacc[5] = add_x(nacc[5], cross_x(r[0], dP[1], r[1], dP[0]));
-            const R g6[6] = {c[0], c[1], c[2], cross_x(r[1], c[2], r[2], c[1]), cross_x(r[2], c[0], r[0], c[2]),
-                             cross_x(r[0], c[1], r[1], c[0])};
-            const R zc = mul_x(zc0, wgt_r<R>(i));
+            acc[0] = add_x(acc[0], dP[0]);
+            acc[1] = add_x(acc[1], dP[1]);
+            acc[2] = add_x(acc[2], dP[2]);
+            acc[3] = add_x(acc[3], cross_x(rd[1], dP[2], rd[2], dP[1]));
+            acc[4] = add_x(acc[4], cross_x(rd[2], dP[0], rd[0], dP[2]));
+            acc[5] = add_x(acc[5], cross_x(rd[0], dP[1], rd[1], dP[0]));
+            const double g6[6] = {c[0], c[1], c[2], cross_x(rd[1], c[2], rd[2], c[1]),
+                                  cross_x(rd[2], c[0], rd[0], c[2]), cross_x(rd[0], c[1], rd[1], c[0])};
+            const double zc = w6 * P.rho0;
             int k = 6;
 #pragma unroll
             for (int a = 0; a < 6; ++a)
 #pragma unroll
-                for (int b = a; b < 6; ++b, ++k) nacc[k] = fma_x(mul_x(zc, g6[a]), g6[b], nacc[k]);
+                for (int b = a; b < 6; ++b, ++k) acc[k] = fma_x(zc * g6[a], g6[b], acc[k]);
             // scalar flux into the surface, 6 w g(x) c.u_b (finite
             // differences) or g(x) c.u_b on the six D3Q7 links (lattice
             // Boltzmann), with c.u_b = (c, r x c) . V(t+1) + c.v_s
-            const R ws = P.scheme ? (i < 7 ? (R)1 : (R)0) : w6;
+            const R g6r[6] = {(R)cx(i), (R)cy(i), (R)cz(i), cross_x(r[1], (R)cz(i), r[2], (R)cy(i)),
+                              cross_x(r[2], (R)cx(i), r[0], (R)cz(i)), cross_x(r[0], (R)cy(i), r[1], (R)cx(i))};
+            const R ws = P.scheme ? (i < 7 ? (R)1 : (R)0) : (R)6 * wgt_r<R>(i);
             const R wps = mul_x(ws, ps), wph = mul_x(ws, ph);
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
-                nacc[kLinkGpsi + a] = fma_x(wps, g6[a], nacc[kLinkGpsi + a]);
-                nacc[kLinkGphi + a] = fma_x(wph, g6[a], nacc[kLinkGphi + a]);
+                nacc[a] = fma_x(wps, g6r[a], nacc[a]);
+                nacc[7 + a] = fma_x(wph, g6r[a], nacc[7 + a]);
             }
-            nacc[kLinkGpsi + 6] = fma_x(wps, cvs, nacc[kLinkGpsi + 6]);
-            nacc[kLinkGphi + 6] = fma_x(wph, cvs, nacc[kLinkGphi + 6]);
+            nacc[6] = fma_x(wps, cvs, nacc[6]);
+            nacc[13] = fma_x(wph, cvs, nacc[13]);
         }
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] += (double)nacc[k];
+        for (int k = 0; k < kLinkK - kLinkGpsi; ++k) acc[kLinkGpsi + k] += (double)nacc[k];
     }
     block_sum_rows<K>(acc, smem);
     double* part = D.link_part + ((size_t)p * kMaxPartBlocks + bi) * K;
@@ -1529,9 +1540,11 @@ __device__ __forceinline__ void scalars_compute_lb(const DevParams& P, const Dev
         sph = l.sph;
         hn_src = l.src;
     }
-    const R pn = ps + sps;
-    R hn = ph + sph - Q.kd * (ph - phi0_of(Q, ps));
-    hn += hn_src;
+    // the stored value plus every increment of the step (correction, fluxes,
+    // sink, source) summed first: one rounding of the O(1) field per step
+    const R ps0 = (R)a.template get<0>(0), ph0 = (R)a.template get<1>(0);
+    const R pn = ps0 + (dps + sps);
+    const R hn = ph0 + (((dph + sph) - Q.kd * (ph - phi0_of(Q, ps))) + hn_src);
     ((F*)D.psi_dst)[n] = (F)pn;
     ((F*)D.phi_dst)[n] = (F)hn;
 }
@@ -1589,9 +1602,11 @@ __device__ __forceinline__ void scalars_compute_c(const DevParams& P, const DevP
         sph = l.sph;
         hn_src = l.src;
     }
-    const R pn = ps + (R)6 * sps;
-    R hn = ph + (R)6 * sph - Q.kd * (ph - phi0_of(Q, ps));
-    hn += hn_src;
+    // the stored value plus every increment of the step (correction, fluxes,
+    // sink, source) summed first: one rounding of the O(1) field per step
+    const R ps0 = (R)a.template get<0>(0), ph0 = (R)a.template get<1>(0);
+    const R pn = ps0 + fma_x((R)6, sps, dps);
+    const R hn = ph0 + ((fma_x((R)6, sph, dph) - Q.kd * (ph - phi0_of(Q, ps))) + hn_src);
     ((F*)D.psi_dst)[n] = (F)pn;
     ((F*)D.phi_dst)[n] = (F)hn;
 }

@@ -169,65 +169,109 @@ def test_plain_config_fp32():
     assert np.max(np.abs(pg["pos"] - pr["pos"])) / 4.0 < TOL32
 
 
+def _dist_to_centre(shape, periodic, pos):
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    d = [x - pos[0], y - pos[1], z - pos[2]]
+    for a, L in enumerate((nx, ny, nz)):
+        if periodic[a]:
+            d[a] = d[a] - L * np.round(d[a] / L)
+    return np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+
+
+def _rms_rel(a, b, mask):
+    sel = mask == 0
+    aa, bb = a[..., sel], b[..., sel]
+    return float(np.sqrt(np.mean((aa - bb) ** 2)) / np.sqrt(np.mean(bb ** 2)))
+
+
 def test_plain_config_fp32_1000_steps():
-    """FP32 over the 1000 steps of the FP64 bar.  A moving sphere covers and
-    uncovers nodes; a node whose distance to the surface sits within the
-    FP32/FP64 trajectory gap of R flips one step apart in the two runs, which
-    leaves a local difference of ~3e-4 in psi at that node and a velocity
-    change that spreads through the box.  What must hold at any length: the
-    masks, the trajectory (|dX|/R <= 1e-4) and psi, phi, rho beyond R + 4 from
-    the sphere (norm-relative <= 1e-4)."""
+    """FP32 over the 1000 steps of the FP64 bar, with a free sphere moving
+    through the lattice.  The masks are compared at every step: until the two
+    runs first cover or uncover a node at different steps, u, psi, phi and rho
+    hold 1e-4 norm-relative on the whole box (checked every 100 steps).  Such
+    a node lies within the FP32/FP64 trajectory gap of the sphere surface; its
+    one-step offset starts a local transient whose pressure wave reaches the
+    whole box, so beyond that step only the trajectory (|dX|/R <= 1e-4) and
+    the masks (equal again at the end) are held to the bar."""
     wl = W.plain_fp64(seed=3)
     box, ref = make_pair(wl.params, wl.fields, wl.particles, precision="fp32")
+    R = wl.particles[0]["R"]
+    first_mismatch = None
+    checked = 0
+    for step in range(1, 1001):
+        box.step(1)
+        ref.step(1)
+        mg, mr = box.mask(), ref.mask()
+        if first_mismatch is None and not np.array_equal(mg, mr):
+            first_mismatch = step
+            # every node covered at a different step sits at the surface
+            dist = _dist_to_centre(mr.shape, wl.params["periodic"], ref.particles()[0]["pos"])
+            assert np.all(np.abs(dist[mg != mr] - R) < 1e-4 * R)
+        if first_mismatch is None and step % 100 == 0:
+            fg, fr = box.fields(), ref.fields()
+            for k in ("u", "psi", "phi", "rho"):
+                assert norm_rel(fg[k], fr[k], mr) < TOL32, (k, step)
+            checked = step
+    assert checked >= 500
+    assert np.array_equal(box.mask(), ref.mask())
+    pg, pr = box.particles()[0], ref.particles()[0]
+    assert np.max(np.abs(pg["pos"] - pr["pos"])) / R < TOL32
+
+
+def test_fixed_active_sphere_fp32_1000_steps():
+    """1000 FP32 steps of a box with every term of the step active -- the
+    interface, solubility coupling (E != 0), a wetting Janus sphere with
+    production and unequal phoretic mobilities, the sink -- and the sphere
+    held in place, so that no node is covered: u, psi, phi, rho within 1e-4
+    norm-relative of the FP64 oracle on the whole box (RMS-relative reported
+    in the assertion message)."""
+    wl = W.plain_fp64(seed=5)
+    params = dict(wl.params, E=0.3, phi_b=1.0, k_d=2e-3)
+    part = dict(wl.particles[0], theta_c_deg=60.0, alpha=1e-2, mu_plus=0.1, mu_minus=-0.05, fixed=1)
+    box, ref = make_pair(params, wl.fields, [part], precision="fp32")
     box.step(1000)
     ref.step(1000)
-    mg = ref.mask()
-    assert np.array_equal(box.mask(), mg)
-    pg, pr = box.particles()[0], ref.particles()[0]
-    R = wl.particles[0]["R"]
-    assert np.max(np.abs(pg["pos"] - pr["pos"])) / R < TOL32
-    n = wl.params["nx"]
-    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
-    d = [x - pr["pos"][0], y - pr["pos"][1], z - pr["pos"][2]]
-    d[0] -= n * np.round(d[0] / n)
-    d[1] -= n * np.round(d[1] / n)
-    far = np.where((d[0] ** 2 + d[1] ** 2 + d[2] ** 2) > (R + 4.0) ** 2, 0, 1).astype(np.uint8)
-    far = np.maximum(far, mg)   # norm_rel compares where this mask is 0
+    mr = ref.mask()
+    assert np.array_equal(box.mask(), mr)
     fg, fr = box.fields(), ref.fields()
-    for k in ("psi", "phi", "rho"):
-        assert norm_rel(fg[k], fr[k], far) < TOL32, k
+    for k in ("u", "psi", "phi", "rho"):
+        e = norm_rel(fg[k], fr[k], mr)
+        assert e < TOL32, (k, e, _rms_rel(fg[k], fr[k], mr))
 
 
-@pytest.mark.parametrize("prec,tol", [("fp16", 3e-2), ("bf16", 1e-1)])
-def test_reduced_storage_error_vs_oracle(prec, tol):
-    """FP16/BF16 population storage: error against the FP64 oracle stays small
-    (reported, not a parity bar)."""
-    wl = W.plain_fp64(seed=0)
+@pytest.mark.parametrize("prec,tol_u,tol_s", [("fp16", 1e-2, 5e-3), ("bf16", 5e-2, 5e-3)])
+def test_reduced_storage_error_vs_oracle(prec, tol_u, tol_s):
+    """FP16/BF16 population storage after 200 steps of the plain
+    configuration: a band around the error the 16-bit deviation storage
+    reaches (measured: FP16 u 3.4e-3, phi 2.1e-3, psi 1.4e-4, rho 2.1e-5;
+    BF16 u 9.4e-3, phi 2.1e-3), not the 1e-4 FP32 bar, which these forms miss
+    by about 30x on u."""
+    wl = W.plain_fp64(seed=3)
     box, ref = make_pair(wl.params, wl.fields, wl.particles, precision=prec)
-    box.step(100)
-    ref.step(100)
-    # the particle may cover slightly different nodes: compare where both are fluid
+    box.step(200)
+    ref.step(200)
     mg = (ref.mask() | box.mask()).astype(np.uint8)
     fg, fr = box.fields(), ref.fields()
+    assert norm_rel(fg["u"], fr["u"], mg) < tol_u
     for k in ("psi", "phi", "rho"):
-        assert norm_rel(fg[k], fr[k], mg) < tol, k
+        assert norm_rel(fg[k], fr[k], mg) < tol_s, k
 
 
-def test_full_size_interface_fp32_two_steps():
+def test_full_size_interface_fp32_100_steps():
     """The 128^3 single-particle interface workload in the launch configuration
-    the benchmark times, two steps against the oracle (whole fields)."""
+    the benchmark times, 100 steps against the oracle: every field, velocity
+    included, within 1e-4 of its maximum over the whole box."""
     wl = W.interface(theta_c_deg=60.0, solubility_ratio=2.0, mobility=0.1)
     assert W.min_node_surface_gap(wl) > 1e-6
     box, ref = make_pair(wl.params, wl.fields, wl.particles, precision="fp32")
-    box.step(2)
-    ref.step(2)
+    box.step(100)
+    ref.step(100)
     mg = ref.mask()
     assert np.array_equal(box.mask(), mg)
     fg, fr = box.fields(), ref.fields()
-    for k in ("psi", "phi", "rho"):
+    for k in ("u", "psi", "phi", "rho"):
         assert norm_rel(fg[k], fr[k], mg) < TOL32, k
-    # the velocity starts from rest: compare it on its own scale
-    assert norm_rel(fg["u"], fr["u"], mg) < 1e-3
     pg, pr = box.particles()[0], ref.particles()[0]
     assert np.max(np.abs(pg["pos"] - pr["pos"])) / 8.0 < TOL32
 
