@@ -65,7 +65,8 @@ enum {
     LB_ERR_OVERLAP = -4,   /* particles met, or a particle reached a wall  */
     LB_ERR_CUDA = -5,      /* a CUDA call failed                           */
     LB_ERR_TIMEOUT = -6,   /* reserved: a bounded device wait expired      */
-    LB_ERR_STATE = -7      /* call not valid in the handle's current state */
+    LB_ERR_STATE = -7,     /* call not valid in the handle's current state */
+    LB_ERR_CANCELLED = -8  /* a served request was cancelled (lbs_cancel)  */
 };
 
 /* Box and model parameters (Sec. "Numerical details" gives the paper's
@@ -141,7 +142,9 @@ void lb_destroy(lb_handle* h);
 /* Set the fields from host arrays rho [N], u [3][N], psi [N], phi [N] (any may
  * be NULL to keep the current field) and reset the populations to the
  * second-order equilibrium of (rho, u) (Sec. "Numerical details": the system
- * starts from equilibrium).  Values at nodes inside particles are ignored. */
+ * starts from equilibrium).  Values at nodes inside particles are ignored.
+ * A NaN or Inf in a given array (at any node) returns LB_ERR_NONFINITE and
+ * leaves the box unchanged. */
 int lb_set_fields(lb_handle* h, const double* rho, const double* u,
                   const double* psi, const double* phi);
 
@@ -193,6 +196,24 @@ int lb_read_populations(lb_handle* h, double* f);
 
 /* Copy the solid mask [N]: 0 fluid, k+1 inside particle k.  Synchronises. */
 int lb_read_mask(lb_handle* h, unsigned char* mask);
+
+/* Checkpoint and restart (no counterpart in the paper: a run can be stopped
+ * and continued).  lb_state_bytes gives the size of a checkpoint of h.
+ * lb_save_state copies the whole state after the last step into the host
+ * buffer buf (bytes >= lb_state_bytes, else LB_ERR_PARAM): populations,
+ * psi, phi and u in the box's storage precision, the solid mask and the
+ * boundary flags, every particle record (position, velocity, spin,
+ * orientation and the covering impulses it carries into the next step), the
+ * pending uniform psi/phi correction, the fluid-node count and the error
+ * word.  Synchronises.  lb_load_state restores such a checkpoint into a box
+ * created with the same lattice size, axes, precision, transport scheme and
+ * model parameters (LB_ERR_PARAM otherwise, nothing changed); its particles
+ * are replaced by the checkpoint's.  A box of a batch cannot be restored into
+ * (LB_ERR_STATE).  Stepping the restored box then gives the
+ * same bits as stepping the saved one. */
+int lb_state_bytes(const lb_handle* h, size_t* bytes);
+int lb_save_state(lb_handle* h, void* buf, size_t bytes);
+int lb_load_state(lb_handle* h, const void* buf, size_t bytes);
 
 /* Copy up to cap particle states; *n_out (may be NULL) gets the count. */
 int lb_read_particles(lb_handle* h, lb_particle_state* out, int cap, int* n_out);

@@ -162,6 +162,12 @@ int lbs_submit(lbs_server* s, const lbs_request* r, long long* id);
  * point.  *active and *queued (optional) receive the resident and waiting
  * request counts after the round. */
 int lbs_pump(lbs_server* s, double now, int* active, int* queued);
+/* Cancel request id between pumps: a queued request leaves the queue, a
+ * resident one leaves the batch and frees its memory at once; either way its
+ * result (status LB_ERR_CANCELLED, done = now, nothing written to its output
+ * buffers) is posted for lbs_poll.  LB_ERR_PARAM for an id that is neither
+ * queued nor resident (unknown, or already finished). */
+int lbs_cancel(lbs_server* s, long long id, double now);
 /* Finished results, oldest first; *n receives how many were written. */
 int lbs_poll(lbs_server* s, lbs_result* out, int cap, int* n);
 /* The batch the server runs (for tuning and diagnostics). */

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <new>
+#include <cmath>
 #include <vector>
 
 #include "lbdp.h"
@@ -250,8 +251,18 @@ void lb_destroy(lb_handle* h)
 int lb_set_fields(lb_handle* h, const double* rho, const double* u, const double* psi, const double* phi)
 {
     if (!h) return LB_ERR_PARAM;
-    cudaSetDevice(h->device);
     const size_t N = (size_t)h->dp.N;
+    // a non-finite input would spread through the whole box in a few steps:
+    // refuse it before anything is copied
+    const struct {
+        const double* a;
+        size_t n;
+    } in[4] = {{rho, N}, {u, 3 * N}, {psi, N}, {phi, N}};
+    for (const auto& v : in)
+        if (v.a)
+            for (size_t k = 0; k < v.n; ++k)
+                if (!std::isfinite(v.a[k])) return LB_ERR_NONFINITE;
+    cudaSetDevice(h->device);
     cudaStream_t s = h->stream;
     double* st_rho = h->staging;
     double* st_u = h->staging + N;
@@ -494,6 +505,145 @@ int lb_read_mask(lb_handle* h, unsigned char* mask)
     return LB_OK;
 }
 
+// Checkpoint blob: header, then the arrays of the current state in a fixed
+// order (current-parity buffers; the correction pair of the current parity
+// first).
+namespace {
+constexpr unsigned long long kStateMagic = 0x4C42445053544154ull;   // "LBDPSTAT"
+struct StateHeader {
+    unsigned long long magic;
+    int version, nx, ny, nz, precision, scheme, thermo, np;
+    int periodic[3];
+    double tau, rho0, g[3], A, kappa, Mpsi, C, Mphi, E, phib, kd;
+};
+
+size_t state_layout(const lb_handle* h, int np, size_t* off)
+{
+    const size_t N = (size_t)h->dp.N;
+    const size_t pb = (size_t)h->ops->pop_bytes, fb = (size_t)h->ops->fld_bytes;
+    const size_t sz[] = {sizeof(StateHeader), 19 * N * pb, N * fb, N * fb, 3 * N * fb, N, N,
+                         (size_t)np * sizeof(DevPart), 8 * sizeof(double), sizeof(long long), sizeof(int)};
+    size_t o = 0;
+    for (int k = 0; k < 11; ++k) {
+        if (off) off[k] = o;
+        o += (sz[k] + 15) & ~(size_t)15;
+    }
+    return o;
+}
+
+void fill_header(const lb_handle* h, int np, StateHeader& H)
+{
+    memset(&H, 0, sizeof(H));
+    H.magic = kStateMagic;
+    H.version = 1;
+    H.nx = h->dp.nx;
+    H.ny = h->dp.ny;
+    H.nz = h->dp.nz;
+    H.precision = h->prm.precision;
+    H.scheme = h->dp.scheme;
+    H.thermo = h->dp.thermo;
+    H.np = np;
+    for (int a = 0; a < 3; ++a) {
+        H.periodic[a] = h->dp.per[a];
+        H.g[a] = h->dp.g[a];
+    }
+    H.tau = h->dp.tau;
+    H.rho0 = h->dp.rho0;
+    H.A = h->dp.A;
+    H.kappa = h->dp.kappa;
+    H.Mpsi = h->dp.Mpsi;
+    H.C = h->dp.C;
+    H.Mphi = h->dp.Mphi;
+    H.E = h->dp.E;
+    H.phib = h->dp.phib;
+    H.kd = h->dp.kd;
+}
+}  // namespace
+
+int lb_state_bytes(const lb_handle* h, size_t* bytes)
+{
+    if (!h || !bytes) return LB_ERR_PARAM;
+    *bytes = state_layout(h, h->dp.np, nullptr);
+    return LB_OK;
+}
+
+int lb_save_state(lb_handle* h, void* buf, size_t bytes)
+{
+    if (!h || !buf) return LB_ERR_PARAM;
+    size_t off[11];
+    if (bytes < state_layout(h, h->dp.np, off)) return LB_ERR_PARAM;
+    cudaSetDevice(h->device);
+    unsigned char* b = (unsigned char*)buf;
+    const size_t N = (size_t)h->dp.N;
+    const size_t pb = (size_t)h->ops->pop_bytes, fb = (size_t)h->ops->fld_bytes;
+    const int c = h->cur;
+    StateHeader H;
+    fill_header(h, h->dp.np, H);
+    memcpy(b + off[0], &H, sizeof(H));
+    cudaStream_t s = h->stream;
+    LB_TRY(cudaMemcpyAsync(b + off[1], h->f[c], 19 * N * pb, cudaMemcpyDeviceToHost, s));
+    LB_TRY(cudaMemcpyAsync(b + off[2], h->psi[c], N * fb, cudaMemcpyDeviceToHost, s));
+    LB_TRY(cudaMemcpyAsync(b + off[3], h->phi[c], N * fb, cudaMemcpyDeviceToHost, s));
+    LB_TRY(cudaMemcpyAsync(b + off[4], h->u, 3 * N * fb, cudaMemcpyDeviceToHost, s));
+    LB_TRY(cudaMemcpyAsync(b + off[5], h->mask[c], N, cudaMemcpyDeviceToHost, s));
+    LB_TRY(cudaMemcpyAsync(b + off[6], h->bflag, N, cudaMemcpyDeviceToHost, s));
+    if (h->dp.np > 0)
+        LB_TRY(cudaMemcpyAsync(b + off[7], h->parts, (size_t)h->dp.np * sizeof(DevPart), cudaMemcpyDeviceToHost, s));
+    LB_TRY(cudaMemcpyAsync(b + off[8], h->corr + 4 * c, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LB_TRY(cudaMemcpyAsync(b + off[8] + 4 * sizeof(double), h->corr + 4 * (c ^ 1), 4 * sizeof(double),
+                           cudaMemcpyDeviceToHost, s));
+    LB_TRY(cudaMemcpyAsync(b + off[9], h->nfluid, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    LB_TRY(cudaMemcpyAsync(b + off[10], h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LB_TRY(cudaStreamSynchronize(s));
+    return LB_OK;
+}
+
+int lb_load_state(lb_handle* h, const void* buf, size_t bytes)
+{
+    if (!h || !buf || bytes < sizeof(StateHeader)) return LB_ERR_PARAM;
+    if (h->batch) return LB_ERR_STATE;   // a batch member's launch plans hold its particle boxes
+    const unsigned char* b = (const unsigned char*)buf;
+    StateHeader H, mine;
+    memcpy(&H, b, sizeof(H));
+    if (H.magic != kStateMagic || H.version != 1 || H.np < 0 || H.np > kMaxParticles) return LB_ERR_PARAM;
+    fill_header(h, H.np, mine);
+    if (memcmp(&H, &mine, sizeof(H)) != 0) return LB_ERR_PARAM;   // another box or model
+    size_t off[11];
+    if (bytes < state_layout(h, H.np, off)) return LB_ERR_PARAM;
+    cudaSetDevice(h->device);
+    const size_t N = (size_t)h->dp.N;
+    const size_t pb = (size_t)h->ops->pop_bytes, fb = (size_t)h->ops->fld_bytes;
+    const int c = h->cur;
+    cudaStream_t s = h->stream;
+    LB_TRY(cudaStreamSynchronize(s));
+    std::vector<DevPart> parts((size_t)H.np);
+    if (H.np > 0) memcpy(parts.data(), b + off[7], (size_t)H.np * sizeof(DevPart));
+    LB_TRY(cudaMemcpyAsync(h->f[c], b + off[1], 19 * N * pb, cudaMemcpyHostToDevice, s));
+    LB_TRY(cudaMemcpyAsync(h->psi[c], b + off[2], N * fb, cudaMemcpyHostToDevice, s));
+    LB_TRY(cudaMemcpyAsync(h->phi[c], b + off[3], N * fb, cudaMemcpyHostToDevice, s));
+    LB_TRY(cudaMemcpyAsync(h->u, b + off[4], 3 * N * fb, cudaMemcpyHostToDevice, s));
+    LB_TRY(cudaMemcpyAsync(h->mask[c], b + off[5], N, cudaMemcpyHostToDevice, s));
+    // the other mask buffer holds the same mask: covering writes only the
+    // cover box of each sphere into it
+    LB_TRY(cudaMemcpyAsync(h->mask[c ^ 1], b + off[5], N, cudaMemcpyHostToDevice, s));
+    LB_TRY(cudaMemcpyAsync(h->bflag, b + off[6], N, cudaMemcpyHostToDevice, s));
+    if (H.np > 0)
+        LB_TRY(cudaMemcpyAsync(h->parts, parts.data(), (size_t)H.np * sizeof(DevPart), cudaMemcpyHostToDevice, s));
+    LB_TRY(cudaMemcpyAsync(h->corr + 4 * c, b + off[8], 4 * sizeof(double), cudaMemcpyHostToDevice, s));
+    LB_TRY(cudaMemcpyAsync(h->corr + 4 * (c ^ 1), b + off[8] + 4 * sizeof(double), 4 * sizeof(double),
+                           cudaMemcpyHostToDevice, s));
+    LB_TRY(cudaMemcpyAsync(h->nfluid, b + off[9], sizeof(long long), cudaMemcpyHostToDevice, s));
+    LB_TRY(cudaMemcpyAsync(h->err, b + off[10], sizeof(int), cudaMemcpyHostToDevice, s));
+    LB_TRY(cudaStreamSynchronize(s));
+    h->host_parts = parts;
+    h->dp.np = H.np;
+    h->rmax = 0.0;
+    for (const DevPart& q : parts)
+        if (q.R > h->rmax) h->rmax = q.R;
+    update_sides(h);
+    return LB_OK;
+}
+
 int lb_read_particles(lb_handle* h, lb_particle_state* out, int cap, int* n_out)
 {
     if (!h || cap < 0 || (cap > 0 && !out)) return LB_ERR_PARAM;
@@ -540,6 +690,7 @@ const char* lb_error_string(int status)
         case LB_ERR_CUDA: return "CUDA call failed";
         case LB_ERR_TIMEOUT: return "device wait expired";
         case LB_ERR_STATE: return "call not valid in this state";
+        case LB_ERR_CANCELLED: return "request cancelled";
         default: return "unknown status";
     }
 }

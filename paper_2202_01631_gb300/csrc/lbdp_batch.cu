@@ -628,6 +628,10 @@ void finish(lbs_server* s, Live& L, int status, double t_done)
     res.arrival = L.q.r.arrival;
     res.admitted = L.admitted;
     res.status = status;
+    if (L.h && status == LB_ERR_CANCELLED) {
+        lb_destroy(L.h);   // results of a cancelled request are not read
+        L.h = nullptr;
+    }
     if (L.h) {
         int n = 0;
         int st = lb_read_particles(L.h, res.particles, 4, &n);
@@ -773,6 +777,30 @@ int lbs_pump(lbs_server* s, double now, int* active, int* queued)
     if (active) *active = (int)s->live.size();
     if (queued) *queued = (int)s->queue.size();
     return st;
+}
+
+int lbs_cancel(lbs_server* s, long long id, double now)
+{
+    if (!s) return LB_ERR_PARAM;
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+        if (it->id != id) continue;
+        Live L;
+        L.q = std::move(*it);
+        L.h = nullptr;
+        L.admitted = -1.0;   // never admitted
+        s->queue.erase(it);
+        finish(s, L, LB_ERR_CANCELLED, now);
+        return LB_OK;
+    }
+    for (size_t i = 0; i < s->live.size(); ++i) {
+        if (s->live[i].q.id != id) continue;
+        // between pumps nothing of the batch is in flight (lbs_pump ends with
+        // a stream synchronisation), so the box can leave at once
+        finish(s, s->live[i], LB_ERR_CANCELLED, now);
+        s->live.erase(s->live.begin() + i);
+        return LB_OK;
+    }
+    return LB_ERR_PARAM;
 }
 
 int lbs_poll(lbs_server* s, lbs_result* out, int cap, int* n)

@@ -110,6 +110,9 @@ def _load():
         "lb_read_mask": (C.c_int, [h, P(C.c_ubyte)]),
         "lb_read_particles": (C.c_int, [h, P(LbParticleState), C.c_int, P(C.c_int)]),
         "lb_conservation": (C.c_int, [h, dp]),
+        "lb_state_bytes": (C.c_int, [h, P(C.c_size_t)]),
+        "lb_save_state": (C.c_int, [h, C.c_void_p, C.c_size_t]),
+        "lb_load_state": (C.c_int, [h, C.c_void_p, C.c_size_t]),
         "lb_totals_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
         "lb_device_bytes": (C.c_int, [P(LbParams), P(C.c_size_t)]),
@@ -141,6 +144,7 @@ def _load():
         "lbs_submit": (C.c_int, [h, P(LbsRequest), P(C.c_longlong)]),
         "lbs_pump": (C.c_int, [h, C.c_double, P(C.c_int), P(C.c_int)]),
         "lbs_poll": (C.c_int, [h, P(LbsResult), C.c_int, P(C.c_int)]),
+        "lbs_cancel": (C.c_int, [h, C.c_longlong, C.c_double]),
         "lbs_batch": (h, [h]),
     }
     for name, (res, args) in sig.items():
@@ -530,6 +534,10 @@ class Server:
         _check(_lib.lbs_pump(self.h, float(now), C.byref(a), C.byref(q)), "lbs_pump")
         return a.value, q.value
 
+    def cancel(self, rid: int, now: float = 0.0):
+        """Cancel a queued or resident request (:func:`lbs_cancel`)."""
+        _check(_lib.lbs_cancel(self.h, int(rid), float(now)), "lbs_cancel")
+
     def poll(self, cap: int = 64) -> List[Dict]:
         out = (LbsResult * cap)()
         n = C.c_int(0)
@@ -628,6 +636,24 @@ class Box:
         f = np.empty(19 * self.N)
         _check(_lib.lb_read_populations(self.h, _dptr(f)), "lb_read_populations")
         return f.reshape((19,) + self.shape)
+
+    def save_state(self) -> bytes:
+        """The whole state after the last step (:func:`lb_save_state`)."""
+        n = C.c_size_t(0)
+        _check(_lib.lb_state_bytes(self.h, C.byref(n)), "lb_state_bytes")
+        buf = (C.c_ubyte * n.value)()
+        _check(_lib.lb_save_state(self.h, buf, n.value), "lb_save_state")
+        return bytes(buf)
+
+    def load_state(self, blob: bytes):
+        """Restore a state saved from a box of the same size and model
+        (:func:`lb_load_state`); its particles replace this box's."""
+        buf = (C.c_ubyte * len(blob)).from_buffer_copy(blob)
+        _check(_lib.lb_load_state(self.h, buf, len(blob)), "lb_load_state")
+        self.np = len(self.particles_raw())
+
+    def particles_raw(self):
+        return lb_read_particles(self.h, 64)
 
     def mask(self) -> np.ndarray:
         m = np.empty(self.N, dtype=np.uint8)

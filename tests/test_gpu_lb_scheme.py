@@ -133,19 +133,18 @@ def test_lb_plain_config_fp32(lbdp):
     assert np.max(np.abs(pg["pos"] - pr["pos"])) / 4.0 < TOL32
 
 
-def test_lb_full_size_interface_fp32_two_steps(lbdp):
-    """The 128^3 interface workload with the LB transport, two steps, whole
-    fields against the oracle."""
+def test_lb_full_size_interface_fp32_100_steps(lbdp):
+    """The 128^3 interface workload with the LB transport, 100 steps: every
+    field, velocity included, within 1e-4 of its maximum over the whole box."""
     wl = W.interface(theta_c_deg=60.0, solubility_ratio=2.0, mobility=0.1)
     box, ref = make_pair(dict(wl.params, **LB), wl.fields, wl.particles, precision="fp32")
-    box.step(2)
-    ref.step(2)
+    box.step(100)
+    ref.step(100)
     mg = ref.mask()
     assert np.array_equal(box.mask(), mg)
     fg, fr = box.fields(), ref.fields()
-    for k in ("psi", "phi", "rho"):
+    for k in ("u", "psi", "phi", "rho"):
         assert norm_rel(fg[k], fr[k], mg) < TOL32, k
-    assert norm_rel(fg["u"], fr["u"], mg) < 1e-3
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
