@@ -619,9 +619,8 @@ def run_batched(args):
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
         "config": {"workload": "batched_%d_boxes_32-96" % len(wls), "nodes": nodes, "precision": args.precision,
                    "steps_per_sim": target, "spheres_per_box": 1,
-                   "tuned": {nc: {"threads": t, "cells": c, "regs": "loose" if r else "tight", "ms": m}
-                             for nc, (t, c, r), m in zip(("mu", "force", "collide", "transport"), shapes,
-                                                         tune_ms)},
+                   "tuned": {nc: {"threads": t, "planes_per_block": z, "ms": m}
+                             for nc, (t, z), m in zip(lbdp.BATCH_KERNEL_CLASSES, shapes, tune_ms)},
                    "l2": "state %.1f GB > L2 (129 MB); no flush" % (batch_bytes(lbdp, wls, args.precision) / 1e9)},
         "mlups": mlups,
         "one_by_one": {"sims_per_hour": alone_sims_h, "ms_per_step_all_boxes": alone_ms,

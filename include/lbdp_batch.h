@@ -89,25 +89,24 @@ int lbb_get_steps(const lbb_batch* b, const lb_handle* h, long long* left);
  * launches the call queued (graph nodes included). */
 int lbb_run(lbb_batch* b, int nsteps, long long* launches);
 
-/* Autotune the launch configuration of the four node kernels (chemical
- * potentials, force, collide-stream, transport) on the current boxes: each
- * candidate (threads per block, cells per thread, register budget) is timed
- * over reps launches and the fastest kept.  The kernels only rewrite their
- * own outputs (the stored velocity is saved and restored), so tuning leaves
- * the state unchanged.  cfg_out[4] (optional): the chosen
- * candidate per kernel; ms_out[4] (optional): its time per launch.  Results do
+/* Autotuning.  The two bulk kernels of a batched step -- the fused one
+ * (chemical potentials, stress, force, collide-stream) and the transport --
+ * march along z through 32 x 8 column tiles of every box; a block takes one z
+ * chunk of a box.  The chunk length is the tuned shape: lbb_tune times each
+ * candidate of each kernel over reps launches on the current boxes and keeps
+ * the fastest.  The kernels only rewrite their own outputs (the stored
+ * velocity is saved and restored), so tuning leaves the state unchanged.
+ * cfg_out[LBB_KERNEL_CLASSES] (optional): the chosen candidate per kernel
+ * (0 fused, 1 transport); ms_out (optional): its time per launch.  Results do
  * not depend on the configuration. */
-int lbb_tune(lbb_batch* b, int reps, int cfg_out[4], double ms_out[4]);
-/* Set the candidates directly (cfg[k] in [0, lbb_num_configs()); candidate
- * 4 -- 32 x 4 x 4 tiles staged in shared memory -- exists for the force and
- * transport kernels (k = 1, 3) only). */
-int lbb_set_config(lbb_batch* b, const int cfg[4]);
+#define LBB_KERNEL_CLASSES 2
+int lbb_tune(lbb_batch* b, int reps, int cfg_out[LBB_KERNEL_CLASSES], double ms_out[LBB_KERNEL_CLASSES]);
+/* Set the candidates directly (cfg[k] in [0, lbb_num_configs())). */
+int lbb_set_config(lbb_batch* b, const int cfg[LBB_KERNEL_CLASSES]);
 int lbb_num_configs(void);
-/* Candidate k: threads per block, cells (nodes) per thread, and the register
- * budget (0: the single-box kernels' budget; 1: a larger one that avoids
- * spills at lower occupancy).  Candidate 4 is the shared-memory tile (two
- * nodes per thread). */
-int lbb_config_shape(int k, int* threads, int* cells, int* regs);
+/* Candidate k: threads per block and planes per block (the z chunk each
+ * thread of the block marches through). */
+int lbb_config_shape(int k, int* threads, int* planes);
 
 /* Wait for the batch stream; report a device error of any member box. */
 int lbb_sync(lbb_batch* b);

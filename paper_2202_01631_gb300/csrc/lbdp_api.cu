@@ -145,12 +145,14 @@ DevPtrs cur_ptrs(const lb_handle* h)
 RowGrid row_grid(const DevParams& P)
 {
     RowGrid g;
-    // z-marching kernels: enough z chunks for about eight waves of two blocks
-    // per SM on 152 SMs, each chunk at least 8 planes long
+    // z-marching kernels: enough z chunks for about six waves of four blocks
+    // per SM on 152 SMs, each chunk at least 6 planes long (measured on GB300:
+    // 256^3 is fastest with chunks of 12 to 24 planes, 128^3 with 6 to 8;
+    // shorter chunks repeat more halo planes, fewer blocks leave SMs idle)
     const long long cols = (long long)((P.nx + 31) / 32) * ((P.ny + 7) / 8);
-    const long long target = 152LL * 2 * 8;
+    const long long target = 152LL * 4 * 6;
     long long chunks = (target + cols - 1) / cols;
-    const long long max_chunks = P.nz / 8 > 1 ? P.nz / 8 : 1;
+    const long long max_chunks = P.nz / 6 > 1 ? P.nz / 6 : 1;
     if (chunks > max_chunks) chunks = max_chunks;
     if (chunks < 1) chunks = 1;
     // no empty chunk: ceil(nz / chunks) planes each

@@ -21,11 +21,6 @@
 
 using namespace lbdp;
 
-namespace lbdp {
-const BatchCfg kBatchCfgs[kNumBatchCfgs] = {
-    {128, 1, 0, 0}, {128, 1, 0, 1}, {256, 1, 1, 1}, {128, 2, 1, 1}, {256, 2, -1, 1}};
-}  // namespace lbdp
-
 // ---------------------------------------------------------------------------
 // arena: first fit over offsets, 256-byte granules, coalescing frees
 // ---------------------------------------------------------------------------
@@ -168,21 +163,16 @@ struct lbb_batch {
     long long* d_left = nullptr;
     std::vector<LaunchPlan> plans;
     int par = 0;            // parity of the steps run since the plans were built
-    int cfg[4] = {0, 0, 0, 0};
+    int cfg[kNumBatchClasses] = {1, 1};   // z chunks of 16 planes until tuned
     cudaGraphExec_t exec[2] = {nullptr, nullptr};   // graphs starting at parity 0 / 1
     SideStream side{};   // particle kernels, overlapping the fluid kernels
 };
 
 namespace {
 
-constexpr int kStepLaunches = 7;   // per launch plan: 4 node kernels, 3 particle kernels
-constexpr int kTilesPerBlock = 8;  // node tiles a block of a box takes
+constexpr int kStepLaunches = 9;   // per launch plan: 2 bulk kernels, 7 particle kernels
 
-// Candidate 4 (shared-memory tiles) exists for the force and transport kernels.
-bool cfg_valid(int nc, int cfg)
-{
-    return cfg >= 0 && cfg < kNumBatchCfgs && (cfg < 4 || nc == 1 || nc == 3);
-}
+bool cfg_valid(int cfg) { return cfg >= 0 && cfg < kNumBatchCfgs; }
 
 int find_member(const lbb_batch* b, const lb_handle* h)
 {
@@ -211,8 +201,8 @@ void rebuild(lbb_batch* b)
         pl.L.left = b->d_left;
         pl.L.base = (int)l * kLaunchBoxes;
         pl.L.nbox = std::min(kLaunchBoxes, nb - pl.L.base);
-        int gmax[kNodeTileSizes] = {1, 1};
-        int tmax = 1, lmax = 1, cmax = 1;
+        int zmax[kNumBatchCfgs] = {1, 1, 1};
+        int lmax = 1, cmax = 1, pmax = 1;
         for (int j = 0; j < pl.L.nbox; ++j) {
             Member& m = b->mem[pl.L.base + j];
             lb_handle* h = m.h;
@@ -222,24 +212,15 @@ void rebuild(lbb_batch* b)
             bd.P = h->dp;
             bd.D[0] = handle_ptrs(h, m.cur0);
             bd.D[1] = handle_ptrs(h, m.cur0 ^ 1);
-            bd.mx = div_magic((unsigned)h->dp.nx);
-            bd.my = div_magic((unsigned)h->dp.ny);
-            for (int k = 0; k < kNodeTileSizes; ++k) {
-                const long long tiles = (h->dp.N + (128 << k) - 1) / (128 << k);
-                const int g = (int)std::max<long long>(1, (tiles + kTilesPerBlock - 1) / kTilesPerBlock);
-                pl.L.gx[k][j] = g;
-                gmax[k] = std::max(gmax[k], g);
-            }
-            const long long t3 = (long long)((h->dp.nx + 31) / 32) * ((h->dp.ny + 3) / 4) * ((h->dp.nz + 3) / 4);
-            pl.L.gt[j] = (int)std::max<long long>(1, (t3 + 1) / 2);   // two tiles per block
-            tmax = std::max(tmax, pl.L.gt[j]);
+            for (int k = 0; k < kNumBatchCfgs; ++k) zmax[k] = std::max(zmax[k], zm_blocks(h->dp, kZChunks[k]));
             lmax = std::max(lmax, h->dp.np * h->dp.nb1);
             cmax = std::max(cmax, h->dp.np * h->dp.nb2);
+            pmax = std::max(pmax, h->dp.np * pt_part_blocks(h->dp));
         }
-        for (int k = 0; k < kNodeTileSizes; ++k) pl.node[k] = dim3(gmax[k], pl.L.nbox);
-        pl.tiles = dim3(tmax, pl.L.nbox);
+        for (int k = 0; k < kNumBatchCfgs; ++k) pl.zgrid[k] = dim3(zmax[k], pl.L.nbox);
         pl.link = dim3(lmax, pl.L.nbox);
         pl.cover = dim3(cmax, pl.L.nbox);
+        pl.ptg = dim3(pmax, pl.L.nbox);
     }
     b->par = 0;
     b->dirty = false;
@@ -339,8 +320,9 @@ int lbb_create(const lbb_params* p, lbb_batch** out)
         e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->side.s, cudaStreamNonBlocking, hi);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.links_done, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.mark_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.bnd_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.collide_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.scal_done, cudaEventDisableTiming);
     }
     size_t cap = p->arena_bytes;
     if (e == cudaSuccess && cap == 0) {
@@ -381,8 +363,9 @@ void lbb_destroy(lbb_batch* b)
         cudaStreamDestroy(b->side.s);
     }
     if (b->side.fork) cudaEventDestroy(b->side.fork);
-    if (b->side.links_done) cudaEventDestroy(b->side.links_done);
-    if (b->side.mark_done) cudaEventDestroy(b->side.mark_done);
+    if (b->side.bnd_done) cudaEventDestroy(b->side.bnd_done);
+    if (b->side.collide_done) cudaEventDestroy(b->side.collide_done);
+    if (b->side.scal_done) cudaEventDestroy(b->side.scal_done);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -491,34 +474,33 @@ int lbb_run(lbb_batch* b, int nsteps, long long* launches)
 
 int lbb_num_configs(void) { return kNumBatchCfgs; }
 
-int lbb_config_shape(int k, int* threads, int* cells, int* regs)
+int lbb_config_shape(int k, int* threads, int* planes)
 {
     if (k < 0 || k >= kNumBatchCfgs) return LB_ERR_PARAM;
-    if (threads) *threads = kBatchCfgs[k].threads;
-    if (cells) *cells = kBatchCfgs[k].cells;
-    if (regs) *regs = kBatchCfgs[k].regs;
+    if (threads) *threads = kZThreads;
+    if (planes) *planes = kZChunks[k];
     return LB_OK;
 }
 
-int lbb_set_config(lbb_batch* b, const int cfg[4])
+int lbb_set_config(lbb_batch* b, const int cfg[LBB_KERNEL_CLASSES])
 {
     if (!b || !cfg) return LB_ERR_PARAM;
-    for (int k = 0; k < 4; ++k)
-        if (!cfg_valid(k, cfg[k])) return LB_ERR_PARAM;
+    for (int k = 0; k < kNumBatchClasses; ++k)
+        if (!cfg_valid(cfg[k])) return LB_ERR_PARAM;
     cudaSetDevice(b->device);
-    for (int k = 0; k < 4; ++k) b->cfg[k] = cfg[k];
+    for (int k = 0; k < kNumBatchClasses; ++k) b->cfg[k] = cfg[k];
     drop_graph(b);
     return LB_OK;
 }
 
-int lbb_tune(lbb_batch* b, int reps, int cfg_out[4], double ms_out[4])
+int lbb_tune(lbb_batch* b, int reps, int cfg_out[LBB_KERNEL_CLASSES], double ms_out[LBB_KERNEL_CLASSES])
 {
     if (!b || reps < 1) return LB_ERR_PARAM;
     if (b->mem.empty()) return LB_ERR_STATE;
     cudaSetDevice(b->device);
     cudaStream_t s = b->stream;
     if (plans_stale(b)) rebuild(b);
-    // collide-stream rewrites the stored velocity: keep a copy in staging
+    // the fused kernel rewrites the stored velocity: keep a copy in staging
     for (const Member& m : b->mem) {
         const size_t ub = 3 * (size_t)m.h->dp.N * m.h->ops->fld_bytes;
         LB_TRY(cudaMemcpyAsync(m.h->staging, m.h->u, ub, cudaMemcpyDeviceToDevice, s));
@@ -527,12 +509,11 @@ int lbb_tune(lbb_batch* b, int reps, int cfg_out[4], double ms_out[4])
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (st == LB_OK) st = cuda_status(cudaEventCreate(&e0));
     if (st == LB_OK) st = cuda_status(cudaEventCreate(&e1));
-    int best[4] = {0, 0, 0, 0};
-    double best_ms[4] = {0, 0, 0, 0};
-    for (int nc = 0; nc < 4 && st == LB_OK; ++nc) {
+    int best[kNumBatchClasses] = {0, 0};
+    double best_ms[kNumBatchClasses] = {0, 0};
+    for (int nc = 0; nc < kNumBatchClasses && st == LB_OK; ++nc) {
         best_ms[nc] = 1e300;
         for (int k = 0; k < kNumBatchCfgs && st == LB_OK; ++k) {
-            if (!cfg_valid(nc, k)) continue;
             auto all = [&]() {
                 for (LaunchPlan& pl : b->plans) {
                     pl.L.par = b->par;
@@ -564,7 +545,7 @@ int lbb_tune(lbb_batch* b, int reps, int cfg_out[4], double ms_out[4])
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (st != LB_OK) return st;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < kNumBatchClasses; ++k) {
         b->cfg[k] = best[k];
         if (cfg_out) cfg_out[k] = best[k];
         if (ms_out) ms_out[k] = best_ms[k];

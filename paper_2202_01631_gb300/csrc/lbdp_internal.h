@@ -60,16 +60,12 @@ struct PrecOps {
 };
 
 // One batched step over the boxes of a batch (see lbdp_batch_kernels.cuh):
-// node kernels in launch configuration cfg[class], particle kernels with the
-// single-box split, then the step count of every box that ran.
+// the bulk kernels with the z chunk length each one's configuration names,
+// the particle kernels with the single-box split, then the step count of
+// every box that ran.
 struct BoxLaunch;
-constexpr int kNumBatchCfgs = 5;   // node kernel configurations (4: shared-memory tiles,
-                                   // force and transport only)
-struct BatchCfg {
-    int threads, cells, tile_index;   // tile = threads * cells = 128 << tile_index nodes (-1: 32x4x4)
-    int regs;                         // register budget: 0 tight, 1 loose
-};
-extern const BatchCfg kBatchCfgs[kNumBatchCfgs];
+constexpr int kNumBatchClasses = 2;   // bulk kernels the autotuner times: fused, transport
+constexpr int kNumBatchCfgs = 3;      // z chunks of 8, 16 or 32 planes per block
 
 // A launch of up to kLaunchBoxes boxes: its parameter block and its grids.
 struct LaunchPlan;
@@ -77,11 +73,12 @@ struct LaunchPlan;
 struct BatchOps {
     // per-device kernel attributes (call once before the first launch or capture)
     cudaError_t (*prepare)();
-    // node kernel of class nc in configuration cfg over one launch's boxes
+    // bulk kernel of class nc (0 fused, 1 transport) in configuration cfg over
+    // one launch's boxes
     cudaError_t (*node)(int nc, int cfg, const LaunchPlan* L, cudaStream_t s);
     // the whole step at parity par over launches L[0..nl-1], then the count-down
     // of left[0..nbox-1]
-    cudaError_t (*step)(const int cfg[4], LaunchPlan* L, int nl, int par, long long* left, int nbox,
+    cudaError_t (*step)(const int cfg[kNumBatchClasses], LaunchPlan* L, int nl, int par, long long* left, int nbox,
                         cudaStream_t s, const SideStream* side);
 };
 

@@ -503,9 +503,9 @@ __device__ __forceinline__ bool box_node(const DevParams& P, const int o[3], con
 // accessor: mask(i) is the mask of neighbour x + c_i (kWallSlot beyond a
 // wall) and get<k>(i) the value of field k there (own(k) = get<k>(0)).  Where
 // mask(i) is not 0 the bodies do not use get<k>(i) except multiplied by 0.
-// GAcc reads global memory through the D3Q19 neighbour indices; TAcc reads a
-// tile staged in shared memory.  Both hand the same values to the same
-// arithmetic.
+// GAcc reads global memory through the D3Q19 neighbour indices; the
+// accessors of lbdp_zmarch.cuh read planes staged in shared memory.  All hand
+// the same values to the same arithmetic.
 // ---------------------------------------------------------------------------
 template <class F, int NF>
 struct GAcc {
@@ -529,111 +529,6 @@ __device__ __forceinline__ bool near_wall(const DevParams& P, int x, int y, int 
            (!P.per[2] && (z == 0 || z == P.nz - 1));
 }
 
-// Global-memory view of a node none of whose neighbours is solid or beyond a
-// wall (boundary flag clear, not at a wall): the neighbour x + c_i is
-// xi[1 + c_x] + yo[1 + c_y] + zo[1 + c_z] (periodic wrap included), and
-// mask(i) is the constant 0.
-template <class F, int NF>
-struct GAccClear {
-    int xi[3], yo[3], zo[3];
-    const F* f[NF];
-    __device__ __forceinline__ int at(int i) const { return xi[1 + cx(i)] + yo[1 + cy(i)] + zo[1 + cz(i)]; }
-    __device__ __forceinline__ uint8_t mask(int) const { return 0; }
-    template <int K>
-    __device__ __forceinline__ F get(int i) const
-    {
-        return f[K][at(i)];
-    }
-    __device__ __forceinline__ void init(const DevParams& P, int x, int y, int z)
-    {
-        const int nx = P.nx, ny = P.ny, sxy = nx * ny;
-        xi[0] = x > 0 ? x - 1 : nx - 1;
-        xi[1] = x;
-        xi[2] = x < nx - 1 ? x + 1 : 0;
-        yo[0] = (y > 0 ? y - 1 : ny - 1) * nx;
-        yo[1] = y * nx;
-        yo[2] = (y < ny - 1 ? y + 1 : 0) * nx;
-        zo[0] = (z > 0 ? z - 1 : P.nz - 1) * sxy;
-        zo[1] = z * sxy;
-        zo[2] = (z < P.nz - 1 ? z + 1 : 0) * sxy;
-    }
-};
-
-// Tile of TX x TY x TZ nodes with a one-node halo, fields [NF][slots] and
-// the mask [slots] in shared memory; slot of tile node (tx, ty, tz) is
-// (tx + 1) + HX ((ty + 1) + HY (tz + 1)).
-template <int TX, int TY, int TZ>
-struct TileShape {
-    static constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
-    static constexpr int slots = HX * HY * HZ;
-    static __host__ __device__ constexpr int off(int i) { return cx(i) + HX * (cy(i) + HY * cz(i)); }
-};
-
-// Shared-memory place of field k of slot s: fields 2j and 2j+1 interleave
-// ([j][slot][2]), so a body that reads both gets them in one 64-bit load; an
-// odd last field stands alone.
-template <class T>
-__host__ __device__ constexpr int tile_index(int k, int s)
-{
-    return (k & ~1) * T::slots + 2 * s + (k & 1);
-}
-template <int NF, class T>
-__host__ __device__ constexpr int tile_index_last(int k, int s)
-{
-    return ((NF & 1) && k == NF - 1) ? (NF - 1) * T::slots + s : tile_index<T>(k, s);
-}
-
-template <class F, int NF, class T>
-struct TAcc {
-    const F* sf;          // NF fields x T::slots, paired (tile_index_last)
-    const uint8_t* sm;    // [T::slots]
-    int slot;
-    __device__ __forceinline__ uint8_t mask(int i) const { return sm[slot + T::off(i)]; }
-    template <int K>
-    __device__ __forceinline__ F get(int i) const
-    {
-        return sf[tile_index_last<NF, T>(K, slot + T::off(i))];
-    }
-};
-
-// The same view of a tile none of whose slots (halo included) is solid or
-// beyond a wall: mask(i) is the constant 0, so a body instantiated with it
-// loses its mask loads and boundary branches at compile time.
-template <class F, int NF, class T>
-struct TAccClear : TAcc<F, NF, T> {
-    __device__ __forceinline__ uint8_t mask(int) const { return 0; }
-};
-
-// Stage fields src[0..NF-1] and the mask of the tile at (x0, y0, z0) plus
-// its halo; slots beyond a wall get kWallSlot and zeros.  Returns whether
-// this thread staged any slot that is not fluid.
-template <class F, int NF, class T>
-__device__ __forceinline__ bool stage_tile(const DevParams& P, const uint8_t* mask, const F* const (&src)[NF],
-                                           int x0, int y0, int z0, F* sf, uint8_t* sm)
-{
-    bool any = false;
-    for (int s = threadIdx.x; s < T::slots; s += blockDim.x) {
-        const int lx = s % T::HX, ly = (s / T::HX) % T::HY, lz = s / (T::HX * T::HY);
-        const int gx = wrap_coord(x0 + lx - 1, P.nx, P.per[0]);
-        const int gy = wrap_coord(y0 + ly - 1, P.ny, P.per[1]);
-        const int gz = wrap_coord(z0 + lz - 1, P.nz, P.per[2]);
-        if (gx >= 0 && gy >= 0 && gz >= 0) {
-            const int g = gx + P.nx * (gy + P.ny * gz);
-            const uint8_t m = mask[g];
-            sm[s] = m;
-            any = any || m != 0;
-#pragma unroll
-            for (int k = 0; k < NF; ++k) sf[tile_index_last<NF, T>(k, s)] = src[k][g];
-        } else {
-            sm[s] = kWallSlot;
-            any = true;
-#pragma unroll
-            for (int k = 0; k < NF; ++k) sf[tile_index_last<NF, T>(k, s)] = (F)0;
-        }
-    }
-    return any;
-}
-
 // ---------------------------------------------------------------------------
 // S1: chemical potentials and pressure tensor, one thread per node.  Every
 // neighbour load is issued before any decision (walls clamp to the node
@@ -641,7 +536,7 @@ __device__ __forceinline__ bool stage_tile(const DevParams& P, const uint8_t* ma
 // ---------------------------------------------------------------------------
 // Fields of the chemical-potential body: 0 psi, 1 phi.  mup_values returns
 // mu_psi, mu_phi and (when P.thermo) the pressure tensor of fluid node
-// (x, y, z); mup_compute stores them.
+// (x, y, z).
 // dps, dph: the uniform psi/phi correction still to be added (corr_r); a
 // kernel that loops over many nodes reads them once.
 template <class C, class A>
@@ -669,48 +564,6 @@ __device__ __forceinline__ void mup_values(const DevParams& P, const DevPtrs& D,
             d[i] = psi_ghost_diff<R>(P, D.parts[mk[i] - 1], x, y, z, i);
     }
     mu_pressure<R>(Q, p0 + dps, d, (R)a.template get<1>(0) + dph, P.thermo != 0, mps, mph, pt);
-}
-
-template <class C, class A>
-__device__ __forceinline__ void mup_compute(const DevParams& P, const DevPtrs& D, int x, int y, int z, int n,
-                                            const A& a)
-{
-    using R = typename C::real;
-    using F = typename C::fld_t;
-    const size_t N = (size_t)P.N;
-    R mps, mph, pt[kPtFields];
-    mup_values<C>(P, D, x, y, z, a, corr_r<R>(D, 0), corr_r<R>(D, 1), mps, mph, pt);
-    ((F*)D.mupsi)[n] = (F)mps;
-    ((F*)D.muphi)[n] = (F)mph;
-    if (P.thermo) {
-        F* ptg = (F*)D.pt;
-#pragma unroll
-        for (int k = 0; k < kPtFields; ++k) ptg[k * N + n] = (F)pt[k];
-    }
-}
-
-template <class C>
-__device__ __forceinline__ void mup_node(const DevParams& P, const DevPtrs& D, int x, int y, int z)
-{
-    using F = typename C::fld_t;
-    const int n = x + P.nx * (y + P.ny * z);
-    const uint8_t mk = D.mask[n], bf = D.bflag[n];
-    if (mk) return;
-    if (!bf && !near_wall(P, x, y, z)) {
-        GAccClear<F, 2> c;
-        c.init(P, x, y, z);
-        c.f[0] = (const F*)D.psi_src;
-        c.f[1] = (const F*)D.phi_src;
-        mup_compute<C>(P, D, x, y, z, n, c);
-        return;
-    }
-    GAcc<F, 2> a;
-    neighbours(P, x, y, z, a.nb);
-    a.n = n;
-    a.mk = D.mask;
-    a.f[0] = (const F*)D.psi_src;
-    a.f[1] = (const F*)D.phi_src;
-    mup_compute<C>(P, D, x, y, z, n, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -984,6 +837,7 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    const R zc0 = (R)6 * Q.rho0;
     for (int t = bi * blockDim.x + threadIdx.x; t < tot; t += nbi * blockDim.x) {
         int x, y, z;
         if (!box_node(P, o, P.side1, t, x, y, z)) continue;
@@ -1001,11 +855,9 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
         }
         if (!have) continue;
         // this node has links into particle p: load everything it needs at once
-        // (populations as deviations g = f - w rho0: the rest part is added
-        // in FP64 below, so that FP32 never rounds f ~ w to the small g)
-        R gv[19];
+        R fv[19];
 #pragma unroll
-        for (int i = 1; i < 19; ++i) gv[i] = (R)PopStore<S>::load_dev(fs, (size_t)i * N + n, i, Q.rho0);
+        for (int i = 1; i < 19; ++i) fv[i] = (R)PopStore<S>::load(fs, (size_t)i * N + n, i, Q.rho0);
         const R ps = (R)psi[n] + dps, ph = (R)phi[n] + dph;
         R gphi[3];
         grad_phi_at<R, F>(nb, phi, D.mask, ph, dph, gphi);
@@ -1016,67 +868,57 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
 #pragma unroll
             for (int k = 0; k < kPtFields; ++k) pt[k] = (R)ptg[k * N + n];
         }
-        // momentum exchange, torque and drag matrix of each link in FP64 (their
-        // sums over a sphere cancel to a small net force, so FP32 terms would
-        // leave a rounding residue that the particle integrates step after
-        // step); the scalar-flux coefficients in the arithmetic precision
-        R nacc[kLinkK - kLinkGpsi];   // this node's flux coefficients, added to the FP64 sums once
+        R nacc[K];   // this node's links, added to the FP64 sums once
 #pragma unroll
-        for (int k = 0; k < kLinkK - kLinkGpsi; ++k) nacc[k] = (R)0;
-        int Di[3];
-        int_offset(P, q.g, x, y, z, Di);
+        for (int k = 0; k < K; ++k) nacc[k] = (R)0;
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
             if (!lk[i]) continue;
             R r[3], ub[3], vs[3];
             link_velocity<R>(P, q, x, y, z, i, gphi, r, ub, vs);
-            double rd[3];
-            link_offset_r<double>(q.g, Di, i, rd);
-            const double w6 = 6.0 * wgt(i);
-            const double c[3] = {(double)cx(i), (double)cy(i), (double)cz(i)};
+            const R fi = fv[i];
+            const R w6 = (R)6 * wgt_r<R>(i);
+            const R c[3] = {(R)cx(i), (R)cy(i), (R)cz(i)};
             const R cvs = cdot<R>(i, vs[0], vs[1], vs[2]);
-            // c [2 f_i - 6 w rho0 c.v_s] with f_i = g_i + w rho0
-            const double mag = fma_x(-(w6 * P.rho0), (double)cvs, fma_x(2.0, (double)gv[i], 2.0 * wgt(i) * P.rho0));
-            double dP[3] = {c[0] * mag, c[1] * mag, c[2] * mag};
+            const R mag = fma_x(-mul_x(w6, Q.rho0), cvs, mul_x((R)2, fi));
+            R dP[3] = {mul_x(c[0], mag), mul_x(c[1], mag), mul_x(c[2], mag)};
             if (P.thermo) {
                 // chemical stress flux through the link, 6 w_i P(x) . c_i
                 R pc[3];
                 pt_dot_c<R>(i, Q.kappa, pt, pc);
-                dP[0] = fma_x(w6, (double)pc[0], dP[0]);
-                dP[1] = fma_x(w6, (double)pc[1], dP[1]);
-                dP[2] = fma_x(w6, (double)pc[2], dP[2]);
+                dP[0] = fma_x(w6, pc[0], dP[0]);
+                dP[1] = fma_x(w6, pc[1], dP[1]);
+                dP[2] = fma_x(w6, pc[2], dP[2]);
             }
-            acc[0] = add_x(acc[0], dP[0]);
-            acc[1] = add_x(acc[1], dP[1]);
-            acc[2] = add_x(acc[2], dP[2]);
-            acc[3] = add_x(acc[3], cross_x(rd[1], dP[2], rd[2], dP[1]));
-            acc[4] = add_x(acc[4], cross_x(rd[2], dP[0], rd[0], dP[2]));
-            acc[5] = add_x(acc[5], cross_x(rd[0], dP[1], rd[1], dP[0]));
-            const double g6[6] = {c[0], c[1], c[2], cross_x(rd[1], c[2], rd[2], c[1]),
-                                  cross_x(rd[2], c[0], rd[0], c[2]), cross_x(rd[0], c[1], rd[1], c[0])};
-            const double zc = w6 * P.rho0;
+            nacc[0] = add_x(nacc[0], dP[0]);
+            nacc[1] = add_x(nacc[1], dP[1]);
+            nacc[2] = add_x(nacc[2], dP[2]);
+            nacc[3] = add_x(nacc[3], cross_x(r[1], dP[2], r[2], dP[1]));
+            nacc[4] = add_x(nacc[4], cross_x(r[2], dP[0], r[0], dP[2]));
+            nacc[5] = add_x(nacc[5], cross_x(r[0], dP[1], r[1], dP[0]));
+            const R g6[6] = {c[0], c[1], c[2], cross_x(r[1], c[2], r[2], c[1]), cross_x(r[2], c[0], r[0], c[2]),
+                             cross_x(r[0], c[1], r[1], c[0])};
+            const R zc = mul_x(zc0, wgt_r<R>(i));
             int k = 6;
 #pragma unroll
             for (int a = 0; a < 6; ++a)
 #pragma unroll
-                for (int b = a; b < 6; ++b, ++k) acc[k] = fma_x(zc * g6[a], g6[b], acc[k]);
+                for (int b = a; b < 6; ++b, ++k) nacc[k] = fma_x(mul_x(zc, g6[a]), g6[b], nacc[k]);
             // scalar flux into the surface, 6 w g(x) c.u_b (finite
             // differences) or g(x) c.u_b on the six D3Q7 links (lattice
             // Boltzmann), with c.u_b = (c, r x c) . V(t+1) + c.v_s
-            const R g6r[6] = {(R)cx(i), (R)cy(i), (R)cz(i), cross_x(r[1], (R)cz(i), r[2], (R)cy(i)),
-                              cross_x(r[2], (R)cx(i), r[0], (R)cz(i)), cross_x(r[0], (R)cy(i), r[1], (R)cx(i))};
-            const R ws = P.scheme ? (i < 7 ? (R)1 : (R)0) : (R)6 * wgt_r<R>(i);
+            const R ws = P.scheme ? (i < 7 ? (R)1 : (R)0) : w6;
             const R wps = mul_x(ws, ps), wph = mul_x(ws, ph);
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
-                nacc[a] = fma_x(wps, g6r[a], nacc[a]);
-                nacc[7 + a] = fma_x(wph, g6r[a], nacc[7 + a]);
+                nacc[kLinkGpsi + a] = fma_x(wps, g6[a], nacc[kLinkGpsi + a]);
+                nacc[kLinkGphi + a] = fma_x(wph, g6[a], nacc[kLinkGphi + a]);
             }
-            nacc[6] = fma_x(wps, cvs, nacc[6]);
-            nacc[13] = fma_x(wph, cvs, nacc[13]);
+            nacc[kLinkGpsi + 6] = fma_x(wps, cvs, nacc[kLinkGpsi + 6]);
+            nacc[kLinkGphi + 6] = fma_x(wph, cvs, nacc[kLinkGphi + 6]);
         }
 #pragma unroll
-        for (int k = 0; k < kLinkK - kLinkGpsi; ++k) acc[kLinkGpsi + k] += (double)nacc[k];
+        for (int k = 0; k < K; ++k) acc[k] += (double)nacc[k];
     }
     block_sum_rows<K>(acc, smem);
     double* part = D.link_part + ((size_t)p * kMaxPartBlocks + bi) * K;
@@ -1182,61 +1024,11 @@ __device__ __forceinline__ void collide_store(const PrmR<typename C::real>& Q, c
 
 // Collide-stream of a fluid node next to a particle (and possibly a wall):
 // halfway bounce-back on wall links, moving bounce-back with
-// u_b = U + Omega x r + v_s on particle links.  Every mask and population
-// load is issued before the first is used.
-template <class C>
-__device__ __forceinline__ void collide_boundary_body(const DevParams& P, const DevPtrs& D, int x, int y, int z)
-{
-    using R = typename C::real;
-    using F = typename C::fld_t;
-    using S = typename C::pop_t;
-    const int n = x + P.nx * (y + P.ny * z);
-    const PrmR<R>& Q = prm<R>(P);
-    const size_t N = (size_t)P.N;
-    const int NN = (int)N;
-    const S* fs = (const S*)D.f_src;
-    const F* force = (const F*)D.force;
-    const R rho0 = Q.rho0;
-    int nb[19];
-    neighbours(P, x, y, z, nb);
-    uint8_t q[19];
-#pragma unroll
-    for (int i = 1; i < 19; ++i) q[i] = nb[i] >= 0 ? D.mask[nb[i]] : (uint8_t)0;
-    const R Fx = (R)force[n], Fy = (R)force[NN + n], Fz = (R)force[2 * NN + n];
-    // population j arrives from x - c_j = x + c_i (i = opp(j)); from a wall
-    // or a particle it is the node's own population i, reflected
-    R fl[19];
-#pragma unroll
-    for (int j = 0; j < 19; ++j) {
-        const int i = opp(j);
-        const bool own = j != 0 && (nb[i] < 0 || q[i] != 0);
-        fl[j] = (R)PopStore<S>::load_dev(fs, own ? i * NN + n : j * NN + (j == 0 ? n : nb[i]), own ? i : j, rho0);
-    }
-    const F* phi = (const F*)D.phi_src;
-    const R dph = corr_r<R>(D, 1);
-    bool have_g = false;
-    R gphi[3] = {0, 0, 0};
-    for (int j = 1; j < 19; ++j) {
-        const int i = opp(j);
-        if (nb[i] < 0 || q[i] == 0) continue;
-        if (!have_g) {
-            grad_phi_at<R, F>(nb, phi, D.mask, (R)phi[n] + dph, dph, gphi);
-            have_g = true;
-        }
-        R r[3], ub[3], vs[3];
-        link_velocity<R>(P, D.parts[q[i] - 1], x, y, z, i, gphi, r, ub, vs);
-        const R cub = cdot<R>(i, ub[0], ub[1], ub[2]);
-        fl[j] = fma_x(-((R)6 * wgt_r<R>(i) * rho0), cub, fl[j]);
-    }
-    collide_store<C>(Q, D, N, n, fl, Fx, Fy, Fz);
-}
-
-// The same node with every load of the node issued before any is used (masks,
-// both candidate sources of each population, phi around the node, the
-// force; then the record of the node's lowest adjacent particle), for
-// k_collide_particles, which has the registers for it.  nb and q (the masks
-// of the neighbours) come from the caller.  Same arithmetic, same bits as
-// collide_boundary_body.
+// u_b = U + Omega x r + v_s on particle links.  Every load of the node is
+// issued before any is used (masks, both candidate sources of each
+// population, phi around the node, the force; then the record of the node's
+// lowest adjacent particle).  nb and q (the masks of the neighbours) come
+// from the caller.
 template <class C>
 __device__ __forceinline__ void collide_boundary_wide(const DevParams& P, const DevPtrs& D, int x, int y, int z,
                                                       const int (&nb)[19], const uint8_t (&q)[19], int lo)
@@ -1303,14 +1095,6 @@ __device__ __forceinline__ void collide_boundary_wide(const DevParams& P, const 
     collide_store<C>(Q, D, N, n, fl, Fx, Fy, Fz);
 }
 
-// The same, out of line, for kernels that meet these few nodes among all
-// others (keeps their code out of the common path).
-template <class C>
-static __device__ __noinline__ void collide_boundary(const DevParams& P, const DevPtrs& D, int x, int y, int z)
-{
-    collide_boundary_body<C>(P, D, x, y, z);
-}
-
 // Pull sources of every population of node (x, y, z) loaded as deviations
 // into fl (wrapped on periodic axes, clamped to the node itself beyond a wall,
 // where bulk_wall_links replaces them): one memory round trip.
@@ -1356,58 +1140,6 @@ __device__ __forceinline__ void bulk_wall_links(const DevParams& P, const DevPtr
     for (int j = 1; j < 19; ++j)
         if (wx[1 - cx(j)] || wy[1 - cy(j)] || wz[1 - cz(j)])
             fl[j] = (R)PopStore<S>::load_dev(fs, opp(j) * NN + n, opp(j), prm<R>(P).rho0);
-}
-
-// kBoundary: nodes next to a particle are collided here (out of line);
-// otherwise they are left to k_collide_particles.
-template <class C, bool kBoundary = true>
-__device__ __forceinline__ void collide_node(const DevParams& P, const DevPtrs& D, int x, int y, int z)
-{
-    using R = typename C::real;
-    using F = typename C::fld_t;
-    using S = typename C::pop_t;
-    const int nx = P.nx, ny = P.ny, sxy = nx * ny;
-    const int n = x + nx * (y + ny * z);
-    const PrmR<R>& Q = prm<R>(P);
-    const size_t N = (size_t)P.N;
-    const int NN = (int)N;
-    const S* fs = (const S*)D.f_src;
-    const F* force = (const F*)D.force;
-    // source x - c_j of population j as xi[1 - c_jx] + yo[1 - c_jy] + zo[1 - c_jz]:
-    // wrapped on periodic axes, clamped beyond a wall (those links are
-    // replaced below)
-    const int xi[3] = {x > 0 ? x - 1 : (P.per[0] ? nx - 1 : 0), x, x < nx - 1 ? x + 1 : (P.per[0] ? 0 : x)};
-    const int yo[3] = {(y > 0 ? y - 1 : (P.per[1] ? ny - 1 : 0)) * nx, y * nx,
-                       (y < ny - 1 ? y + 1 : (P.per[1] ? 0 : y)) * nx};
-    const int zo[3] = {(z > 0 ? z - 1 : (P.per[2] ? P.nz - 1 : 0)) * sxy, z * sxy,
-                       (z < P.nz - 1 ? z + 1 : (P.per[2] ? 0 : z)) * sxy};
-    // issue every load of the common case at once (one memory round trip);
-    // solid and particle-boundary nodes drop them (a few per mille)
-    const uint8_t mk = D.mask[n], bf = D.bflag[n];
-    const R Fx = (R)force[n], Fy = (R)force[NN + n], Fz = (R)force[2 * NN + n];
-    R fl[19];
-#pragma unroll
-    for (int j = 0; j < 19; ++j) {
-        const int m = xi[1 - cx(j)] + yo[1 - cy(j)] + zo[1 - cz(j)];
-        fl[j] = (R)PopStore<S>::load_dev(fs, j * NN + m, j, Q.rho0);
-    }
-    if (mk) return;
-    if (bf) {
-        if (kBoundary) collide_boundary<C>(P, D, x, y, z);
-        return;
-    }
-    if (near_wall(P, x, y, z)) {
-        // halfway bounce-back: a link whose source lies beyond a wall brings
-        // back the node's own population of the opposite direction
-        const bool wx[3] = {!P.per[0] && x == 0, false, !P.per[0] && x == nx - 1};
-        const bool wy[3] = {!P.per[1] && y == 0, false, !P.per[1] && y == ny - 1};
-        const bool wz[3] = {!P.per[2] && z == 0, false, !P.per[2] && z == P.nz - 1};
-#pragma unroll
-        for (int j = 1; j < 19; ++j)
-            if (wx[1 - cx(j)] || wy[1 - cy(j)] || wz[1 - cz(j)])
-                fl[j] = (R)PopStore<S>::load_dev(fs, opp(j) * NN + n, opp(j), Q.rho0);
-    }
-    collide_store<C>(Q, D, N, n, fl, Fx, Fy, Fz);
 }
 
 // ---------------------------------------------------------------------------
@@ -1864,33 +1596,6 @@ __device__ __forceinline__ void cover_apply_block(const DevParams& P, const DevP
 // particle kernels of the single box: grid (blocks per particle, particles)
 // (the bulk kernels of the single box are in lbdp_zmarch.cuh)
 // ---------------------------------------------------------------------------
-// Shared-memory tiles of the batched force and transport kernels: a
-// 256-thread block stages the inputs of a 32 x 4 x 4 tile and its halo once,
-// then each thread computes two nodes, reading all neighbours at fixed
-// shared-memory offsets.
-using Tile = TileShape<32, 4, 4>;
-constexpr int kTileThreads = 256;
-
-template <class F, int NF>
-__host__ __device__ constexpr size_t tile_smem() { return (size_t)NF * Tile::slots * sizeof(F) + Tile::slots; }
-
-// The two nodes of this thread in the tile at (x0, y0, z0): (tx, ty, tz0)
-// and (tx, ty, tz0 + 2).
-template <class Body>
-__device__ __forceinline__ void tile_nodes(const DevParams& P, const uint8_t* sm, int x0, int y0, int z0, Body body)
-{
-    const int tx = threadIdx.x & 31, ty = (threadIdx.x >> 5) & 3, tz0 = threadIdx.x >> 7;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int tz = tz0 + 2 * h;
-        const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
-        if (x >= P.nx || y >= P.ny || z >= P.nz) continue;
-        const int slot = (tx + 1) + Tile::HX * ((ty + 1) + Tile::HY * (tz + 1));
-        if (sm[slot]) continue;   // node inside a particle
-        body(x, y, z, x + P.nx * (y + P.ny * z), slot);
-    }
-}
-
 // Collide-stream of the fluid nodes next to particles, beside the bulk kernel
 // (which leaves them out).  These nodes read the particle records and their
 // neighbours' masks in chains of dependent loads; inside the bulk kernel,
@@ -1898,14 +1603,12 @@ __device__ __forceinline__ void tile_nodes(const DevParams& P, const uint8_t* sm
 // its block long after the others finish.  Block (b, p) walks the link box of particle
 // p; a node next to several particles is collided by the lowest of them.
 template <class C>
-__global__ void __launch_bounds__(kPartThreads) k_collide_particles(const __grid_constant__ DevParams P,
-                                                                     const __grid_constant__ DevPtrs D)
+__device__ __forceinline__ void collide_particles_block(const DevParams& P, const DevPtrs& D, int p, int bi, int nbi)
 {
-    const int p = blockIdx.y;
     const DevPart& q = D.parts[p];
     const int o[3] = {q.g.Xi[0] - q.Rc - 2, q.g.Xi[1] - q.Rc - 2, q.g.Xi[2] - q.Rc - 2};
     const int tot = P.side1[0] * P.side1[1] * P.side1[2];
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+    for (int t = bi * blockDim.x + threadIdx.x; t < tot; t += nbi * blockDim.x) {
         int x, y, z;
         if (!box_node(P, o, P.side1, t, x, y, z)) continue;
         const int n = x + P.nx * (y + P.ny * z);
@@ -1925,18 +1628,23 @@ __global__ void __launch_bounds__(kPartThreads) k_collide_particles(const __grid
     }
 }
 
+template <class C>
+__global__ void __launch_bounds__(kPartThreads) k_collide_particles(const __grid_constant__ DevParams P,
+                                                                     const __grid_constant__ DevPtrs D)
+{
+    collide_particles_block<C>(P, D, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
 // Transport of the fluid nodes next to particles, beside kz_scalars (which
 // leaves them out), for the same reason and with the same split as
 // k_collide_particles.
 template <class C>
-__global__ void __launch_bounds__(kPartThreads) k_scalars_particles(const __grid_constant__ DevParams P,
-                                                                     const __grid_constant__ DevPtrs D)
+__device__ __forceinline__ void scalars_particles_block(const DevParams& P, const DevPtrs& D, int p, int bi, int nbi)
 {
-    const int p = blockIdx.y;
     const DevPart& q = D.parts[p];
     const int o[3] = {q.g.Xi[0] - q.Rc - 2, q.g.Xi[1] - q.Rc - 2, q.g.Xi[2] - q.Rc - 2};
     const int tot = P.side1[0] * P.side1[1] * P.side1[2];
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+    for (int t = bi * blockDim.x + threadIdx.x; t < tot; t += nbi * blockDim.x) {
         int x, y, z;
         if (!box_node(P, o, P.side1, t, x, y, z)) continue;
         const int n = x + P.nx * (y + P.ny * z);
@@ -1952,6 +1660,13 @@ __global__ void __launch_bounds__(kPartThreads) k_scalars_particles(const __grid
         if (lo != p + 1) continue;
         scalars_node<C>(P, D, x, y, z);
     }
+}
+
+template <class C>
+__global__ void __launch_bounds__(kPartThreads) k_scalars_particles(const __grid_constant__ DevParams P,
+                                                                     const __grid_constant__ DevPtrs D)
+{
+    scalars_particles_block<C>(P, D, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 template <class C>

@@ -59,25 +59,7 @@ struct Ops {
         return e;
     }
 
-    // Blocks per particle of a box of the given edges (about one node per
-    // thread, at most kMaxPartBlocks).
-    static int part_blocks(long long nodes)
-    {
-        const long long b = (nodes + kPartThreads - 1) / kPartThreads;
-        return (int)(b < 1 ? 1 : (b > kMaxPartBlocks ? kMaxPartBlocks : b));
-    }
-
-    static dim3 pt_grid(const DevParams& P)
-    {
-        long long t = 1;
-        const int L[3] = {P.nx, P.ny, P.nz};
-        for (int a = 0; a < 3; ++a) {
-            int s = P.side1[a] + 2;
-            if (P.per[a] && s > L[a]) s = L[a];
-            t *= s;
-        }
-        return dim3(part_blocks(t), P.np);
-    }
+    static dim3 pt_grid(const DevParams& P) { return dim3(pt_part_blocks(P), P.np); }
 
     // One time step.  With particles and a side stream: the particle kernels
     // (pressure tensor and force next to the particles, link sums and the
@@ -205,29 +187,27 @@ struct Ops {
 // Launchers of the batched kernels of one precision configuration.
 template <class C>
 struct BOps {
+    using F = typename C::fld_t;
     using KFn = void (*)(BoxLaunch);
-
-    template <int NC>
-    static KFn node_fn(int cfg)
-    {
-        static_assert(kNumBatchCfgs == 5, "configuration table");
-        switch (cfg) {
-            case 0: return kb_node<C, NC, 128, 1, 0, 0>;
-            case 1: return kb_node<C, NC, 128, 1, 0, 1>;
-            case 2: return kb_node<C, NC, 256, 1, 1, 1>;
-            default: return kb_node<C, NC, 128, 2, 1, 1>;
-        }
-    }
 
     static KFn fn(int nc, int cfg)
     {
-        switch (nc) {
-            case kNcMup: return node_fn<kNcMup>(cfg);
-            case kNcFdiv: return node_fn<kNcFdiv>(cfg);
-            case kNcCollide: return node_fn<kNcCollide>(cfg);
-            default: return node_fn<kNcScalars>(cfg);
+        static_assert(kNumBatchCfgs == 3, "configuration table");
+        if (nc == 0) {
+            switch (cfg) {
+                case 0: return kbz_fused<C, kZChunks[0]>;
+                case 1: return kbz_fused<C, kZChunks[1]>;
+                default: return kbz_fused<C, kZChunks[2]>;
+            }
+        }
+        switch (cfg) {
+            case 0: return kbz_scalars<C, kZChunks[0]>;
+            case 1: return kbz_scalars<C, kZChunks[1]>;
+            default: return kbz_scalars<C, kZChunks[2]>;
         }
     }
+
+    static size_t smem(int nc) { return nc == 0 ? sizeof(FusedSmem<F>) : sizeof(ScalSmem<F>); }
 
     static cudaError_t prepare()
     {
@@ -238,39 +218,27 @@ struct BOps {
         if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
         e = cudaFuncSetAttribute(kb_links<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)block_rows_bytes<kLinkK>(kPartThreads));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(kb_tiled<C, kNcFdiv>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)tile_smem<typename C::fld_t, kPtFields>());
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(kb_tiled<C, kNcScalars>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)tile_smem<typename C::fld_t, 7>());
-        if (e == cudaSuccess)
-            e = set_carveout((const void*)kb_tiled<C, kNcFdiv>, kFdivBlocks, tile_smem<typename C::fld_t, kPtFields>());
-        if (e == cudaSuccess)
-            e = set_carveout((const void*)kb_tiled<C, kNcScalars>, kScalBlocks, tile_smem<typename C::fld_t, 7>());
+        for (int nc = 0; nc < kNumBatchClasses && e == cudaSuccess; ++nc)
+            for (int k = 0; k < kNumBatchCfgs && e == cudaSuccess; ++k)
+                e = cudaFuncSetAttribute((const void*)fn(nc, k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem(nc));
         if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
         return e;
     }
 
     static cudaError_t node(int nc, int cfg, const LaunchPlan* L, cudaStream_t s)
     {
-        if (nc < 0 || nc >= kNumNodeClasses || cfg < 0 || cfg >= kNumBatchCfgs) return cudaErrorInvalidValue;
+        if (nc < 0 || nc >= kNumBatchClasses || cfg < 0 || cfg >= kNumBatchCfgs) return cudaErrorInvalidValue;
         void* args[] = {(void*)&L->L};
-        if (cfg == 4) {
-            if (nc == kNcFdiv)
-                return cudaLaunchKernel((const void*)kb_tiled<C, kNcFdiv>, L->tiles, dim3(kTileThreads), args,
-                                        tile_smem<typename C::fld_t, kPtFields>(), s);
-            if (nc == kNcScalars)
-                return cudaLaunchKernel((const void*)kb_tiled<C, kNcScalars>, L->tiles, dim3(kTileThreads), args,
-                                        tile_smem<typename C::fld_t, 7>(), s);
-            return cudaErrorInvalidValue;
-        }
-        return cudaLaunchKernel((const void*)fn(nc, cfg), L->node[kBatchCfgs[cfg].tile_index],
-                                dim3(kBatchCfgs[cfg].threads), args, 0, s);
+        return cudaLaunchKernel((const void*)fn(nc, cfg), L->zgrid[cfg], dim3(kZThreads), args, smem(nc), s);
     }
 
-    static cudaError_t step(const int cfg[4], LaunchPlan* Ls, int nl, int par, long long* left, int nbox,
-                            cudaStream_t s, const SideStream* side)
+    // The single-box step over each launch's boxes, in the single-box order:
+    // the particle kernels on the side stream beside the fused bulk kernel,
+    // the bulk transport after the boundary collide-stream, the boundary
+    // transport and covering beside it.
+    static cudaError_t step(const int cfg[kNumBatchClasses], LaunchPlan* Ls, int nl, int par, long long* left,
+                            int nbox, cudaStream_t s, const SideStream* side)
     {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
@@ -278,27 +246,35 @@ struct BOps {
         for (int l = 0; l < nl; ++l) {
             LaunchPlan* L = Ls + l;
             L->L.par = par;   // copied into each launch's parameters at the call
-            if ((e = node(kNcMup, cfg[0], L, s)) != cudaSuccess) return e;
             if (side) {
                 cudaEventRecord(side->fork, s);
                 cudaStreamWaitEvent(side->s, side->fork, 0);
+                kb_pt_part<C><<<L->ptg, kPartThreads, 0, side->s>>>(L->L);
+                kb_f_part<C><<<L->link, kPartThreads, 0, side->s>>>(L->L);
                 kb_links<C><<<L->link, kPartThreads, lsm, side->s>>>(L->L);
-                cudaEventRecord(side->links_done, side->s);
+                kb_collide_particles<C><<<L->link, kPartThreads, 0, side->s>>>(L->L);
+                cudaEventRecord(side->bnd_done, side->s);
                 kb_cover_mark<C><<<L->cover, kPartThreads, 0, side->s>>>(L->L);
-                cudaEventRecord(side->mark_done, side->s);
-                if ((e = node(kNcFdiv, cfg[1], L, s)) != cudaSuccess) return e;
-                cudaStreamWaitEvent(s, side->links_done, 0);
-                if ((e = node(kNcCollide, cfg[2], L, s)) != cudaSuccess) return e;
-                if ((e = node(kNcScalars, cfg[3], L, s)) != cudaSuccess) return e;
-                cudaStreamWaitEvent(s, side->mark_done, 0);
+                if ((e = node(0, cfg[0], L, s)) != cudaSuccess) return e;
+                cudaEventRecord(side->collide_done, s);
+                cudaStreamWaitEvent(side->s, side->collide_done, 0);
+                kb_scalars_particles<C><<<L->link, kPartThreads, 0, side->s>>>(L->L);
+                kb_cover_apply<C><<<L->cover, kPartThreads, 0, side->s>>>(L->L);
+                cudaEventRecord(side->scal_done, side->s);
+                cudaStreamWaitEvent(s, side->bnd_done, 0);
+                if ((e = node(1, cfg[1], L, s)) != cudaSuccess) return e;
+                cudaStreamWaitEvent(s, side->scal_done, 0);
             } else {
-                if ((e = node(kNcFdiv, cfg[1], L, s)) != cudaSuccess) return e;
+                kb_pt_part<C><<<L->ptg, kPartThreads, 0, s>>>(L->L);
+                kb_f_part<C><<<L->link, kPartThreads, 0, s>>>(L->L);
                 kb_links<C><<<L->link, kPartThreads, lsm, s>>>(L->L);
-                if ((e = node(kNcCollide, cfg[2], L, s)) != cudaSuccess) return e;
-                if ((e = node(kNcScalars, cfg[3], L, s)) != cudaSuccess) return e;
+                kb_collide_particles<C><<<L->link, kPartThreads, 0, s>>>(L->L);
+                if ((e = node(0, cfg[0], L, s)) != cudaSuccess) return e;
+                if ((e = node(1, cfg[1], L, s)) != cudaSuccess) return e;
+                kb_scalars_particles<C><<<L->link, kPartThreads, 0, s>>>(L->L);
                 kb_cover_mark<C><<<L->cover, kPartThreads, 0, s>>>(L->L);
+                kb_cover_apply<C><<<L->cover, kPartThreads, 0, s>>>(L->L);
             }
-            kb_cover_apply<C><<<L->cover, kPartThreads, 0, s>>>(L->L);
         }
         kb_advance<<<(nbox + 255) / 256, 256, 0, s>>>(left, nbox);
         return cudaGetLastError();

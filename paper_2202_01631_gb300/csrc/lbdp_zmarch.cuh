@@ -45,6 +45,20 @@ struct ZPlane1 {
     static constexpr int slots = kZ1;
 };
 
+// Shared-memory place of field k of slot s in a plane of T::slots slots:
+// fields 2j and 2j+1 interleave ([j][slot][2]), so a body that reads both
+// gets them in one 64-bit load; an odd last field stands alone.
+template <class T>
+__host__ __device__ constexpr int tile_index(int k, int s)
+{
+    return (k & ~1) * T::slots + 2 * s + (k & 1);
+}
+template <int NF, class T>
+__host__ __device__ constexpr int tile_index_last(int k, int s)
+{
+    return ((NF & 1) && k == NF - 1) ? (NF - 1) * T::slots + s : tile_index<T>(k, s);
+}
+
 // The stress of one node (p_iso, grad psi) as one aligned vector, so that a
 // neighbour's four numbers come in one shared-memory load.
 template <class F>
@@ -71,7 +85,7 @@ struct ScalSmem {
 __device__ __forceinline__ int zm_coord(int o, int l, int L, int per) { return wrap_coord(o + l, L, per); }
 
 // ---------------------------------------------------------------------------
-// accessors over the shared-memory planes (same interface as GAcc / TAcc)
+// accessors over the shared-memory planes (same interface as GAcc)
 // ---------------------------------------------------------------------------
 // chemical-potential body: field 0 psi (two-halo planes), field 1 phi (own)
 template <class F, bool kClear>
@@ -437,19 +451,15 @@ constexpr int fused_blocks_per_sm()
     return sizeof(typename C::real) == 8 ? 2 : 4;
 }
 
+// The march of one block: columns x0 .. x0 + 31, y0 .. y0 + 7, planes
+// z0 .. z0 + nt - 1 (nt >= 1), smem of sizeof(FusedSmem<F>) bytes.
 template <class C>
-__global__ void __launch_bounds__(kZThreads, fused_blocks_per_sm<C>()) kz_fused(const __grid_constant__ DevParams P,
-                                                                               const __grid_constant__ DevPtrs D)
+__device__ __forceinline__ void kz_fused_run(const DevParams& P, const DevPtrs& D, int x0, int y0, int z0, int nt,
+                                             unsigned char* smem_raw)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
-    extern __shared__ __align__(16) unsigned char smem_raw[];   // sizeof(FusedSmem<F>)
     FusedSmem<F>& sm = *reinterpret_cast<FusedSmem<F>*>(smem_raw);
-    const int x0 = blockIdx.x * kZX, y0 = blockIdx.y * kZY;
-    const int zc = zm_chunk(P.nz, gridDim.z);
-    const int z0 = blockIdx.z * zc;
-    const int nt = min(z0 + zc, P.nz) - z0;   // planes of this chunk
-    if (nt <= 0) return;
     MuCols cols;
     mu_cols(P, x0, y0, cols);
     MuSlots ms;
@@ -516,6 +526,19 @@ __global__ void __launch_bounds__(kZThreads, fused_blocks_per_sm<C>()) kz_fused(
     cp_async_wait<0>();
 }
 
+// Single box: grid (column tiles in x, in y, z chunks).
+template <class C>
+__global__ void __launch_bounds__(kZThreads, fused_blocks_per_sm<C>()) kz_fused(const __grid_constant__ DevParams P,
+                                                                               const __grid_constant__ DevPtrs D)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];   // sizeof(FusedSmem<F>)
+    const int zc = zm_chunk(P.nz, gridDim.z);
+    const int z0 = blockIdx.z * zc;
+    const int nt = min(z0 + zc, P.nz) - z0;   // planes of this chunk
+    if (nt <= 0) return;                      // block-uniform
+    kz_fused_run<C>(P, D, blockIdx.x * kZX, blockIdx.y * kZY, z0, nt, smem_raw);
+}
+
 // ---------------------------------------------------------------------------
 // kz_scalars
 // ---------------------------------------------------------------------------
@@ -540,19 +563,14 @@ __device__ __forceinline__ void scal_stage(const DevParams& P, const DevPtrs& D,
     scalars_compute_c<C, false>(P, D, x, y, zs, x + P.nx * (y + P.ny * zs), a, dps, dph);
 }
 
+// The march of one block, as kz_fused_run (smem of sizeof(ScalSmem<F>) bytes).
 template <class C>
-__global__ void __launch_bounds__(kZThreads, 3) kz_scalars(const __grid_constant__ DevParams P,
-                                                           const __grid_constant__ DevPtrs D)
+__device__ __forceinline__ void kz_scalars_run(const DevParams& P, const DevPtrs& D, int x0, int y0, int z0, int nt,
+                                               unsigned char* smem_raw)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
-    extern __shared__ __align__(16) unsigned char smem_raw[];   // sizeof(ScalSmem<F>)
     ScalSmem<F>& sm = *reinterpret_cast<ScalSmem<F>*>(smem_raw);
-    const int x0 = blockIdx.x * kZX, y0 = blockIdx.y * kZY;
-    const int zc = zm_chunk(P.nz, gridDim.z);
-    const int z0 = blockIdx.z * zc;
-    const int nt = min(z0 + zc, P.nz) - z0;
-    if (nt <= 0) return;
     ScalCols cols;
     scal_cols(P, x0, y0, cols);
     const R dps = corr_r<R>(D, 0), dph = corr_r<R>(D, 1);
@@ -594,6 +612,22 @@ __global__ void __launch_bounds__(kZThreads, 3) kz_scalars(const __grid_constant
     cp_async_wait<0>();
 }
 
+// Resident blocks per SM of the transport: three (80 registers) measured
+// faster than four (64) on the 256^3 workload.
+constexpr int kScalBlocksPerSM = 3;
+
+template <class C>
+__global__ void __launch_bounds__(kZThreads, kScalBlocksPerSM) kz_scalars(const __grid_constant__ DevParams P,
+                                                                          const __grid_constant__ DevPtrs D)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];   // sizeof(ScalSmem<F>)
+    const int zc = zm_chunk(P.nz, gridDim.z);
+    const int z0 = blockIdx.z * zc;
+    const int nt = min(z0 + zc, P.nz) - z0;
+    if (nt <= 0) return;   // block-uniform
+    kz_scalars_run<C>(P, D, blockIdx.x * kZX, blockIdx.y * kZY, z0, nt, smem_raw);
+}
+
 // ---------------------------------------------------------------------------
 // the pressure tensor and force next to particles, for the side stream
 // ---------------------------------------------------------------------------
@@ -611,19 +645,32 @@ __device__ __forceinline__ void pt_box(const DevParams& P, const DevPart& q, int
     }
 }
 
+// Blocks per particle of k_pt_part (about one node of the box per thread).
+__host__ __device__ inline int pt_part_blocks(const DevParams& P)
+{
+    long long t = 1;
+    const int L[3] = {P.nx, P.ny, P.nz};
+    for (int a = 0; a < 3; ++a) {
+        int s = P.side1[a] + 2;
+        if (P.per[a] && s > L[a]) s = L[a];
+        t *= s;
+    }
+    const long long b = (t + kPartThreads - 1) / kPartThreads;
+    return (int)(b < 1 ? 1 : (b > kMaxPartBlocks ? kMaxPartBlocks : b));
+}
+
+// Block bi of the nbi blocks of particle p.
 template <class C>
-__global__ void __launch_bounds__(kPartThreads) k_pt_part(const __grid_constant__ DevParams P,
-                                                           const __grid_constant__ DevPtrs D)
+__device__ __forceinline__ void pt_part_block(const DevParams& P, const DevPtrs& D, int p, int bi, int nbi)
 {
     using R = typename C::real;
     using F = typename C::fld_t;
     if (!P.thermo) return;
-    const int p = blockIdx.y;
     int o[3], sd[3];
     pt_box(P, D.parts[p], o, sd);
     const int tot = sd[0] * sd[1] * sd[2];
     const size_t N = (size_t)P.N;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+    for (int t = bi * blockDim.x + threadIdx.x; t < tot; t += nbi * blockDim.x) {
         int x, y, z;
         if (!box_node(P, o, sd, t, x, y, z)) continue;
         const int n = x + P.nx * (y + P.ny * z);
@@ -642,17 +689,22 @@ __global__ void __launch_bounds__(kPartThreads) k_pt_part(const __grid_constant_
     }
 }
 
+template <class C>
+__global__ void __launch_bounds__(kPartThreads) k_pt_part(const __grid_constant__ DevParams P,
+                                                           const __grid_constant__ DevPtrs D)
+{
+    pt_part_block<C>(P, D, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
 // F at the fluid nodes next to particle p (those whose lowest adjacent
 // particle is p, as in k_collide_particles), into the force array.
 template <class C>
-__global__ void __launch_bounds__(kPartThreads) k_f_part(const __grid_constant__ DevParams P,
-                                                          const __grid_constant__ DevPtrs D)
+__device__ __forceinline__ void f_part_block(const DevParams& P, const DevPtrs& D, int p, int bi, int nbi)
 {
-    const int p = blockIdx.y;
     const DevPart& q = D.parts[p];
     const int o[3] = {q.g.Xi[0] - q.Rc - 2, q.g.Xi[1] - q.Rc - 2, q.g.Xi[2] - q.Rc - 2};
     const int tot = P.side1[0] * P.side1[1] * P.side1[2];
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+    for (int t = bi * blockDim.x + threadIdx.x; t < tot; t += nbi * blockDim.x) {
         int x, y, z;
         if (!box_node(P, o, P.side1, t, x, y, z)) continue;
         const int n = x + P.nx * (y + P.ny * z);
@@ -668,6 +720,13 @@ __global__ void __launch_bounds__(kPartThreads) k_f_part(const __grid_constant__
         if (lo != p + 1) continue;
         fdiv_node<C>(P, D, x, y, z);
     }
+}
+
+template <class C>
+__global__ void __launch_bounds__(kPartThreads) k_f_part(const __grid_constant__ DevParams P,
+                                                          const __grid_constant__ DevPtrs D)
+{
+    f_part_block<C>(P, D, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 }  // namespace lbdp

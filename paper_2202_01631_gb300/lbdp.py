@@ -137,7 +137,7 @@ def _load():
         "lbb_tune": (C.c_int, [h, C.c_int, P(C.c_int), dp]),
         "lbb_set_config": (C.c_int, [h, P(C.c_int)]),
         "lbb_num_configs": (C.c_int, []),
-        "lbb_config_shape": (C.c_int, [C.c_int, P(C.c_int), P(C.c_int), P(C.c_int)]),
+        "lbb_config_shape": (C.c_int, [C.c_int, P(C.c_int), P(C.c_int)]),
         "lbb_sync": (C.c_int, [h]),
         "lbs_create": (C.c_int, [P(LbsParams), P(h)]),
         "lbs_destroy": (None, [h]),
@@ -403,17 +403,25 @@ def lbb_run(b, nsteps: int) -> int:
     return int(n.value)
 
 
+# bulk kernel classes the batch autotuner times (include/lbdp_batch.h)
+BATCH_KERNEL_CLASSES = ("fused", "transport")
+
+
 def lbb_tune(b, reps: int = 10):
-    """Autotune the node kernels; returns the chosen candidate per kernel class
-    and its time in ms (four of each)."""
-    cfg = (C.c_int * 4)()
-    ms = np.zeros(4)
+    """Autotune the z chunk of the two bulk kernels; returns the chosen
+    candidate per kernel class and its time in ms."""
+    k = len(BATCH_KERNEL_CLASSES)
+    cfg = (C.c_int * k)()
+    ms = np.zeros(k)
     _check(_lib.lbb_tune(b, int(reps), cfg, _dptr(ms)), "lbb_tune")
     return list(cfg), ms.tolist()
 
 
 def lbb_set_config(b, cfg) -> None:
-    _check(_lib.lbb_set_config(b, (C.c_int * 4)(*[int(c) for c in cfg])), "lbb_set_config")
+    k = len(BATCH_KERNEL_CLASSES)
+    if len(cfg) != k:
+        raise ValueError("one candidate per bulk kernel class (%d)" % k)
+    _check(_lib.lbb_set_config(b, (C.c_int * k)(*[int(c) for c in cfg])), "lbb_set_config")
 
 
 def lbb_num_configs() -> int:
@@ -421,10 +429,10 @@ def lbb_num_configs() -> int:
 
 
 def lbb_config_shape(k: int):
-    """(threads, cells per thread, register budget) of candidate k."""
-    t, c, r = C.c_int(0), C.c_int(0), C.c_int(0)
-    _check(_lib.lbb_config_shape(int(k), C.byref(t), C.byref(c), C.byref(r)), "lbb_config_shape")
-    return t.value, c.value, r.value
+    """(threads per block, planes per block) of candidate k."""
+    t, z = C.c_int(0), C.c_int(0)
+    _check(_lib.lbb_config_shape(int(k), C.byref(t), C.byref(z)), "lbb_config_shape")
+    return t.value, z.value
 
 
 def lbb_sync(b) -> None:

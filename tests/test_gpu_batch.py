@@ -98,7 +98,7 @@ def test_batch_matches_alone(lbdp, precision):
             batch.set_steps(b, steps[k])
             members.append(b)
         launches = batch.run(100)          # stops when every box is done: 2 graphs + 2 plain steps
-        assert launches == 10 * 8
+        assert launches == 10 * 10         # 9 per launch plan + the count-down, per step
         batch.sync()
         for k, b in enumerate(members):
             assert batch.steps_left(b) == 0
@@ -108,11 +108,14 @@ def test_batch_matches_alone(lbdp, precision):
 
 
 def test_batch_autotuned_launch_shapes(lbdp):
-    """Every candidate shape, and the tuner's pick, give the same bits; the
-    tuning runs leave the state unchanged."""
+    """Every candidate shape (z chunk of the fused and transport kernels), and
+    the tuner's pick, give the same bits; the tuning runs leave the state
+    unchanged."""
     specs = _specs()
     ref = [_alone(lbdp, s, k, "fp32", 6) for k, s in enumerate(specs)]
-    for cfg in [[0, 0, 0, 0], [1, 2, 3, 1], [3, 4, 2, 4], None]:
+    assert lbdp.lbb_num_configs() == 3
+    assert [lbdp.lbb_config_shape(k) for k in range(3)] == [(256, 8), (256, 16), (256, 32)]
+    for cfg in [[0, 0], [2, 1], [1, 2], None]:
         batch = lbdp.Batch(precision="fp32", arena_bytes=1 << 30, graph_steps=3)
         try:
             members = []
@@ -122,7 +125,7 @@ def test_batch_autotuned_launch_shapes(lbdp):
                 batch.set_steps(b, 6)
                 members.append(b)
             with pytest.raises(lbdp.LbError):
-                batch.set_config([4, 0, 0, 0])   # the tile candidate exists for force and transport only
+                batch.set_config([3, 0])   # no such candidate
             if cfg is None:
                 got, ms = batch.tune(reps=3)
                 assert all(0 <= c < lbdp.lbb_num_configs() for c in got) and all(m > 0 for m in ms)
