@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--scalar-scheme", type=int, default=0, choices=[0, 1],
                     help="psi/phi transport: 0 finite differences, 1 D3Q7 lattice Boltzmann")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="single form: keep the size heuristic's z chunks")
     ap.add_argument("--form", default="single", choices=["single", "batched", "served"])
     ap.add_argument("--boxes", type=int, default=64, help="batched form: number of boxes")
     ap.add_argument("--requests", type=int, default=32, help="served form: number of requests")
@@ -425,6 +426,11 @@ def run_ours(args):
     box = build_box(wl, args.precision, stream.cuda_stream)
     box.step(args.warmup)
     box.sync()
+    # z chunk length of the two bulk kernels, timed on this machine (not timed)
+    if args.no_tune:
+        planes, tune_ms = box.planes(), None
+    else:
+        planes, tune_ms = box.tune(reps=5)
 
     # ---- device-resident throughput -------------------------------------
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -470,6 +476,7 @@ def run_ours(args):
     outs = {k: torch.empty_like(v).pin_memory() for k, v in host.items()}
     e2e_steps = args.steps
     box2 = build_box(wl, args.precision, stream.cuda_stream)
+    box2.set_planes(planes["k_fused"], planes["k_scalars"])
     box2.sync()
     barrier(group)
     torch.cuda.synchronize()
@@ -501,7 +508,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
         "config": dict(workload_config(args, wl), precision=args.precision,
                        parallelism="replicas" if world > 1 else "single",
-                       l2="state %.2f GB > L2 (129 MB); no flush" % (lbdp.lb_device_bytes(box.params) / 1e9)),
+                       l2="state %.2f GB > L2 (129 MB); no flush" % (lbdp.lb_device_bytes(box.params) / 1e9),
+                       z_planes=planes, z_tune_ms=tune_ms),
         "roofline": {"bound": "hbm", "kernel": coll_name, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": traffic,

@@ -176,6 +176,26 @@ int lb_step(lb_handle* h, int nsteps);
  * call is for the split. */
 int lb_profile_step(lb_handle* h, int nsteps, double* ms, int* launches);
 
+/* Autotuning.  The two bulk kernels (the fused chemical potentials, stress,
+ * force and collide-stream, and the psi/phi transport) march along z through
+ * 32 x 8 column tiles; a block takes one z chunk.  Short chunks recompute
+ * more halo planes, long ones leave SMs idle, and the best length depends on
+ * the box, so lb_tune times each kernel alone over reps launches for chunk
+ * lengths from 4 to 64 planes (each rounded to equal chunks) and keeps the
+ * fastest per kernel.  The kernels only rewrite the next step's buffers and
+ * the stored velocity, which is saved and restored: the state is unchanged,
+ * and the results of later steps do not depend on the chunk length (bit for
+ * bit).  planes_out[2], ms_out[2] (optional): the chosen lengths and their
+ * times per launch (0 fused, 1 transport).  Synchronises.  LB_ERR_PARAM for
+ * reps < 1. */
+int lb_tune(lb_handle* h, int reps, int planes_out[2], double ms_out[2]);
+/* Set the chunk lengths directly; 0 restores the size heuristic (a chunk
+ * count of about six waves of four blocks per SM, chunks of at least 6
+ * planes); lengths above nz are clamped.  LB_ERR_PARAM for a negative one. */
+int lb_set_planes(lb_handle* h, const int planes[2]);
+/* The chunk lengths the next lb_step uses (after rounding to equal chunks). */
+int lb_get_planes(const lb_handle* h, int planes[2]);
+
 /* Number of kernels lb_step(h, nsteps) launches (for launch accounting). */
 int lb_step_launches(const lb_handle* h, int nsteps);
 

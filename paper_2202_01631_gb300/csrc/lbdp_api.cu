@@ -6,6 +6,7 @@
 
 #include <new>
 #include <cmath>
+#include <algorithm>
 #include <vector>
 
 #include "lbdp.h"
@@ -142,23 +143,37 @@ DevPtrs cur_ptrs(const lb_handle* h)
     return d;
 }
 
-RowGrid row_grid(const DevParams& P)
+// z chunk length the size heuristic picks: enough chunks for about six waves
+// of four blocks per SM on 152 SMs, each chunk at least 6 planes long
+// (measured on GB300: 256^3 is fastest with chunks of 12 to 24 planes, 128^3
+// with 6 to 8; shorter chunks repeat more halo planes, fewer blocks leave SMs
+// idle).  lb_tune replaces it with a measured choice.
+int default_planes(const DevParams& P)
 {
-    RowGrid g;
-    // z-marching kernels: enough z chunks for about six waves of four blocks
-    // per SM on 152 SMs, each chunk at least 6 planes long (measured on GB300:
-    // 256^3 is fastest with chunks of 12 to 24 planes, 128^3 with 6 to 8;
-    // shorter chunks repeat more halo planes, fewer blocks leave SMs idle)
     const long long cols = (long long)((P.nx + 31) / 32) * ((P.ny + 7) / 8);
     const long long target = 152LL * 4 * 6;
     long long chunks = (target + cols - 1) / cols;
     const long long max_chunks = P.nz / 6 > 1 ? P.nz / 6 : 1;
     if (chunks > max_chunks) chunks = max_chunks;
     if (chunks < 1) chunks = 1;
-    // no empty chunk: ceil(nz / chunks) planes each
-    const int zc = (int)((P.nz + chunks - 1) / chunks);
-    chunks = (P.nz + zc - 1) / zc;
-    g.zgrid = dim3((P.nx + 31) / 32, (P.ny + 7) / 8, (unsigned)chunks);
+    return (int)((P.nz + chunks - 1) / chunks);
+}
+
+// Grid of a z-marching kernel with chunks of `planes` planes (no empty chunk).
+dim3 zm_grid(const DevParams& P, int planes)
+{
+    if (planes < 1) planes = 1;
+    if (planes > P.nz) planes = P.nz;
+    const int chunks = (P.nz + planes - 1) / planes;
+    return dim3((P.nx + 31) / 32, (P.ny + 7) / 8, (unsigned)chunks);
+}
+
+RowGrid row_grid(const lb_handle* h)
+{
+    RowGrid g;
+    const int d = default_planes(h->dp);
+    g.zgrid = zm_grid(h->dp, h->zplanes[0] > 0 ? h->zplanes[0] : d);
+    g.zgrid_s = zm_grid(h->dp, h->zplanes[1] > 0 ? h->zplanes[1] : d);
     return g;
 }
 
@@ -183,9 +198,18 @@ void update_sides(lb_handle* h)
     h->dp.nb2 = (int)(b2 < kMaxPartBlocks ? (b2 > 0 ? b2 : 1) : kMaxPartBlocks);
 }
 
+void drop_step_graphs(lb_handle* h)
+{
+    for (cudaGraphExec_t& g : h->gexec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
 void free_all(lb_handle* h)
 {
     if (h->device >= 0) cudaSetDevice(h->device);
+    drop_step_graphs(h);
     if (h->side.s) {
         cudaStreamSynchronize(h->side.s);
         cudaStreamDestroy(h->side.s);
@@ -225,6 +249,46 @@ int read_err(lb_handle* h)
     if (e & (kErrOverlap | kErrWall)) return LB_ERR_OVERLAP;
     if (e & kErrSolve) return LB_ERR_NONFINITE;
     return LB_OK;
+}
+
+
+// Steps per captured graph of lb_step (even: a launch leaves the parity).
+constexpr int kGraphSteps = 8;
+
+bool same_grid(const dim3& a, const dim3& b) { return a.x == b.x && a.y == b.y && a.z == b.z; }
+
+// kGraphSteps steps from parity p0 captured on the handle's stream.
+int capture_steps(lb_handle* h, const RowGrid& g, int p0)
+{
+    LB_TRY(h->ops->prepare());
+    cudaGraph_t graph = nullptr;
+    LB_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int st = LB_OK;
+    for (int t = 0; t < kGraphSteps && st == LB_OK; ++t)
+        st = cuda_status(h->ops->step(h->dp, ptrs(h, (p0 + t) & 1), g, h->stream, h->side.s ? &h->side : nullptr));
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (st == LB_OK) st = cuda_status(e);
+    if (st == LB_OK) st = cuda_status(cudaGraphInstantiate(&h->gexec[p0], graph, 0));
+    if (graph) cudaGraphDestroy(graph);
+    if (st != LB_OK) {
+        h->gexec[p0] = nullptr;
+        cudaGetLastError();
+    }
+    return st;
+}
+
+// Whether lb_step may capture on the handle's stream: not the legacy default
+// stream, and not while the caller is capturing it into a graph of its own
+// (then the plain launches become part of the caller's graph).
+bool can_capture(lb_handle* h)
+{
+    if (!h->stream) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs == cudaStreamCaptureStatusNone;
 }
 
 }  // namespace
@@ -398,8 +462,31 @@ int lb_step(lb_handle* h, int nsteps)
 {
     if (!h || nsteps < 0) return LB_ERR_PARAM;
     cudaSetDevice(h->device);
-    const RowGrid g = row_grid(h->dp);
-    for (int t = 0; t < nsteps; ++t) {
+    const RowGrid g = row_grid(h);
+    int t = 0;
+    // A box without particles runs whole groups of kGraphSteps steps as one
+    // graph launch each (measured on GB300: 170 instead of 174 us per step at
+    // 128^3); the graphs are captured again when the parameters or the launch
+    // grids have changed since.  With particles the step forks onto the side
+    // stream, and the captured form measured slower than the plain launches
+    // (283 instead of 245 us at 128^3 with one sphere, the side kernels'
+    // priority attribute notwithstanding), so those steps stay plain.
+    if (h->dp.np == 0 && nsteps >= kGraphSteps && can_capture(h)) {
+        if (memcmp(&h->g_dp, &h->dp, sizeof(DevParams)) != 0 || !same_grid(h->g_grid.zgrid, g.zgrid) ||
+            !same_grid(h->g_grid.zgrid_s, g.zgrid_s)) {
+            drop_step_graphs(h);
+            memcpy(&h->g_dp, &h->dp, sizeof(DevParams));
+            h->g_grid = g;
+        }
+        for (; nsteps - t >= kGraphSteps; t += kGraphSteps) {
+            if (!h->gexec[h->cur]) {
+                const int st = capture_steps(h, g, h->cur);
+                if (st != LB_OK) return st;
+            }
+            LB_TRY(cudaGraphLaunch(h->gexec[h->cur], h->stream));
+        }
+    }
+    for (; t < nsteps; ++t) {
         LB_TRY(h->ops->step(h->dp, ptrs(h, h->cur), g, h->stream, h->side.s ? &h->side : nullptr));
         h->cur ^= 1;
     }
@@ -410,7 +497,7 @@ int lb_profile_step(lb_handle* h, int nsteps, double* ms, int* launches)
 {
     if (!h || nsteps < 0 || !ms) return LB_ERR_PARAM;
     cudaSetDevice(h->device);
-    const RowGrid g = row_grid(h->dp);
+    const RowGrid g = row_grid(h);
     std::vector<cudaEvent_t> ev((size_t)nsteps * 6);
     for (auto& e : ev) LB_TRY(cudaEventCreate(&e));
     int st = LB_OK;
@@ -433,6 +520,83 @@ int lb_profile_step(lb_handle* h, int nsteps, double* ms, int* launches)
     for (auto& e : ev) cudaEventDestroy(e);
     if (launches) *launches = nsteps * (h->dp.np > 0 ? 9 : 2);
     return st;
+}
+
+int lb_tune(lb_handle* h, int reps, int planes_out[2], double ms_out[2])
+{
+    if (!h || reps < 1) return LB_ERR_PARAM;
+    cudaSetDevice(h->device);
+    cudaStream_t s = h->stream;
+    const DevParams& P = h->dp;
+    const DevPtrs D = ptrs(h, h->cur);
+    // kz_fused rewrites the stored velocity of the bulk nodes: keep a copy
+    const size_t ub = 3 * (size_t)P.N * h->ops->fld_bytes;
+    LB_TRY(cudaMemcpyAsync(h->staging, h->u, ub, cudaMemcpyDeviceToDevice, s));
+    // candidate chunk lengths, each kept once after rounding to equal chunks
+    static const int kCand[] = {4, 6, 8, 12, 16, 24, 32, 48, 64};
+    std::vector<int> cand;
+    for (int c : kCand) {
+        if (c > P.nz && !cand.empty()) break;
+        const int p = (int)zm_grid(P, c).z;
+        const int planes = (P.nz + p - 1) / p;
+        if (std::find(cand.begin(), cand.end(), planes) == cand.end()) cand.push_back(planes);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int st = cuda_status(cudaEventCreate(&e0));
+    if (st == LB_OK) st = cuda_status(cudaEventCreate(&e1));
+    int best[2] = {0, 0};
+    double best_ms[2] = {1e300, 1e300};
+    // kz_scalars reads the chemical potentials and velocity kz_fused leaves:
+    // one kz_fused launch first gives it the inputs of a step
+    for (int which = 0; which < 2 && st == LB_OK; ++which) {
+        for (int planes : cand) {
+            const dim3 grid = zm_grid(P, planes);
+            for (int w = 0; w < 2 && st == LB_OK; ++w) st = cuda_status(h->ops->bulk(which, P, D, grid, s));
+            if (st == LB_OK) st = cuda_status(cudaEventRecord(e0, s));
+            for (int r = 0; r < reps && st == LB_OK; ++r) st = cuda_status(h->ops->bulk(which, P, D, grid, s));
+            if (st == LB_OK) st = cuda_status(cudaEventRecord(e1, s));
+            if (st == LB_OK) st = cuda_status(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            if (st == LB_OK) st = cuda_status(cudaEventElapsedTime(&ms, e0, e1));
+            if (st != LB_OK) break;
+            if (ms / reps < best_ms[which]) {
+                best_ms[which] = ms / reps;
+                best[which] = planes;
+            }
+        }
+    }
+    {
+        const cudaError_t e = cudaMemcpyAsync(h->u, h->staging, ub, cudaMemcpyDeviceToDevice, s);
+        if (st == LB_OK) st = cuda_status(e);
+    }
+    if (st == LB_OK) st = cuda_status(cudaStreamSynchronize(s));
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != LB_OK) return st;
+    for (int k = 0; k < 2; ++k) {
+        h->zplanes[k] = best[k];
+        if (planes_out) planes_out[k] = best[k];
+        if (ms_out) ms_out[k] = best_ms[k];
+    }
+    return LB_OK;
+}
+
+int lb_set_planes(lb_handle* h, const int planes[2])
+{
+    if (!h || !planes) return LB_ERR_PARAM;
+    for (int k = 0; k < 2; ++k)
+        if (planes[k] < 0) return LB_ERR_PARAM;
+    for (int k = 0; k < 2; ++k) h->zplanes[k] = planes[k] > h->dp.nz ? h->dp.nz : planes[k];
+    return LB_OK;
+}
+
+int lb_get_planes(const lb_handle* h, int planes[2])
+{
+    if (!h || !planes) return LB_ERR_PARAM;
+    const RowGrid g = row_grid(h);
+    planes[0] = (h->dp.nz + (int)g.zgrid.z - 1) / (int)g.zgrid.z;
+    planes[1] = (h->dp.nz + (int)g.zgrid_s.z - 1) / (int)g.zgrid_s.z;
+    return LB_OK;
 }
 
 int lb_step_launches(const lb_handle* h, int nsteps)
@@ -791,6 +955,7 @@ int lb_create_in(const lb_params* p, lbb_batch* batch, void* region, lb_handle**
     if (e == cudaSuccess) {
         int lo = 0, hi = 0;
         e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        h->side.prio = hi;
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side.s, cudaStreamNonBlocking, hi);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.links_done, cudaEventDisableTiming);

@@ -318,6 +318,7 @@ int lbb_create(const lbb_params* p, lbb_batch** out)
     if (e == cudaSuccess) {
         int lo = 0, hi = 0;
         e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        b->side.prio = hi;
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->side.s, cudaStreamNonBlocking, hi);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.bnd_done, cudaEventDisableTiming);

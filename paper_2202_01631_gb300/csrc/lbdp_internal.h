@@ -15,7 +15,8 @@ namespace lbdp {
 
 // Launch geometry of the bulk kernels of one box.
 struct RowGrid {
-    dim3 zgrid;   // grid of the z-marching kernels: 32 x 8 column tiles x z chunks
+    dim3 zgrid;     // grid of kz_fused: 32 x 8 column tiles x z chunks
+    dim3 zgrid_s;   // grid of kz_scalars, the same tiles with its own z chunks
 };
 
 // Kernel classes of one step, in the order of the sequential profile: the
@@ -37,16 +38,24 @@ enum KernelClass { kKParticles = 0, kKFused, kKScalars, kKScalarsParticles, kKCo
 struct SideStream {
     cudaStream_t s;
     cudaEvent_t fork, links_done, mark_done, fdiv_done, bnd_done, collide_done, scal_done;
+    // the stream's priority (the device's highest), also given to each of
+    // its kernels as a launch attribute: a kernel node of a captured graph
+    // does not keep the priority of the stream it was captured from
+    int prio;
 };
 
 struct PrecOps {
     int pop_bytes;   // bytes per stored population value
     int fld_bytes;   // bytes per stored field value
+    // per-device kernel attributes (before the first launch or capture)
+    cudaError_t (*prepare)();
     // one full time step (fluid kernels, then particle kernels when np > 0)
     cudaError_t (*step)(const DevParams&, const DevPtrs&, const RowGrid&, cudaStream_t, const SideStream*);
     // the same step with an event recorded before the first kernel and after
     // each kernel class: ev[0..5] around mu, links, collide, scalars, cover
     cudaError_t (*step_events)(const DevParams&, const DevPtrs&, const RowGrid&, cudaStream_t, cudaEvent_t* ev);
+    // one bulk kernel alone over grid: which 0 kz_fused, 1 kz_scalars
+    cudaError_t (*bulk)(int which, const DevParams&, const DevPtrs&, dim3 grid, cudaStream_t);
     // staging (FP64, device) -> state; NULL entries keep the field
     cudaError_t (*set_fields)(const DevParams&, const DevPtrs&, cudaStream_t, const double* rho,
                               const double* u, const double* psi, const double* phi);
@@ -142,6 +151,12 @@ struct lb_handle {
     double* red_out;
     unsigned long long* count;
     int red_blocks;
+    int zplanes[2];   // z chunk length of kz_fused, kz_scalars (0 = size heuristic)
+    // lb_step's CUDA graphs of kGraphSteps steps from parity 0 / 1, and the
+    // parameters and grids they were captured with (recaptured on a change)
+    cudaGraphExec_t gexec[2];
+    lbdp::DevParams g_dp;
+    lbdp::RowGrid g_grid;
     std::vector<lbdp::DevPart> host_parts;
     double rmax;
 };

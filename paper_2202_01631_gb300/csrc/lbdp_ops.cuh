@@ -27,6 +27,24 @@ inline cudaError_t set_carveout(const void* fn, int blocks, size_t smem)
     return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)pct);
 }
 
+// Launch of a side-stream kernel with the side stream's priority as a launch
+// attribute, so that it keeps the priority inside captured graphs too.
+template <class... A>
+inline void side_launch(void (*k)(A...), dim3 grid, size_t smem, const SideStream* side, A... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kPartThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = side->s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = side->prio;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Resident blocks per SM the tiled force and transport kernels are given
 // (measured on the 128^3 workload: 5 and 4 beat the 7 and 6 their register
 // counts allow by 5 and 10 us).
@@ -78,23 +96,23 @@ struct Ops {
         if (P.np > 0 && side && !ev) {
             cudaEventRecord(side->fork, s);
             cudaStreamWaitEvent(side->s, side->fork, 0);
-            k_pt_part<C><<<pgt, kPartThreads, 0, side->s>>>(P, D);
-            k_f_part<C><<<pg1, kPartThreads, 0, side->s>>>(P, D);
-            k_links<C><<<pg1, kPartThreads, kLinkSmem, side->s>>>(P, D);
-            k_collide_particles<C><<<pg1, kPartThreads, 0, side->s>>>(P, D);
+            side_launch(k_pt_part<C>, pgt, 0, side, P, D);
+            side_launch(k_f_part<C>, pg1, 0, side, P, D);
+            side_launch(k_links<C>, pg1, kLinkSmem, side, P, D);
+            side_launch(k_collide_particles<C>, pg1, 0, side, P, D);
             cudaEventRecord(side->bnd_done, side->s);
-            k_cover_mark<C><<<pg2, kPartThreads, 0, side->s>>>(P, D);
+            side_launch(k_cover_mark<C>, pg2, 0, side, P, D);
             kz_fused<C><<<g.zgrid, kZThreads, kFusedSmem, s>>>(P, D);
             cudaEventRecord(side->collide_done, s);
             cudaStreamWaitEvent(side->s, side->collide_done, 0);
-            k_scalars_particles<C><<<pg1, kPartThreads, 0, side->s>>>(P, D);
+            side_launch(k_scalars_particles<C>, pg1, 0, side, P, D);
             // covering touches only nodes next to particles, whose fields the
             // side-stream kernels wrote, and leaves the next step's uniform
             // correction in the other buffer: it runs beside the transport
-            k_cover_apply<C><<<pg2, kPartThreads, 0, side->s>>>(P, D);
+            side_launch(k_cover_apply<C>, pg2, 0, side, P, D);
             cudaEventRecord(side->scal_done, side->s);
             cudaStreamWaitEvent(s, side->bnd_done, 0);
-            kz_scalars<C><<<g.zgrid, kZThreads, kZScalSmem, s>>>(P, D);
+            kz_scalars<C><<<g.zgrid_s, kZThreads, kZScalSmem, s>>>(P, D);
             cudaStreamWaitEvent(s, side->scal_done, 0);   // the step ends with the side stream
             return cudaGetLastError();
         }
@@ -108,7 +126,7 @@ struct Ops {
         if (ev) cudaEventRecord(ev[1], s);
         kz_fused<C><<<g.zgrid, kZThreads, kFusedSmem, s>>>(P, D);
         if (ev) cudaEventRecord(ev[2], s);
-        kz_scalars<C><<<g.zgrid, kZThreads, kZScalSmem, s>>>(P, D);
+        kz_scalars<C><<<g.zgrid_s, kZThreads, kZScalSmem, s>>>(P, D);
         if (ev) cudaEventRecord(ev[3], s);
         if (P.np > 0) k_scalars_particles<C><<<pg1, kPartThreads, 0, s>>>(P, D);
         if (ev) cudaEventRecord(ev[4], s);
@@ -132,6 +150,17 @@ struct Ops {
                                    cudaEvent_t* ev)
     {
         return launch_step(P, D, g, s, ev, nullptr);
+    }
+
+    static cudaError_t bulk(int which, const DevParams& P, const DevPtrs& D, dim3 grid, cudaStream_t s)
+    {
+        cudaError_t e = prepare();
+        if (e != cudaSuccess) return e;
+        if (which == 0)
+            kz_fused<C><<<grid, kZThreads, kFusedSmem, s>>>(P, D);
+        else
+            kz_scalars<C><<<grid, kZThreads, kZScalSmem, s>>>(P, D);
+        return cudaGetLastError();
     }
 
     static int grid1d(const DevParams& P)
@@ -174,8 +203,10 @@ struct Ops {
         PrecOps t;
         t.pop_bytes = (int)sizeof(typename C::pop_t);
         t.fld_bytes = (int)sizeof(typename C::fld_t);
+        t.prepare = &prepare;
         t.step = &step;
         t.step_events = &step_events;
+        t.bulk = &bulk;
         t.set_fields = &set_fields;
         t.get_fields = &get_fields;
         t.get_pop = &get_pop;
@@ -249,17 +280,17 @@ struct BOps {
             if (side) {
                 cudaEventRecord(side->fork, s);
                 cudaStreamWaitEvent(side->s, side->fork, 0);
-                kb_pt_part<C><<<L->ptg, kPartThreads, 0, side->s>>>(L->L);
-                kb_f_part<C><<<L->link, kPartThreads, 0, side->s>>>(L->L);
-                kb_links<C><<<L->link, kPartThreads, lsm, side->s>>>(L->L);
-                kb_collide_particles<C><<<L->link, kPartThreads, 0, side->s>>>(L->L);
+                side_launch(kb_pt_part<C>, L->ptg, 0, side, L->L);
+                side_launch(kb_f_part<C>, L->link, 0, side, L->L);
+                side_launch(kb_links<C>, L->link, lsm, side, L->L);
+                side_launch(kb_collide_particles<C>, L->link, 0, side, L->L);
                 cudaEventRecord(side->bnd_done, side->s);
-                kb_cover_mark<C><<<L->cover, kPartThreads, 0, side->s>>>(L->L);
+                side_launch(kb_cover_mark<C>, L->cover, 0, side, L->L);
                 if ((e = node(0, cfg[0], L, s)) != cudaSuccess) return e;
                 cudaEventRecord(side->collide_done, s);
                 cudaStreamWaitEvent(side->s, side->collide_done, 0);
-                kb_scalars_particles<C><<<L->link, kPartThreads, 0, side->s>>>(L->L);
-                kb_cover_apply<C><<<L->cover, kPartThreads, 0, side->s>>>(L->L);
+                side_launch(kb_scalars_particles<C>, L->link, 0, side, L->L);
+                side_launch(kb_cover_apply<C>, L->cover, 0, side, L->L);
                 cudaEventRecord(side->scal_done, side->s);
                 cudaStreamWaitEvent(s, side->bnd_done, 0);
                 if ((e = node(1, cfg[1], L, s)) != cudaSuccess) return e;
@@ -285,6 +316,7 @@ struct BOps {
         BatchOps t;
         t.prepare = &prepare;
         t.node = &node;
+        t.prepare = &prepare;
         t.step = &step;
         return t;
     }

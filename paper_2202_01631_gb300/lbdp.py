@@ -104,6 +104,9 @@ def _load():
         "lb_sync": (C.c_int, [h]),
         "lb_profile_step": (C.c_int, [h, C.c_int, dp, P(C.c_int)]),
         "lb_step_launches": (C.c_int, [h, C.c_int]),
+        "lb_tune": (C.c_int, [h, C.c_int, P(C.c_int), dp]),
+        "lb_set_planes": (C.c_int, [h, P(C.c_int)]),
+        "lb_get_planes": (C.c_int, [h, P(C.c_int)]),
         "lb_read_fields": (C.c_int, [h, dp, dp, dp, dp]),
         "lb_read_mu": (C.c_int, [h, dp, dp]),
         "lb_read_populations": (C.c_int, [h, dp]),
@@ -234,6 +237,27 @@ def lb_profile_step(h, nsteps: int):
     n = C.c_int(0)
     _check(_lib.lb_profile_step(h, int(nsteps), _dptr(ms), C.byref(n)), "lb_profile_step")
     return dict(zip(KERNEL_CLASSES, ms.tolist())), n.value
+
+
+def lb_tune(h, reps: int = 10):
+    """Time the two bulk kernels over z chunk lengths and keep the fastest;
+    returns ({kernel: planes}, {kernel: ms per launch}) for k_fused, k_scalars."""
+    planes = (C.c_int * 2)()
+    ms = np.zeros(2)
+    _check(_lib.lb_tune(h, int(reps), planes, _dptr(ms)), "lb_tune")
+    return (dict(zip(("k_fused", "k_scalars"), list(planes))), dict(zip(("k_fused", "k_scalars"), ms.tolist())))
+
+
+def lb_set_planes(h, fused: int, scalars: int) -> None:
+    """Chunk lengths of the two bulk kernels (0 = size heuristic)."""
+    planes = (C.c_int * 2)(int(fused), int(scalars))
+    _check(_lib.lb_set_planes(h, planes), "lb_set_planes")
+
+
+def lb_get_planes(h):
+    planes = (C.c_int * 2)()
+    _check(_lib.lb_get_planes(h, planes), "lb_get_planes")
+    return {"k_fused": planes[0], "k_scalars": planes[1]}
 
 
 def lb_step_launches(h, nsteps: int) -> int:
@@ -624,6 +648,16 @@ class Box:
 
     def step(self, n: int = 1):
         lb_step(self.h, n)
+
+    def tune(self, reps: int = 10):
+        """Pick the z chunk length of each bulk kernel by timing (lb_tune)."""
+        return lb_tune(self.h, reps)
+
+    def set_planes(self, fused: int = 0, scalars: int = 0):
+        lb_set_planes(self.h, fused, scalars)
+
+    def planes(self):
+        return lb_get_planes(self.h)
 
     def sync(self):
         lb_sync(self.h)

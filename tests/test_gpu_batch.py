@@ -138,6 +138,64 @@ def test_batch_autotuned_launch_shapes(lbdp):
             batch.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_single_box_chunk_lengths_and_tuner(lbdp, precision):
+    """A single box gives the same bits with every z chunk length of its two
+    bulk kernels (one plane up to the whole box, ragged last chunks included)
+    and after lb_tune in mid-run; the tuner's timing launches leave the state
+    unchanged."""
+    spec = _specs()[2]
+    ref = _alone(lbdp, spec, 2, precision, 8)
+    nz = spec["params"]["nz"]
+    for planes in [(1, 1), (7, 4), (4, 7), (16, 30), (nz, 9), (0, 0)]:
+        box = lbdp.Box(precision=precision, **spec["params"])
+        _setup(box, spec, 2)
+        box.set_planes(*planes)
+        got = box.planes()
+        for want, k in zip(planes, ("k_fused", "k_scalars")):
+            if want:
+                assert got[k] * -(-nz // got[k]) >= nz and got[k] <= want
+        box.step(8)
+        _assert_same(box, ref)
+    box = lbdp.Box(precision=precision, **spec["params"])
+    _setup(box, spec, 2)
+    with pytest.raises(lbdp.LbError):
+        box.set_planes(-1, 0)
+    box.step(3)
+    planes, ms = box.tune(reps=2)
+    assert box.planes() == planes and all(1 <= v <= nz for v in planes.values())
+    assert all(m > 0 for m in ms.values())
+    box.step(5)
+    _assert_same(box, ref)
+
+
+def test_single_box_graph_runs_match_plain_steps(lbdp):
+    """lb_step runs whole groups of steps of a box without particles as
+    captured CUDA graphs and the rest as plain launches: one step at a time, in
+    graph-sized runs, and across a change of the launch grids (which makes it
+    capture again) or an added particle between runs (after which it launches
+    plainly), the bits are the same."""
+    spec = _specs()[1]
+    extra = dict(pos=(16.2, 8.1, 10.3), R=2.6, m_hat=(0.0, 0.0, 1.0), alpha=0.0, mu_plus=0.0, mu_minus=0.0,
+                 theta_c_deg=90.0)
+
+    def run(chunks):
+        box = lbdp.Box(precision="fp32", **spec["params"])
+        _setup(box, spec, 1)
+        for c in chunks:
+            if c == "planes":
+                box.set_planes(5, 3)
+            elif c == "particle":
+                box.add_particle(**extra)
+            else:
+                box.step(c)
+        return box
+
+    one = run([1] * 9 + ["planes"] + [1] * 16 + ["particle"] + [1] * 17)
+    graphs = run([9, "planes", 16, "particle", 17])
+    _assert_same(graphs, one)
+
+
 def test_batch_members_leave_and_join(lbdp):
     """A box removed mid-run returns its memory; a new box joins the running
     batch; the others continue undisturbed."""
