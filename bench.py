@@ -702,7 +702,9 @@ def run_served(args):
                 time.sleep(max(0.0, reqs[nxt][0] - (time.perf_counter() - t0)))
     wall = time.perf_counter() - t0
     srv.close()
-    lat = [done[i]["done"] - done[i]["arrival"] for i in done]
+    lat = [done[i]["done"] - done[i]["arrival"] for i in sorted(done)]
+    # a sustainable rate keeps the latency of late arrivals at that of early ones
+    half = len(lat) // 2
     failed = sum(1 for i in done if done[i]["status"] != 0)   # ended early: reported, not hidden
     work = sum(wl.nodes * wl.steps for _, wl in reqs)
     span = max(done[i]["done"] for i in done) - reqs[0][0]
@@ -742,6 +744,8 @@ def run_served(args):
                    "precision": args.precision, "chunk_steps": 64, "arena_gb": 48,
                    "l2": "resident states exceed L2 (129 MB); no flush"},
         "p50_s": _percentile(lat, 50), "p99_s": _percentile(lat, 99), "sims_per_hour": sims_h,
+        "p50_first_half_s": _percentile(lat[:half], 50), "p50_second_half_s": _percentile(lat[half:], 50),
+        "arrival_rate_per_h": args.rate * 3600.0,
         "mlups": work / wall / 1e6, "wall_s": wall, "rounds": rounds, "failed_requests": failed,
         "one_by_one": {"p50_s": _percentile(lat1, 50), "p99_s": _percentile(lat1, 99), "sims_per_hour": sims_h1,
                        "method": "each request timed alone on a sample of its steps; FIFO over the same arrivals"},

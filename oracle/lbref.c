@@ -33,6 +33,15 @@
  * sums, the flux into the moving surfaces, covering) is taken by one thread in
  * the node order x fastest, then y, then z, so the result is bit-identical for
  * any thread count.
+ *
+ * Pins (tests/test_oracle_*.py): every function below is checked against a
+ * closed form, an invariant, a special case or an independent per-node
+ * transcription of the step on 8^3 boxes.  Parity unpinned: the magnitude of
+ * the phoretic speed (the continuum relation of Sec. Particles ties the slip
+ * to a surface flux, not to the lattice production rate, so only its sign and
+ * linearity in the mobility are pinned), and the refill rule of an uncovered
+ * node in step_cover (means of the neighbours), a reading held only by the
+ * exact totals and momentum it keeps.
  */
 #include "lbref.h"
 
