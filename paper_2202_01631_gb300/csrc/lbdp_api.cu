@@ -214,9 +214,6 @@ void free_all(lb_handle* h)
         cudaStreamSynchronize(h->side.s);
         cudaStreamDestroy(h->side.s);
         cudaEventDestroy(h->side.fork);
-        cudaEventDestroy(h->side.links_done);
-        cudaEventDestroy(h->side.mark_done);
-        cudaEventDestroy(h->side.fdiv_done);
         cudaEventDestroy(h->side.bnd_done);
         cudaEventDestroy(h->side.collide_done);
         cudaEventDestroy(h->side.scal_done);
@@ -958,9 +955,6 @@ int lb_create_in(const lb_params* p, lbb_batch* batch, void* region, lb_handle**
         h->side.prio = hi;
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side.s, cudaStreamNonBlocking, hi);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.links_done, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.mark_done, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.fdiv_done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.bnd_done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.collide_done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.scal_done, cudaEventDisableTiming);

@@ -25,23 +25,18 @@ struct RowGrid {
 // fused bulk kernel, the bulk transport, the boundary transport, covering.
 enum KernelClass { kKParticles = 0, kKFused, kKScalars, kKScalarsParticles, kKCover, kNumKernelClasses };
 
-// A second stream for the particle kernels of a step: k_links (which needs
-// only mu/P and the populations) and k_cover_mark run there while the force,
-// collide-stream and transport kernels run on the main stream.  The bulk
-// collide-stream touches no particle, so it does not wait for them;
-// k_collide_particles (the nodes next to particles, which bounce back with
-// the new particle velocities) runs on the side stream after k_links and
-// fdiv_done (the force), beside k_collide, and the transport waits for
-// bnd_done.  In the same way k_scalars_particles and then k_cover_apply wait
-// for collide_done and run beside kt_scalars; the main stream ends the step
-// by waiting for scal_done.
+// A second stream for the particle kernels of a step, at the device's highest
+// priority.  k_pt_part, k_f_part, k_links, k_collide_particles (the nodes next
+// to particles, which bounce back with the new particle velocities; then
+// bnd_done) and k_cover_mark run there beside kz_fused, which touches no node
+// next to a particle.  After kz_fused (collide_done) k_scalars_particles and
+// k_cover_apply run beside kz_scalars, which waits for bnd_done (it reads the
+// velocity of the boundary nodes); the main stream ends the step by waiting
+// for scal_done.
 struct SideStream {
     cudaStream_t s;
-    cudaEvent_t fork, links_done, mark_done, fdiv_done, bnd_done, collide_done, scal_done;
-    // the stream's priority (the device's highest), also given to each of
-    // its kernels as a launch attribute: a kernel node of a captured graph
-    // does not keep the priority of the stream it was captured from
-    int prio;
+    cudaEvent_t fork, bnd_done, collide_done, scal_done;
+    int prio;   // the stream's priority, also given to each of its launches as an attribute
 };
 
 struct PrecOps {

@@ -66,10 +66,6 @@ __host__ __device__ constexpr int cz(int i)
     constexpr int t[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
     return t[i];
 }
-__host__ __device__ constexpr double wgt(int i)
-{
-    return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
-}
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 // Weights and their reciprocals in a given precision: selecting among
 // constants of that type keeps FP64 out of FP32 code even where a loop over
@@ -336,12 +332,6 @@ __device__ __forceinline__ void offset_from(const DevParams& P, const double Xc[
     r[0] = min_image(__dsub_rn((double)x, Xc[0]), P.nx, P.per[0]);
     r[1] = min_image(__dsub_rn((double)y, Xc[1]), P.ny, P.per[1]);
     r[2] = min_image(__dsub_rn((double)z, Xc[2]), P.nz, P.per[2]);
-}
-
-__device__ __forceinline__ void node_offset(const DevParams& P, const DevPart& q, int x, int y, int z,
-                                            double r[3])
-{
-    offset_from(P, q.X, x, y, z, r);
 }
 
 __device__ __forceinline__ double dot3_rn(const double a[3], const double b[3])
