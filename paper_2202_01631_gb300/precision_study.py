@@ -1,7 +1,9 @@
-"""Error of reduced-precision storage against FP64 on the 256^3 workload.
+"""Error of FP32 arithmetic and reduced-precision storage against FP64.
 
-The same seeded input (a 256^3 box, eight Janus spheres R=6 in the slab
-20 < z < 60 below a flat interface at z = 128) is advanced in every
+The same seeded input -- by default the 256^3 box with eight Janus spheres
+R=6 in the slab 20 < z < 60 below a flat interface at z = 128, or with
+``--workload interface`` the 128^3 box with one sphere R=8 at the interface
+(contact angle, solubility ratio and mobility as given) -- is advanced in every
 precision mode of the library side by side; every ``--every`` steps the
 fields and particles of each mode are read back and compared with the FP64
 mode (which the parity tests hold to the CPU oracle within 1e-10 on smaller
@@ -9,6 +11,8 @@ boxes).  Reported per field: max-abs difference and max|a - b| / max|b| over
 nodes that are fluid in both runs; per particle: |dX| / R.
 
     python -m paper_2202_01631_gb300.precision_study --steps 5000 --every 1000
+    python -m paper_2202_01631_gb300.precision_study --workload interface --theta 120 \
+        --ratio 0.5 --mobility -0.1 --steps 20000 --every 5000 --modes fp32,fp16
 
 prints one JSON line per checkpoint and a final summary line.
 """
@@ -62,7 +66,12 @@ def _errors(ref, got, mref, mgot, far):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--edge", type=int, default=256)
+    ap.add_argument("--workload", default="precision", choices=["precision", "interface"],
+                    help="precision: 256^3 with eight spheres; interface: one sphere at a flat interface")
+    ap.add_argument("--edge", type=int, default=0, help="box edge (default 256 / 128 by workload)")
+    ap.add_argument("--theta", type=float, default=60.0, help="interface workload: contact angle (deg)")
+    ap.add_argument("--ratio", type=float, default=2.0, help="interface workload: solubility ratio")
+    ap.add_argument("--mobility", type=float, default=0.1, help="interface workload: phoretic mobility")
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--every", type=int, default=1000)
     ap.add_argument("--modes", default="fp32,fp16,bf16")
@@ -77,7 +86,11 @@ def main(argv=None):
     from paper_2202_01631_gb300 import lbdp
     from paper_2202_01631_gb300 import workloads as W
 
-    wl = W.precision(seed=args.seed, edge=args.edge)
+    if args.workload == "precision":
+        wl = W.precision(seed=args.seed, edge=args.edge or 256)
+    else:
+        wl = W.interface(theta_c_deg=args.theta, solubility_ratio=args.ratio, mobility=args.mobility,
+                         seed=args.seed, edge=args.edge or 128)
     if args.no_particles:
         wl.particles = []
     modes = ["fp64"] + [m for m in args.modes.split(",") if m and m != "fp64"]
@@ -120,6 +133,9 @@ def main(argv=None):
         print(json.dumps(row), flush=True)
     nodes = wl.nodes
     summary = {"workload": wl.name, "nodes": nodes, "spheres": len(wl.particles), "steps": args.steps,
+               "theta_c_deg": wl.particles[0]["theta_c_deg"] if wl.particles else None,
+               "solubility_ratio": wl.params.get("solubility_ratio"),
+               "mobility": wl.particles[0]["mu_plus"] if wl.particles else None,
                "mlups": {m: nodes * args.steps / timing[m] / 1e6 for m in modes},
                "final": history[-1] if history else None}
     print(json.dumps({"summary": summary}), flush=True)

@@ -258,11 +258,13 @@ def test_reduced_storage_error_vs_oracle(prec, tol_u, tol_s):
         assert norm_rel(fg[k], fr[k], mg) < tol_s, k
 
 
-def test_full_size_interface_fp32_100_steps():
-    """The 128^3 single-particle interface workload in the launch configuration
-    the benchmark times, 100 steps against the oracle: every field, velocity
-    included, within 1e-4 of its maximum over the whole box."""
-    wl = W.interface(theta_c_deg=60.0, solubility_ratio=2.0, mobility=0.1)
+@pytest.mark.parametrize("theta,ratio,mobility", [(60.0, 2.0, 0.1), (90.0, 1.0, -0.1), (120.0, 0.5, 0.1)])
+def test_full_size_interface_fp32_100_steps(theta, ratio, mobility):
+    """The 128^3 single-particle interface workload (three points of its sweep
+    over contact angle, solubility ratio and mobility sign), 100 steps against
+    the oracle: every field, velocity included, within 1e-4 of its maximum
+    over the whole box, and the trajectory within 1e-4 R."""
+    wl = W.interface(theta_c_deg=theta, solubility_ratio=ratio, mobility=mobility)
     assert W.min_node_surface_gap(wl) > 1e-6
     box, ref = make_pair(wl.params, wl.fields, wl.particles, precision="fp32")
     box.step(100)
