@@ -855,9 +855,11 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
         }
         if (!have) continue;
         // this node has links into particle p: load everything it needs at once
+        // (the populations as deviations g_i = f_i - w_i rho0: their constant
+        // part is added exactly below, so the link terms carry small numbers)
         R fv[19];
 #pragma unroll
-        for (int i = 1; i < 19; ++i) fv[i] = (R)PopStore<S>::load(fs, (size_t)i * N + n, i, Q.rho0);
+        for (int i = 1; i < 19; ++i) fv[i] = (R)PopStore<S>::load_dev(fs, (size_t)i * N + n, i, Q.rho0);
         const R ps = (R)psi[n] + dps, ph = (R)phi[n] + dph;
         R gphi[3];
         grad_phi_at<R, F>(nb, phi, D.mask, ph, dph, gphi);
@@ -871,9 +873,15 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
         R nacc[K];   // this node's links, added to the FP64 sums once
 #pragma unroll
         for (int k = 0; k < K; ++k) nacc[k] = (R)0;
+        // sum over this node's links of 36 w_i c_i (integers: 2 c_i on an
+        // axis link, c_i on a diagonal one)
+        int wc36[3] = {0, 0, 0};
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
             if (!lk[i]) continue;
+            wc36[0] += (i < 7 ? 2 : 1) * cx(i);
+            wc36[1] += (i < 7 ? 2 : 1) * cy(i);
+            wc36[2] += (i < 7 ? 2 : 1) * cz(i);
             R r[3], ub[3], vs[3];
             link_velocity<R>(P, q, x, y, z, i, gphi, r, ub, vs);
             const R fi = fv[i];
@@ -919,6 +927,29 @@ __device__ __forceinline__ void links_block(const DevParams& P, const DevPtrs& D
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] += (double)nacc[k];
+        // The constant parts of the link momentum -- 2 w_i rho0 c_i of the
+        // bounced populations and 6 w_i (A/4) c_i of the chemical stress, whose
+        // stored isotropic part leaves out the bulk pressure A/4 -- in FP64
+        // from the exact counts: the force (2 rho0 + 1.5 A) sum_i w_i c_i and
+        // its torque about the centre, (x - X) x that force (the c_i / 2 of
+        // each link point is parallel to c_i).  Over the closed surface of a
+        // sphere they cancel; they are kept so that every link counts as in
+        // the definition, next to other spheres too.
+        {
+            const PrmR<double>& Qd = prm<double>(P);
+            const double kc = (2.0 * Qd.rho0 + (P.thermo ? 1.5 * Qd.A : 0.0)) / 36.0;
+            const double fc[3] = {kc * (double)wc36[0], kc * (double)wc36[1], kc * (double)wc36[2]};
+            int Dn[3];
+            int_offset(P, q.g, x, y, z, Dn);
+            const double r0[3] = {__dsub_rn((double)Dn[0], q.g.frd[0]), __dsub_rn((double)Dn[1], q.g.frd[1]),
+                                  __dsub_rn((double)Dn[2], q.g.frd[2])};
+            acc[0] += fc[0];
+            acc[1] += fc[1];
+            acc[2] += fc[2];
+            acc[3] += cross_x(r0[1], fc[2], r0[2], fc[1]);
+            acc[4] += cross_x(r0[2], fc[0], r0[0], fc[2]);
+            acc[5] += cross_x(r0[0], fc[1], r0[1], fc[0]);
+        }
     }
     block_sum_rows<K>(acc, smem);
     double* part = D.link_part + ((size_t)p * kMaxPartBlocks + bi) * K;
