@@ -157,7 +157,13 @@ int lb_add_particle(lb_handle* h, const lb_particle_desc* desc, int* id_out);
 /* Queue nsteps time steps (nsteps >= 0) on the handle's stream and return
  * without waiting.  Each step: chemical potentials (Eq. chem_potentials);
  * force, streaming with bounce-back and BGK collision; psi/phi transport
- * (Eq. diffusion_reaction); particle update; covering/uncovering. */
+ * (Eq. diffusion_reaction); particle update; covering/uncovering.  The
+ * particle kernels run on a second stream of the library's that joins the
+ * handle's stream before each step ends.  A box without particles runs whole
+ * groups of 8 steps as one captured CUDA graph (captured on first use and
+ * again after its parameters or launch grids change); while the caller is
+ * itself capturing the handle's stream, and on the legacy default stream,
+ * every step is launched plainly.  Results do not depend on the route. */
 int lb_step(lb_handle* h, int nsteps);
 
 /* Run nsteps steps like lb_step, but with every kernel on the handle's stream
