@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="single form: keep the size heuristic's z chunks")
     ap.add_argument("--form", default="single", choices=["single", "batched", "served"])
     ap.add_argument("--boxes", type=int, default=64, help="batched form: number of boxes")
+    ap.add_argument("--graph-steps", type=int, default=16,
+                    help="batched form: steps per captured CUDA graph (more than --steps: plain launches)")
     ap.add_argument("--requests", type=int, default=32, help="served form: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="served form: mean arrivals per second")
     return ap.parse_args()
@@ -550,7 +552,8 @@ def run_batched(args):
     target = wls[0].steps                        # steps per simulation (5000)
     nodes = sum(w.nodes for w in wls)
     stream = torch.cuda.Stream()
-    batch = lbdp.Batch(precision=args.precision, arena_bytes=0, graph_steps=16, stream=stream.cuda_stream)
+    batch = lbdp.Batch(precision=args.precision, arena_bytes=0, graph_steps=args.graph_steps,
+                       stream=stream.cuda_stream)
     boxes = []
     for wl in wls:
         b = batch.add_box(**wl.params)
