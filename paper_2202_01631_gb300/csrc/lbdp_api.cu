@@ -217,6 +217,14 @@ void free_all(lb_handle* h)
         cudaEventDestroy(h->side.bnd_done);
         cudaEventDestroy(h->side.collide_done);
         cudaEventDestroy(h->side.scal_done);
+        if (h->side.s2) {
+            cudaStreamSynchronize(h->side.s2);
+            cudaStreamDestroy(h->side.s2);
+            cudaEventDestroy(h->side.pt_done);
+            cudaEventDestroy(h->side.links_done);
+            cudaEventDestroy(h->side.mark_done);
+            h->side.s2 = nullptr;
+        }
         h->side.s = nullptr;
     }
     if (h->batch)
@@ -958,6 +966,10 @@ int lb_create_in(const lb_params* p, lbb_batch* batch, void* region, lb_handle**
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.bnd_done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.collide_done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.scal_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side.s2, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.pt_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.links_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.mark_done, cudaEventDisableTiming);
     }
     h->region_bytes = layout(p, h->ops, h->red_blocks, nullptr, nullptr);
     if (e == cudaSuccess) {

@@ -25,17 +25,21 @@ struct RowGrid {
 // fused bulk kernel, the bulk transport, the boundary transport, covering.
 enum KernelClass { kKParticles = 0, kKFused, kKScalars, kKScalarsParticles, kKCover, kNumKernelClasses };
 
-// A second stream for the particle kernels of a step, at the device's highest
-// priority.  k_pt_part, k_f_part, k_links, k_collide_particles (the nodes next
-// to particles, which bounce back with the new particle velocities; then
-// bnd_done) and k_cover_mark run there beside kz_fused, which touches no node
-// next to a particle.  After kz_fused (collide_done) k_scalars_particles and
-// k_cover_apply run beside kz_scalars, which waits for bnd_done (it reads the
-// velocity of the boundary nodes); the main stream ends the step by waiting
-// for scal_done.
+// Two more streams for the particle kernels of a step, at the device's highest
+// priority.  On s: k_pt_part, k_f_part, then (after k_links) k_collide_particles
+// (the nodes next to particles, which bounce back with the new particle
+// velocities; then bnd_done).  On s2, after k_pt_part: k_links and
+// k_cover_mark (the new mask needs only the new positions).  All of it runs
+// beside kz_fused, which touches no node next to a particle.  After kz_fused
+// (collide_done) k_scalars_particles and then, once the new mask is there,
+// k_cover_apply run on s beside kz_scalars, which waits for bnd_done (it
+// reads the velocity of the boundary nodes); the main stream ends the step
+// by waiting for scal_done, which follows everything on s2 as well.
 struct SideStream {
     cudaStream_t s;
     cudaEvent_t fork, bnd_done, collide_done, scal_done;
+    cudaStream_t s2;   // k_links, k_cover_mark (single box; NULL in a batch, whose kernels use s alone)
+    cudaEvent_t pt_done, links_done, mark_done;
     int prio;   // the stream's priority, also given to each of its launches as an attribute
 };
 

@@ -29,6 +29,24 @@ inline cudaError_t set_carveout(const void* fn, int blocks, size_t smem)
 
 // Launch of a side-stream kernel with the side stream's priority as a launch
 // attribute, so that it keeps the priority inside captured graphs too.
+// The same on another stream of the side group.
+template <class... A>
+inline void side_launch_on(cudaStream_t st, void (*k)(A...), dim3 grid, size_t smem, const SideStream* side,
+                           A... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kPartThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = side->prio;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <class... A>
 inline void side_launch(void (*k)(A...), dim3 grid, size_t smem, const SideStream* side, A... args)
 {
@@ -79,12 +97,13 @@ struct Ops {
 
     static dim3 pt_grid(const DevParams& P) { return dim3(pt_part_blocks(P), P.np); }
 
-    // One time step.  With particles and a side stream: the particle kernels
+    // One time step.  With particles and side streams: the particle kernels
     // (pressure tensor and force next to the particles, link sums and the
-    // particle update, collide-stream of the nodes next to particles, the new
-    // mask) run on the side stream beside kz_fused; the transport of the bulk
-    // waits for the boundary collide-stream (it reads u there), and the
-    // boundary transport and covering wait for kz_fused and run beside it.
+    // particle update with the new mask on a stream of their own, then the
+    // collide-stream of the nodes next to particles) run beside kz_fused; the
+    // transport of the bulk waits for the boundary collide-stream (it reads u
+    // there), and the boundary transport and covering wait for kz_fused and
+    // run beside it.
     // ev (optional, 6 events): the same kernels in sequence, an event before
     // the first and after each kernel class.
     static cudaError_t launch_step(const DevParams& P, const DevPtrs& D, const RowGrid& g, cudaStream_t s,
@@ -97,15 +116,21 @@ struct Ops {
             cudaEventRecord(side->fork, s);
             cudaStreamWaitEvent(side->s, side->fork, 0);
             side_launch(k_pt_part<C>, pgt, 0, side, P, D);
+            cudaEventRecord(side->pt_done, side->s);
+            cudaStreamWaitEvent(side->s2, side->pt_done, 0);
+            side_launch_on(side->s2, k_links<C>, pg1, kLinkSmem, side, P, D);
+            cudaEventRecord(side->links_done, side->s2);
+            side_launch_on(side->s2, k_cover_mark<C>, pg2, 0, side, P, D);
+            cudaEventRecord(side->mark_done, side->s2);
             side_launch(k_f_part<C>, pg1, 0, side, P, D);
-            side_launch(k_links<C>, pg1, kLinkSmem, side, P, D);
+            cudaStreamWaitEvent(side->s, side->links_done, 0);
             side_launch(k_collide_particles<C>, pg1, 0, side, P, D);
             cudaEventRecord(side->bnd_done, side->s);
-            side_launch(k_cover_mark<C>, pg2, 0, side, P, D);
             kz_fused<C><<<g.zgrid, kZThreads, kFusedSmem, s>>>(P, D);
             cudaEventRecord(side->collide_done, s);
             cudaStreamWaitEvent(side->s, side->collide_done, 0);
             side_launch(k_scalars_particles<C>, pg1, 0, side, P, D);
+            cudaStreamWaitEvent(side->s, side->mark_done, 0);
             // covering touches only nodes next to particles, whose fields the
             // side-stream kernels wrote, and leaves the next step's uniform
             // correction in the other buffer: it runs beside the transport
