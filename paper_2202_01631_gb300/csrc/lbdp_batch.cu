@@ -324,6 +324,10 @@ int lbb_create(const lbb_params* p, lbb_batch** out)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.bnd_done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.collide_done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.scal_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->side.s2, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.pt_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.links_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.mark_done, cudaEventDisableTiming);
     }
     size_t cap = p->arena_bytes;
     if (e == cudaSuccess && cap == 0) {
@@ -367,6 +371,13 @@ void lbb_destroy(lbb_batch* b)
     if (b->side.bnd_done) cudaEventDestroy(b->side.bnd_done);
     if (b->side.collide_done) cudaEventDestroy(b->side.collide_done);
     if (b->side.scal_done) cudaEventDestroy(b->side.scal_done);
+    if (b->side.s2) {
+        cudaStreamSynchronize(b->side.s2);
+        cudaStreamDestroy(b->side.s2);
+    }
+    if (b->side.pt_done) cudaEventDestroy(b->side.pt_done);
+    if (b->side.links_done) cudaEventDestroy(b->side.links_done);
+    if (b->side.mark_done) cudaEventDestroy(b->side.mark_done);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }

@@ -38,7 +38,7 @@ enum KernelClass { kKParticles = 0, kKFused, kKScalars, kKScalarsParticles, kKCo
 struct SideStream {
     cudaStream_t s;
     cudaEvent_t fork, bnd_done, collide_done, scal_done;
-    cudaStream_t s2;   // k_links, k_cover_mark (single box; NULL in a batch, whose kernels use s alone)
+    cudaStream_t s2;   // the link sums and the new mask
     cudaEvent_t pt_done, links_done, mark_done;
     int prio;   // the stream's priority, also given to each of its launches as an attribute
 };
@@ -69,8 +69,8 @@ struct PrecOps {
 
 // One batched step over the boxes of a batch (see lbdp_batch_kernels.cuh):
 // the bulk kernels with the z chunk length each one's configuration names,
-// the particle kernels with the single-box split, then the step count of
-// every box that ran.
+// the particle kernels with the single-box split and stream order, then the
+// step count of every box that ran.
 struct BoxLaunch;
 constexpr int kNumBatchClasses = 2;   // bulk kernels the autotuner times: fused, transport
 constexpr int kNumBatchCfgs = 3;      // z chunks of 8, 16 or 32 planes per block

@@ -303,18 +303,26 @@ struct BOps {
             LaunchPlan* L = Ls + l;
             L->L.par = par;   // copied into each launch's parameters at the call
             if (side) {
+                // the single-box stream order: link sums and the new mask on
+                // s2 beside the force and boundary collide on s
                 cudaEventRecord(side->fork, s);
                 cudaStreamWaitEvent(side->s, side->fork, 0);
                 side_launch(kb_pt_part<C>, L->ptg, 0, side, L->L);
+                cudaEventRecord(side->pt_done, side->s);
+                cudaStreamWaitEvent(side->s2, side->pt_done, 0);
+                side_launch_on(side->s2, kb_links<C>, L->link, lsm, side, L->L);
+                cudaEventRecord(side->links_done, side->s2);
+                side_launch_on(side->s2, kb_cover_mark<C>, L->cover, 0, side, L->L);
+                cudaEventRecord(side->mark_done, side->s2);
                 side_launch(kb_f_part<C>, L->link, 0, side, L->L);
-                side_launch(kb_links<C>, L->link, lsm, side, L->L);
+                cudaStreamWaitEvent(side->s, side->links_done, 0);
                 side_launch(kb_collide_particles<C>, L->link, 0, side, L->L);
                 cudaEventRecord(side->bnd_done, side->s);
-                side_launch(kb_cover_mark<C>, L->cover, 0, side, L->L);
                 if ((e = node(0, cfg[0], L, s)) != cudaSuccess) return e;
                 cudaEventRecord(side->collide_done, s);
                 cudaStreamWaitEvent(side->s, side->collide_done, 0);
                 side_launch(kb_scalars_particles<C>, L->link, 0, side, L->L);
+                cudaStreamWaitEvent(side->s, side->mark_done, 0);
                 side_launch(kb_cover_apply<C>, L->cover, 0, side, L->L);
                 cudaEventRecord(side->scal_done, side->s);
                 cudaStreamWaitEvent(s, side->bnd_done, 0);
