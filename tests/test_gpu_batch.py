@@ -169,6 +169,32 @@ def test_single_box_chunk_lengths_and_tuner(lbdp, precision):
     _assert_same(box, ref)
 
 
+@pytest.mark.parametrize("shape", [(1, 1, 40), (33, 17, 3), (40, 5, 2)])
+def test_tuner_on_thin_boxes(lbdp, shape):
+    """The chunk tuner and explicit chunk lengths on boxes thinner than a
+    column tile or a chunk (one node wide, three planes, two planes): every
+    choice stays within the box and gives the bits of the heuristic."""
+    nx, ny, nz = shape
+    params = dict(W.BASE_PARAMS, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 0), E=0.2, k_d=1e-3,
+                  body_force=(1e-5, 0.0, 0.0))
+
+    def run(planes):
+        box = lbdp.Box(precision="fp32", **params)
+        box.set_fields(**_fields((nz, ny, nx), 7))
+        if planes == "tune":
+            got, ms = box.tune(reps=2)
+            assert all(1 <= v <= nz for v in got.values()) and all(m > 0 for m in ms.values())
+        elif planes is not None:
+            box.set_planes(*planes)
+            assert all(1 <= v <= nz for v in box.planes().values())
+        box.step(12)
+        return box
+
+    ref = run(None)
+    for planes in ("tune", (1, 1), (64, 64), (2, 5)):
+        _assert_same(run(planes), ref)
+
+
 def test_single_box_graph_runs_match_plain_steps(lbdp):
     """lb_step runs whole groups of steps of a box without particles as
     captured CUDA graphs and the rest as plain launches: one step at a time, in
